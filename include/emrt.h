@@ -1,0 +1,210 @@
+/*
+ * emrt — dynamic urban EM ray tracing on one GB300 GPU (arXiv 2303.10521).
+ *
+ * C-ABI of libemrt.so.  Plain pointers and sizes only.  Unless stated
+ * otherwise every array argument is a DEVICE pointer owned by the caller and
+ * every call is asynchronous on the given stream (a cudaStream_t passed as
+ * void*; NULL = legacy default stream).  Argument errors are returned
+ * synchronously.  Errors raised inside kernels (capacity overflow, traversal
+ * stack overflow) are recorded in the scene's device error word and returned
+ * by emrt_sync.  The scene owns its BVHs and scratch buffers; it allocates
+ * them in emrt_scene_create and grows them inside emrt_trace only when a
+ * larger problem than before is requested.
+ *
+ * Method (paper passages): per frame the engine refits a BVH over static
+ * building triangles and moving vehicle boxes (Sec. II-A "dynamic BVH",
+ * Sec. III-A "only the subtrees need to be rebuilt", Sec. V-A factors 1-2),
+ * shoots and bounces rays from each transmitter with reception spheres at
+ * every receiver (Sec. II-A: direct and reflected rays), stores paths as
+ * face-ID sequences in a cache revalidated every frame (Sec. II-A path
+ * caching, Sec. III-B: paths kept and updated until removed), and gives each
+ * accepted path its complex field with Fresnel reflection, spreading and the
+ * Doppler shift (Sec. III-C, Eq. 3), reduced per receiver into the
+ * statistics of Table III (Sec. V-D).
+ *
+ * Geometry conventions
+ *  - float32 metres centred on the scene origin, z up.
+ *  - Static faces are convex planar polygons (CCW seen from outside); the
+ *    triangles of tri_xyz must cover them exactly (tri_face maps each
+ *    triangle to its face).  Static face IDs are 0..F_s-1.
+ *  - Vehicle v is the axis-aligned box pos - half .. pos + half; its faces
+ *    have IDs F_s + 6v + j, j = 0..5 for -x, +x, -y, +y, -z, +z.
+ *
+ * Path record (8 x uint32, canonical order = lexicographic over w0..w6):
+ *   w0 transmitter index, w1 receiver index,
+ *   w2 depth (bits 0-3) | EMRT_PATH_* flags (bits 8-15),
+ *   w3..w6 face IDs of the reflections in travel order (0xFFFFFFFF unused),
+ *   w7 smallest index j of a discovering ray (ray = offset + stride * j).
+ */
+#ifndef EMRT_H
+#define EMRT_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMRT_MAX_DEPTH 4
+#define EMRT_PATH_WORDS 8
+#define EMRT_NO_FACE 0xFFFFFFFFu
+
+/* path flags (w2 bits 8-15) */
+#define EMRT_PATH_VALID 0x100u     /* passed image-method acceptance        */
+#define EMRT_PATH_MARGINAL 0x200u  /* a reflection point lies within the
+                                      margin of its face boundary           */
+
+/* emrt_trace_params.flags */
+#define EMRT_TRACE_KEEP_REJECTED 0x1u  /* output every unique candidate, with
+                                          EMRT_PATH_VALID set on accepted ones */
+#define EMRT_TRACE_SORT_RAYS 0x2u      /* reorder rays between bounces by
+                                          origin cell and direction bin       */
+/* emrt_revalidate flags */
+#define EMRT_REVALIDATE_KEEP 0x1u      /* do not compact: flag only          */
+
+typedef void *emrt_stream; /* cudaStream_t */
+
+typedef enum {
+  EMRT_OK = 0,
+  EMRT_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter               */
+  EMRT_ERR_OOM = 2,         /* device allocation failed                      */
+  EMRT_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
+  EMRT_ERR_CAPACITY = 4,    /* an output or scratch buffer was too small;
+                               emrt_stats reports the required sizes         */
+  EMRT_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                 */
+  EMRT_ERR_STATE = 6,       /* call order violated (e.g. trace before update) */
+  EMRT_ERR_DEVICE = 7       /* kernel-raised error (traversal stack overflow) */
+} emrt_status;
+
+typedef struct emrt_scene_s *emrt_scene;
+
+/* Static scene description.  All pointers are device pointers read during
+ * emrt_scene_create only; the scene keeps its own copies. */
+typedef struct {
+  uint32_t n_static_faces;   /* F_s                                        */
+  const uint32_t *face_off;  /* [F_s+1] vertex offsets into face_xyz       */
+  const float *face_xyz;     /* [face_off[F_s]][3] polygon vertices         */
+  const uint32_t *face_mat;  /* [F_s] material index                        */
+  uint32_t n_tris;           /* T                                           */
+  const float *tri_xyz;      /* [T][3][3]                                   */
+  const uint32_t *tri_face;  /* [T] face of each triangle                   */
+  uint32_t n_vehicles;       /* V (may be 0)                                */
+  const float *veh_half;     /* [V][3] box half extents                     */
+  uint32_t veh_mat;          /* material of every vehicle face              */
+  uint32_t max_rx;           /* capacity for receivers                      */
+  uint32_t max_tx;           /* capacity for transmitters (<= 255)          */
+  uint32_t rebuild_every;    /* dynamic BVH: full rebuild every n updates,
+                                refit otherwise (0 = default 10)            */
+} emrt_scene_desc;
+
+/* Sec. II-A/III-A: builds the static LBVH once (Morton codes, radix sort,
+ * binary radix tree, bottom-up boxes).  Synchronises the stream. */
+emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream s,
+                              emrt_scene *out);
+void emrt_scene_destroy(emrt_scene sc);
+
+/* Per-frame update (Sec. II-A dynamic BVH; Sec. III-C static base station,
+ * tracked object speeds): vehicle boxes at veh_pos (box centres, [V][3]) with
+ * velocities veh_vel; receivers rx_pos/rx_vel [n_rx][3]; transmitters
+ * tx_pos/tx_vel [n_tx][3].  Refits the vehicle BVH (rebuilds it every
+ * rebuild_every calls) and rebuilds the receiver BVH.  veh_* may be NULL
+ * when V = 0; *_vel may be NULL for zero velocity. */
+emrt_status emrt_scene_update_dynamic(emrt_scene sc, const float *veh_pos,
+                                      const float *veh_vel, const float *rx_pos,
+                                      const float *rx_vel, uint32_t n_rx,
+                                      const float *tx_pos, const float *tx_vel,
+                                      uint32_t n_tx, emrt_stream s);
+
+typedef struct {
+  uint32_t max_depth;   /* K reflections, 0..EMRT_MAX_DEPTH               */
+  uint64_t n_rays;      /* N directions on the Fibonacci sphere per Tx      */
+  uint64_t ray_offset;  /* traced subset: ray offset + stride * j, j<count  */
+  uint64_t ray_stride;  /* >= 1                                            */
+  uint64_t ray_count;   /* 0 = all rays from ray_offset                    */
+  uint32_t flags;       /* EMRT_TRACE_*                                     */
+} emrt_trace_params;
+
+/* Caller-owned path set. */
+typedef struct {
+  uint32_t *rec;      /* [capacity][8] records (device)                    */
+  uint32_t capacity;  /* records that rec can hold                          */
+  uint32_t *count;    /* device uint32: records present / required          */
+} emrt_paths;
+
+/* Plain per-frame discovery (Sec. II-A): shoot-and-bounce from every Tx with
+ * reception spheres r(L) = 1.25 sqrt(8 pi / (3 sqrt(3) N)) L, deduplicate
+ * the face-ID sequences, accept them by the image method with occlusion
+ * rays, write the accepted set to out in canonical order.  If more records
+ * are needed than out->capacity, *out->count receives the required number,
+ * the excess is dropped and emrt_sync returns EMRT_ERR_CAPACITY. */
+emrt_status emrt_trace(emrt_scene sc, const emrt_trace_params *p,
+                       emrt_paths *out, emrt_stream s);
+
+/* Cached frame (Sec. II-A path caching, Sec. III-B): re-runs image-method
+ * acceptance and occlusion on every record of `cache` with the current
+ * poses; removes the paths that failed (keeps order) unless
+ * EMRT_REVALIDATE_KEEP, in which case only EMRT_PATH_VALID is updated. */
+emrt_status emrt_revalidate(emrt_scene sc, emrt_paths *cache, uint32_t flags,
+                            emrt_stream s);
+
+/* cache <- sorted union of cache and fresh (both canonical). */
+emrt_status emrt_cache_merge(emrt_scene sc, emrt_paths *cache,
+                             const emrt_paths *fresh, emrt_stream s);
+
+typedef struct {
+  uint32_t n_mat;
+  const double *eps_r;   /* [n_mat] relative permittivity (device)         */
+  const double *sigma;   /* [n_mat] conductivity S/m (device)               */
+  const double *gamma;   /* [n_mat] Table I coefficients, or NULL           */
+  uint32_t const_gamma;  /* 1: Gamma_s = -gamma, Gamma_p = +gamma           */
+} emrt_materials;
+
+typedef struct {
+  double *path_out;  /* [paths capacity][4]: Re a, Im a, tau (s), f_D (Hz);
+                        a is the complex amplitude for 1 W transmit power  */
+  double *pair_out;  /* [n_tx][n_rx][8]: Re h, Im h, sum|a|^2, mean f_D,
+                        RMS Doppler spread, mean delay, RMS delay spread,
+                        path count (h = coherent sum of a)                  */
+  double *rx_out;    /* [n_rx][2]: received power (W) coherent per Tx and
+                        summed over Tx; fully incoherent power (W)          */
+} emrt_channel_out;
+
+/* Field of every path in `paths` at frequency freq_hz (Sec. III-C, Eq. 3
+ * generalised to moving endpoints and reflectors; Table III statistics).
+ * Paths must be canonical (sorted). */
+emrt_status emrt_channel(emrt_scene sc, const emrt_paths *paths,
+                         const emrt_materials *m, double freq_hz,
+                         double tx_power_w, emrt_channel_out *out,
+                         emrt_stream s);
+
+/* Adjoint of emrt_channel's coherent sums over a frozen path topology:
+ * given dloss_dh [n_tx][n_rx][2] (d loss / d Re h, d loss / d Im h),
+ * accumulates (overwrites) grad_eps [n_mat], grad_sigma [n_mat] and
+ * grad_tx [n_tx][3].  Reflection points are recomputed, not stored. */
+emrt_status emrt_channel_backward(emrt_scene sc, const emrt_paths *paths,
+                                  const emrt_materials *m, double freq_hz,
+                                  const double *dloss_dh, double *grad_eps,
+                                  double *grad_sigma, double *grad_tx,
+                                  emrt_stream s);
+
+typedef struct {
+  uint64_t segments[EMRT_MAX_DEPTH + 1]; /* closest-hit segments per bounce */
+  uint64_t candidates;        /* reception-sphere detections                 */
+  uint64_t unique_candidates; /* after deduplication                         */
+  uint64_t accepted;          /* paths written                                */
+  uint64_t occlusion_rays;    /* any-hit segments traced by acceptance        */
+  uint64_t node_visits;       /* BVH nodes visited by closest-hit traversal  */
+  uint64_t tri_tests;         /* triangles tested by closest-hit traversal   */
+  uint32_t error_bits;        /* device error word                            */
+  uint32_t required_candidates; /* scratch sizes needed by the last trace   */
+  uint32_t required_paths;
+} emrt_stats;
+
+/* Waits for the stream, reads and clears the device error word, returns the
+ * first error recorded since the last emrt_sync and fills *st if non-NULL. */
+emrt_status emrt_sync(emrt_scene sc, emrt_stream s, emrt_stats *st);
+
+const char *emrt_status_string(emrt_status e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,544 @@
+// C-ABI of libemrt.so: scene lifetime, argument checks, scratch management
+// and the order of kernel launches for each entry point.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "bvh.cuh"
+#include "field.cuh"
+#include "trace.cuh"
+
+using namespace emrt;
+
+struct emrt_scene_s {
+  int device = 0;
+  uint32_t Fs = 0, T = 0, V = 0, NV = 0, max_rx = 0, max_tx = 0, veh_mat = 0;
+  uint32_t rebuild_every = 10, n_updates = 0;
+  double4 *face_plane = nullptr;
+  uint4 *face_info = nullptr;
+  float4 *face_vert = nullptr;
+  float4 *bbox = nullptr;  // [4]: lo, hi, scratch
+  BVHBuf stat, dyn, rxb;
+  float4 *veh_half = nullptr, *veh_lo = nullptr, *veh_hi = nullptr, *veh_vel = nullptr;
+  float4 *rx_pos = nullptr, *rx_vel = nullptr, *tx_pos = nullptr, *tx_vel = nullptr;
+  uint32_t n_rx = 0, n_tx = 0;
+  bool updated = false;
+  Counters *ctr = nullptr;
+  uint32_t *hist = nullptr, *partial = nullptr;
+  // primary direction table cache
+  uint64_t dt_n = 0, dt_off = 0, dt_stride = 0;
+  uint32_t dt_count = 0;
+  float4 *dirs = nullptr;
+  uint32_t dirs_cap = 0;
+  // ray ping-pong buffers
+  Ray *rays[2] = {nullptr, nullptr};
+  uint64_t ray_cap = 0;
+  // candidate and path scratch
+  uint32_t cand_cap = 0, want_cand = 0;
+  uint32_t *cand = nullptr, *uniq = nullptr, *head = nullptr, *pos = nullptr;
+  KeyW<4> *keys[2] = {nullptr, nullptr};
+  uint32_t *vals[2] = {nullptr, nullptr};
+  // reduction / adjoint scratch
+  uint32_t *seg_b = nullptr, *seg_e = nullptr;
+  uint32_t pair_cap = 0;
+  double *contrib = nullptr;
+  uint64_t contrib_cap = 0;
+  emrt_status sticky = EMRT_OK;
+};
+
+namespace {
+
+constexpr uint32_t kNO = EMRT_NO_FACE;
+
+emrt_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return EMRT_OK;
+  if (e == cudaErrorMemoryAllocation) return EMRT_ERR_OOM;
+  return EMRT_ERR_CUDA;
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t _e = (x);                       \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+template <typename T>
+cudaError_t grow(T **p, uint64_t &cap, uint64_t need) {
+  if (need <= cap && *p) return cudaSuccess;
+  cudaFree(*p);
+  *p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (need ? need : 1));
+  if (e == cudaSuccess) cap = need;
+  return e;
+}
+
+__global__ void k_faces(const uint32_t *off, const float *xyz, const uint32_t *mat, uint32_t F,
+                        double4 *plane, uint4 *info, float4 *vert) {
+  uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  uint32_t a = off[f], nv = off[f + 1] - off[f];
+  double nx = 0, ny = 0, nz = 0, cx = 0, cy = 0, cz = 0;
+  for (uint32_t i = 0; i < nv; i++) {
+    const float *p = xyz + 3ull * (a + i);
+    const float *q = xyz + 3ull * (a + (i + 1) % nv);
+    double px = p[0], py = p[1], pz = p[2], qx = q[0], qy = q[1], qz = q[2];
+    // Newell's normal of a planar polygon
+    nx += (py - qy) * (pz + qz);
+    ny += (pz - qz) * (px + qx);
+    nz += (px - qx) * (py + qy);
+    cx += px; cy += py; cz += pz;
+    vert[a + i] = make_float4(p[0], p[1], p[2], 0.f);
+  }
+  double l = sqrt(nx * nx + ny * ny + nz * nz);
+  nx /= l; ny /= l; nz /= l;
+  plane[f] = make_double4(nx, ny, nz, (nx * cx + ny * cy + nz * cz) / nv);
+  info[f] = make_uint4(a, nv, mat[f], 0u);
+}
+
+__global__ void k_half(const float *h, uint32_t V, float4 *out) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < V) out[v] = make_float4(h[3 * v], h[3 * v + 1], h[3 * v + 2], 0.f);
+}
+
+// per-frame state: box corners in float32 arithmetic, receivers, transmitters
+__global__ void k_update(const float *vp, const float *vv, const float4 *half, uint32_t V,
+                         float4 *lo, float4 *hi, float4 *vel, const float *rp, const float *rv,
+                         uint32_t R, float4 *rxp, float4 *rxv, const float *tp, const float *tv,
+                         uint32_t X, float4 *txp, float4 *txv) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < V) {
+    float4 h = half[i];
+    float x = vp[3 * i], y = vp[3 * i + 1], z = vp[3 * i + 2];
+    lo[i] = make_float4(__fsub_rn(x, h.x), __fsub_rn(y, h.y), __fsub_rn(z, h.z), 0.f);
+    hi[i] = make_float4(__fadd_rn(x, h.x), __fadd_rn(y, h.y), __fadd_rn(z, h.z), 0.f);
+    vel[i] = vv ? make_float4(vv[3 * i], vv[3 * i + 1], vv[3 * i + 2], 0.f) : make_float4(0, 0, 0, 0);
+  }
+  if (i < R) {
+    rxp[i] = make_float4(rp[3 * i], rp[3 * i + 1], rp[3 * i + 2], 0.f);
+    rxv[i] = rv ? make_float4(rv[3 * i], rv[3 * i + 1], rv[3 * i + 2], 0.f) : make_float4(0, 0, 0, 0);
+  }
+  if (i < X) {
+    txp[i] = make_float4(tp[3 * i], tp[3 * i + 1], tp[3 * i + 2], 0.f);
+    txv[i] = tv ? make_float4(tv[3 * i], tv[3 * i + 1], tv[3 * i + 2], 0.f) : make_float4(0, 0, 0, 0);
+  }
+}
+
+__global__ void k_check_cand(Counters *c, uint32_t cap) {
+  if (c->n_cand > cap) atomicOr(&c->err, ERR_CAND_OVERFLOW);
+}
+
+__global__ void k_publish_count(const Counters *c, uint32_t *count) { *count = c->n_accepted; }
+
+__global__ void k_clamp_count(const uint32_t *n, uint32_t cap, uint32_t *out) { *out = min(*n, cap); }
+
+GeomView geom(const emrt_scene_s *s) {
+  GeomView g;
+  g.stat = s->stat.view();
+  g.dyn = s->dyn.view();
+  g.rxb = s->rxb.view();
+  g.face_plane = s->face_plane;
+  g.face_info = s->face_info;
+  g.face_vert = s->face_vert;
+  g.veh_lo = s->veh_lo;
+  g.veh_hi = s->veh_hi;
+  g.veh_vel = s->veh_vel;
+  g.rx_pos = s->rx_pos;
+  g.rx_vel = s->rx_vel;
+  g.tx_pos = s->tx_pos;
+  g.tx_vel = s->tx_vel;
+  g.n_static_faces = s->Fs;
+  g.n_veh = s->V;
+  g.n_rx = s->n_rx;
+  g.n_tx = s->n_tx;
+  g.veh_mat = s->veh_mat;
+  return g;
+}
+
+cudaError_t ensure_cand(emrt_scene_s *s, uint64_t need) {
+  if (need <= s->cand_cap && s->cand) return cudaSuccess;
+  uint64_t c = 0;
+  cudaError_t e;
+  uint64_t cap = std::max<uint64_t>(need, 1024);
+  if (cap > 0xffffffffull / 2) cap = 0xffffffffull / 2;
+  e = grow(&s->cand, c, cap * 8); if (e) return e; c = 0;
+  e = grow(&s->uniq, c, cap * 8); if (e) return e; c = 0;
+  e = grow(&s->head, c, cap); if (e) return e; c = 0;
+  e = grow(&s->pos, c, cap); if (e) return e; c = 0;
+  for (int k = 0; k < 2; k++) {
+    e = grow(&s->keys[k], c, cap); if (e) return e; c = 0;
+    e = grow(&s->vals[k], c, cap); if (e) return e; c = 0;
+  }
+  s->cand_cap = (uint32_t)cap;
+  return cudaSuccess;
+}
+
+// Sort + unique of records [0, *n) of `src` (capacity cap) into s->uniq;
+// unique count in ctr->n_unique.
+void dedup(emrt_scene_s *s, const uint32_t *src, const uint32_t *n, uint32_t cap, KeyLayout kl,
+           cudaStream_t st) {
+  Counters *c = s->ctr;
+  launch_path_keys(src, n, cap, kl, s->keys[0], s->vals[0], &c->n_eff, st);
+  bool alt = radix_sort<4>(&c->n_eff, s->keys[0], s->vals[0], s->keys[1], s->vals[1], kl.total,
+                           s->hist, st);
+  KeyW<4> *ks = s->keys[alt ? 1 : 0];
+  uint32_t *vs = s->vals[alt ? 1 : 0];
+  launch_heads(ks, &c->n_eff, s->head, st);
+  exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_unique, s->partial, st);
+  launch_unique(src, ks, vs, s->head, s->pos, &c->n_eff, s->uniq, st);
+}
+
+emrt_status check_paths(const emrt_paths *p) {
+  if (!p || !p->rec || !p->count) return EMRT_ERR_INVALID_ARG;
+  return EMRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *emrt_status_string(emrt_status e) {
+  switch (e) {
+    case EMRT_OK: return "ok";
+    case EMRT_ERR_INVALID_ARG: return "invalid argument";
+    case EMRT_ERR_OOM: return "device allocation failed";
+    case EMRT_ERR_CUDA: return "CUDA runtime error";
+    case EMRT_ERR_CAPACITY: return "buffer capacity exceeded";
+    case EMRT_ERR_TIMEOUT: return "bounded device wait gave up";
+    case EMRT_ERR_STATE: return "call order violated";
+    case EMRT_ERR_DEVICE: return "kernel-raised error";
+  }
+  return "unknown status";
+}
+
+emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt_scene *out) {
+  if (!d || !out) return EMRT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((d->n_static_faces && (!d->face_off || !d->face_xyz || !d->face_mat)) ||
+      (d->n_tris && (!d->tri_xyz || !d->tri_face)) || (d->n_vehicles && !d->veh_half) ||
+      d->max_tx == 0 || d->max_tx > 255 || d->max_rx == 0)
+    return EMRT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  emrt_scene_s *s = new emrt_scene_s();
+  cudaGetDevice(&s->device);
+  s->Fs = d->n_static_faces;
+  s->T = d->n_tris;
+  s->V = d->n_vehicles;
+  s->max_rx = d->max_rx;
+  s->max_tx = d->max_tx;
+  s->veh_mat = d->veh_mat;
+  s->rebuild_every = d->rebuild_every ? d->rebuild_every : 10;
+  auto fail = [&](cudaError_t e) {
+    emrt_scene_destroy(s);
+    return cuda_status(e);
+  };
+  cudaError_t e;
+  uint64_t c = 0;
+  if (s->Fs) {
+    e = cudaMemcpy(&s->NV, d->face_off + s->Fs, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e) return fail(e);
+  }
+  if ((e = grow(&s->face_plane, c, std::max(s->Fs, 1u)))) return fail(e); c = 0;
+  if ((e = grow(&s->face_info, c, std::max(s->Fs, 1u)))) return fail(e); c = 0;
+  if ((e = grow(&s->face_vert, c, std::max(s->NV, 1u)))) return fail(e); c = 0;
+  if ((e = grow(&s->bbox, c, 4))) return fail(e); c = 0;
+  if (s->Fs) k_faces<<<ceil_div(s->Fs, 128), 128, 0, st>>>(d->face_off, d->face_xyz, d->face_mat,
+                                                          s->Fs, s->face_plane, s->face_info,
+                                                          s->face_vert);
+  if ((e = grow(&s->ctr, c, 1))) return fail(e); c = 0;
+  if ((e = grow(&s->hist, c, 256 * kPrimGrid + 1))) return fail(e); c = 0;
+  if ((e = grow(&s->partial, c, kPrimGrid + 1))) return fail(e); c = 0;
+  cudaMemsetAsync(s->ctr, 0, sizeof(Counters), st);
+  bbox_of_tris(d->tri_xyz, s->T, s->bbox, st);
+  if ((e = bvh_alloc(s->stat, PRIM_TRI, std::max(s->T, 2u)))) return fail(e);
+  if ((e = bvh_build_tris(s->stat, d->tri_xyz, d->tri_face, s->T, s->bbox, s->hist, st)))
+    return fail(e);
+  if ((e = bvh_alloc(s->dyn, PRIM_BOX, std::max(s->V, 2u)))) return fail(e);
+  if ((e = bvh_alloc(s->rxb, PRIM_POINT, std::max(s->max_rx, 2u)))) return fail(e);
+  uint32_t V1 = std::max(s->V, 1u);
+  if ((e = grow(&s->veh_half, c, V1))) return fail(e); c = 0;
+  if ((e = grow(&s->veh_lo, c, V1))) return fail(e); c = 0;
+  if ((e = grow(&s->veh_hi, c, V1))) return fail(e); c = 0;
+  if ((e = grow(&s->veh_vel, c, V1))) return fail(e); c = 0;
+  if ((e = grow(&s->rx_pos, c, s->max_rx))) return fail(e); c = 0;
+  if ((e = grow(&s->rx_vel, c, s->max_rx))) return fail(e); c = 0;
+  if ((e = grow(&s->tx_pos, c, s->max_tx))) return fail(e); c = 0;
+  if ((e = grow(&s->tx_vel, c, s->max_tx))) return fail(e); c = 0;
+  if (s->V) k_half<<<ceil_div(s->V, 256), 256, 0, st>>>(d->veh_half, s->V, s->veh_half);
+  e = cudaStreamSynchronize(st);
+  if (!e) e = cudaGetLastError();
+  if (e) return fail(e);
+  *out = s;
+  return EMRT_OK;
+}
+
+void emrt_scene_destroy(emrt_scene s) {
+  if (!s) return;
+  cudaFree(s->face_plane); cudaFree(s->face_info); cudaFree(s->face_vert); cudaFree(s->bbox);
+  bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb);
+  cudaFree(s->veh_half); cudaFree(s->veh_lo); cudaFree(s->veh_hi); cudaFree(s->veh_vel);
+  cudaFree(s->rx_pos); cudaFree(s->rx_vel); cudaFree(s->tx_pos); cudaFree(s->tx_vel);
+  cudaFree(s->ctr); cudaFree(s->hist); cudaFree(s->partial); cudaFree(s->dirs);
+  cudaFree(s->rays[0]); cudaFree(s->rays[1]);
+  cudaFree(s->cand); cudaFree(s->uniq); cudaFree(s->head); cudaFree(s->pos);
+  for (int k = 0; k < 2; k++) { cudaFree(s->keys[k]); cudaFree(s->vals[k]); }
+  cudaFree(s->seg_b); cudaFree(s->seg_e); cudaFree(s->contrib);
+  delete s;
+}
+
+emrt_status emrt_scene_update_dynamic(emrt_scene s, const float *veh_pos, const float *veh_vel,
+                                      const float *rx_pos, const float *rx_vel, uint32_t n_rx,
+                                      const float *tx_pos, const float *tx_vel, uint32_t n_tx,
+                                      emrt_stream stream) {
+  if (!s) return EMRT_ERR_INVALID_ARG;
+  if ((s->V && !veh_pos) || n_rx == 0 || n_rx > s->max_rx || n_tx == 0 || n_tx > s->max_tx ||
+      !rx_pos || !tx_pos)
+    return EMRT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->n_rx = n_rx;
+  s->n_tx = n_tx;
+  uint32_t m = std::max(s->V, std::max(n_rx, n_tx));
+  k_update<<<ceil_div(m, 256), 256, 0, st>>>(veh_pos, veh_vel, s->veh_half, s->V, s->veh_lo,
+                                             s->veh_hi, s->veh_vel, rx_pos, rx_vel, n_rx,
+                                             s->rx_pos, s->rx_vel, tx_pos, tx_vel, n_tx, s->tx_pos,
+                                             s->tx_vel);
+  if (s->V) {
+    if (s->n_updates % s->rebuild_every == 0)
+      CK(bvh_build_boxes(s->dyn, s->veh_lo, s->veh_hi, s->V, s->bbox, s->hist, st));
+    else
+      CK(bvh_refit_boxes(s->dyn, s->veh_lo, s->veh_hi, st));
+  }
+  CK(bvh_build_points(s->rxb, s->rx_pos, n_rx, s->bbox, s->hist, st));
+  s->n_updates++;
+  s->updated = true;
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out,
+                       emrt_stream stream) {
+  if (!s || !p || check_paths(out) != EMRT_OK) return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  if (p->max_depth > EMRT_MAX_DEPTH || p->n_rays == 0 || p->ray_stride == 0 ||
+      p->ray_offset >= p->n_rays)
+    return EMRT_ERR_INVALID_ARG;
+  uint64_t count = p->ray_count ? p->ray_count
+                                : (p->n_rays - p->ray_offset + p->ray_stride - 1) / p->ray_stride;
+  if (count == 0 || p->ray_offset + (count - 1) * p->ray_stride >= p->n_rays ||
+      count > (1u << 24) || count * s->n_tx >= (1ull << 32))
+    return EMRT_ERR_INVALID_ARG;
+  uint32_t nf = s->Fs + 6 * s->V;
+  KeyLayout kl = key_layout(s->n_tx, s->n_rx, nf + 1, (int)p->max_depth);
+  if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Counters *c = s->ctr;
+  // primary direction table (recomputed when the ray set changes)
+  if (!s->dirs || s->dt_n != p->n_rays || s->dt_off != p->ray_offset ||
+      s->dt_stride != p->ray_stride || s->dt_count != count) {
+    uint64_t cap = s->dirs_cap;
+    CK(grow(&s->dirs, cap, count));
+    s->dirs_cap = (uint32_t)cap;
+    KeyW<1> *k0, *k1;
+    uint32_t *v0, *v1;
+    CK(cudaMalloc(&k0, sizeof(KeyW<1>) * count * 2));
+    CK(cudaMalloc(&v0, sizeof(uint32_t) * count * 2));
+    k1 = k0 + count;
+    v1 = v0 + count;
+    build_dir_table(p->n_rays, p->ray_offset, p->ray_stride, (uint32_t)count, s->dirs, k0, k1, v0,
+                    v1, &c->tmp, s->hist, st);
+    cudaStreamSynchronize(st);
+    cudaFree(k0);
+    cudaFree(v0);
+    s->dt_n = p->n_rays;
+    s->dt_off = p->ray_offset;
+    s->dt_stride = p->ray_stride;
+    s->dt_count = (uint32_t)count;
+  }
+  uint64_t nrays = count * s->n_tx;
+  if (p->max_depth > 0 && nrays > s->ray_cap) {
+    cudaFree(s->rays[0]);
+    cudaFree(s->rays[1]);
+    s->rays[0] = s->rays[1] = nullptr;
+    s->ray_cap = 0;
+    CK(cudaMalloc(&s->rays[0], sizeof(Ray) * nrays));
+    CK(cudaMalloc(&s->rays[1], sizeof(Ray) * nrays));
+    s->ray_cap = nrays;
+  }
+  uint64_t want = std::max<uint64_t>(s->want_cand,
+                                     std::max<uint64_t>(1u << 16, 4ull * s->n_tx * s->n_rx * (p->max_depth + 1)));
+  want = std::max<uint64_t>(want, out->capacity);
+  CK(ensure_cand(s, want));
+  // counters: keep the error word, clear the rest
+  cudaMemsetAsync(reinterpret_cast<char *>(c) + sizeof(uint32_t), 0,
+                  sizeof(Counters) - sizeof(uint32_t), st);
+  GeomView g = geom(s);
+  float kappa = (float)(1.25 * sqrt(8.0 * 3.14159265358979323846 /
+                                    (3.0 * sqrt(3.0) * (double)p->n_rays)));
+  int grid = bounce_grid();
+  for (uint32_t b = 0; b <= p->max_depth; b++) {
+    BounceLaunch L;
+    L.g = g;
+    L.rin = b ? s->rays[(b - 1) & 1] : nullptr;
+    L.n_in = &c->n_ray[b];
+    L.n_primary = (uint32_t)nrays;
+    L.dirs = s->dirs;
+    L.count = (uint32_t)count;
+    L.rout = s->rays[b & 1];
+    L.n_out = &c->n_ray[b + 1];
+    L.cand = s->cand;
+    L.cand_cap = s->cand_cap;
+    L.n_cand = &c->n_cand;
+    L.work = &c->work[b];
+    L.ctr = c;
+    L.kappa = kappa;
+    L.b = (int)b;
+    L.K = (int)p->max_depth;
+    launch_bounce(L, grid, st);
+  }
+  k_check_cand<<<1, 1, 0, st>>>(c, s->cand_cap);
+  dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
+  launch_accept(g, s->uniq, &c->n_unique, c, st);
+  launch_keep_flags(s->uniq, &c->n_unique, (p->flags & EMRT_TRACE_KEEP_REJECTED) ? 1 : 0, s->head,
+                    st);
+  exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_accepted, s->partial, st);
+  launch_scatter(s->uniq, &c->n_unique, s->head, s->pos, out->rec, out->capacity, &c->n_accepted,
+                 c, st);
+  k_publish_count<<<1, 1, 0, st>>>(c, out->count);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emrt_stream stream) {
+  if (!s || check_paths(cache) != EMRT_OK) return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(ensure_cand(s, std::max<uint64_t>(s->want_cand, cache->capacity)));
+  Counters *c = s->ctr;
+  GeomView g = geom(s);
+  // clamp the count to the capacity before acceptance
+  k_clamp_count<<<1, 1, 0, st>>>(cache->count, cache->capacity, &c->n_eff);
+  launch_copy_records(cache->rec, &c->n_eff, s->uniq, cache->capacity, st);
+  launch_accept(g, s->uniq, &c->n_eff, c, st);
+  int keep_all = (flags & EMRT_REVALIDATE_KEEP) ? 1 : 0;
+  launch_keep_flags(s->uniq, &c->n_eff, keep_all, s->head, st);
+  exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_accepted, s->partial, st);
+  launch_scatter(s->uniq, &c->n_eff, s->head, s->pos, cache->rec, cache->capacity, &c->n_accepted,
+                 c, st);
+  k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_cache_merge(emrt_scene s, emrt_paths *cache, const emrt_paths *fresh,
+                             emrt_stream stream) {
+  if (!s || check_paths(cache) != EMRT_OK || check_paths(fresh) != EMRT_OK)
+    return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(ensure_cand(s, std::max<uint64_t>(s->want_cand,
+                                       (uint64_t)cache->capacity + fresh->capacity)));
+  Counters *c = s->ctr;
+  uint32_t nf = s->Fs + 6 * s->V;
+  KeyLayout kl = key_layout(s->n_tx, s->n_rx, nf + 1, EMRT_MAX_DEPTH);
+  if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
+  launch_concat(cache->rec, cache->count, cache->capacity, fresh->rec, fresh->count,
+                fresh->capacity, s->cand, s->cand_cap, &c->tmp, c, st);
+  dedup(s, s->cand, &c->tmp, s->cand_cap, kl, st);
+  launch_keep_flags(s->uniq, &c->n_unique, 1, s->head, st);
+  exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_accepted, s->partial, st);
+  launch_scatter(s->uniq, &c->n_unique, s->head, s->pos, cache->rec, cache->capacity,
+                 &c->n_accepted, c, st);
+  k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+static emrt_status check_mat(const emrt_materials *m) {
+  if (!m || m->n_mat == 0 || !m->eps_r || !m->sigma || (m->const_gamma && !m->gamma))
+    return EMRT_ERR_INVALID_ARG;
+  return EMRT_OK;
+}
+
+static MatView matview(const emrt_materials *m) {
+  MatView v;
+  v.eps_r = m->eps_r;
+  v.sigma = m->sigma;
+  v.gamma = m->gamma;
+  v.n_mat = m->n_mat;
+  v.const_gamma = m->const_gamma;
+  return v;
+}
+
+emrt_status emrt_channel(emrt_scene s, const emrt_paths *paths, const emrt_materials *m,
+                         double freq_hz, double tx_power_w, emrt_channel_out *out,
+                         emrt_stream stream) {
+  if (!s || check_paths(paths) != EMRT_OK || check_mat(m) != EMRT_OK || !out || !out->path_out ||
+      !out->pair_out || !(freq_hz > 0))
+    return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  GeomView g = geom(s);
+  uint64_t np = (uint64_t)s->n_tx * s->n_rx;
+  if (np > s->pair_cap) {
+    uint64_t c = 0;
+    CK(grow(&s->seg_b, c, np)); c = 0;
+    CK(grow(&s->seg_e, c, np));
+    s->pair_cap = (uint32_t)np;
+  }
+  launch_field(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, out->path_out,
+               st);
+  launch_reduce(paths->rec, paths->count, paths->capacity, out->path_out, s->n_tx, s->n_rx,
+                tx_power_w, s->seg_b, s->seg_e, out->pair_out, out->rx_out, st);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_channel_backward(emrt_scene s, const emrt_paths *paths, const emrt_materials *m,
+                                  double freq_hz, const double *dloss_dh, double *grad_eps,
+                                  double *grad_sigma, double *grad_tx, emrt_stream stream) {
+  if (!s || check_paths(paths) != EMRT_OK || check_mat(m) != EMRT_OK || !dloss_dh || !grad_eps ||
+      !grad_sigma || !grad_tx || !(freq_hz > 0))
+    return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint64_t need = (uint64_t)paths->capacity * (3 + 2 * EMRT_MAX_DEPTH);
+  CK(grow(&s->contrib, s->contrib_cap, std::max<uint64_t>(need, s->contrib_cap)));
+  GeomView g = geom(s);
+  launch_field_adjoint(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, dloss_dh,
+                       s->n_rx, s->contrib, grad_eps, grad_sigma, grad_tx, st);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
+  if (!s) return EMRT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(st));
+  Counters h;
+  CK(cudaMemcpy(&h, s->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(s->ctr, 0, sizeof(uint32_t)));
+  if (h.n_cand > s->cand_cap) s->want_cand = (uint32_t)std::min<uint64_t>(
+      (uint64_t)h.n_cand + h.n_cand / 4 + 1024, 0x7fffffffull);
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    for (int b = 0; b <= EMRT_MAX_DEPTH; b++) out->segments[b] = h.segments[b];
+    out->candidates = h.n_cand;
+    out->unique_candidates = h.n_unique;
+    out->accepted = h.n_accepted;
+    out->occlusion_rays = h.occl_rays;
+    out->node_visits = h.node_visits;
+    out->tri_tests = h.tri_tests;
+    out->error_bits = h.err;
+    out->required_candidates = h.n_cand;
+    out->required_paths = h.n_accepted;
+  }
+  emrt_status r = s->sticky;
+  s->sticky = EMRT_OK;
+  if (r != EMRT_OK) return r;
+  if (h.err & ERR_STACK) return EMRT_ERR_DEVICE;
+  if (h.err & (ERR_CAND_OVERFLOW | ERR_PATH_OVERFLOW | ERR_RAY_OVERFLOW)) return EMRT_ERR_CAPACITY;
+  return EMRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,348 @@
+// LBVH build and refit.  Binary radix tree of Karras (2012, "Maximizing
+// parallelism in the construction of BVHs, octrees and k-d trees"), restated
+// from the published algorithm; boxes are filled bottom-up with one arrival
+// counter per inner node (the second thread to arrive merges the children).
+#include <cfloat>
+
+#include "bvh.cuh"
+
+namespace emrt {
+
+namespace {
+
+__device__ inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ inline uint64_t morton63(float3 p, const float4 *bb) {
+  float4 lo = bb[0], hi = bb[1];
+  float q[3] = {(p.x - lo.x) / fmaxf(hi.x - lo.x, 1e-6f), (p.y - lo.y) / fmaxf(hi.y - lo.y, 1e-6f),
+                (p.z - lo.z) / fmaxf(hi.z - lo.z, 1e-6f)};
+  uint32_t c[3];
+  for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 2097151.f);
+  return spread3(c[0]) << 2 | spread3(c[1]) << 1 | spread3(c[2]);
+}
+
+__device__ inline void put_key(KeyW<2> &k, uint64_t v) {
+  k.w[0] = (uint32_t)v;
+  k.w[1] = (uint32_t)(v >> 32);
+}
+__device__ inline uint64_t get_key(const KeyW<2> &k) {
+  return (uint64_t)k.w[1] << 32 | k.w[0];
+}
+
+__global__ void k_morton_tris(const float *t, uint32_t n, const float4 *bb, KeyW<2> *keys,
+                              uint32_t *idx) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float *v = t + 9ull * i;
+  float3 c = make_float3((v[0] + v[3] + v[6]) * (1.f / 3.f), (v[1] + v[4] + v[7]) * (1.f / 3.f),
+                         (v[2] + v[5] + v[8]) * (1.f / 3.f));
+  put_key(keys[i], morton63(c, bb));
+  idx[i] = i;
+}
+
+__global__ void k_morton_boxes(const float4 *lo, const float4 *hi, uint32_t n, const float4 *bb,
+                               KeyW<2> *keys, uint32_t *idx) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = lo[i], b = hi[i];
+  put_key(keys[i], morton63(make_float3(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)), bb));
+  idx[i] = i;
+}
+
+__global__ void k_morton_points(const float4 *p, uint32_t n, const float4 *bb, KeyW<2> *keys,
+                                uint32_t *idx) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  put_key(keys[i], morton63(f3(p[i]), bb));
+  idx[i] = i;
+}
+
+__device__ inline int delta(const KeyW<2> *k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  uint64_t a = get_key(k[i]), b = get_key(k[j]);
+  if (a == b) return 64 + __clz(i ^ j);
+  return __clzll(a ^ b);
+}
+
+// one thread per inner node i in [0, n-2]
+__global__ void k_hierarchy(const KeyW<2> *k, int n, float4 *nodes, uint32_t *leaf_parent) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(k, n, i, i - d);
+  int lmax = 2;
+  while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = delta(k, n, i, j);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int gamma = i + s * d + min(d, 0);
+  int left = min(i, j) == gamma ? ~gamma : gamma;
+  int right = max(i, j) == gamma + 1 ? ~(gamma + 1) : gamma + 1;
+  int *n3 = reinterpret_cast<int *>(nodes + 4ll * i + 3);
+  n3[0] = left;
+  n3[1] = right;
+  n3[3] = 0;
+  int code0 = 2 * i, code1 = 2 * i + 1;
+  if (left < 0) leaf_parent[~left] = code0;
+  else reinterpret_cast<int *>(nodes + 4ll * left + 3)[2] = code0;
+  if (right < 0) leaf_parent[~right] = code1;
+  else reinterpret_cast<int *>(nodes + 4ll * right + 3)[2] = code1;
+  if (i == 0) n3[2] = -1;
+}
+
+__global__ void k_gather_tris(const float *t, const uint32_t *face, const uint32_t *idx,
+                              uint32_t n, float4 *prims) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  uint32_t s = idx[g];
+  const float *v = t + 9ull * s;
+  prims[3ull * g + 0] = make_float4(v[0], v[1], v[2], __uint_as_float(face[s]));
+  prims[3ull * g + 1] = make_float4(v[3], v[4], v[5], 0.f);
+  prims[3ull * g + 2] = make_float4(v[6], v[7], v[8], 0.f);
+}
+
+__global__ void k_gather_boxes(const float4 *lo, const float4 *hi, const uint32_t *idx, uint32_t n,
+                               float4 *prims) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  uint32_t s = idx[g];
+  float4 a = lo[s], b = hi[s];
+  prims[2ull * g + 0] = make_float4(a.x, a.y, a.z, __uint_as_float(s));
+  prims[2ull * g + 1] = make_float4(b.x, b.y, b.z, 0.f);
+}
+
+__global__ void k_move_boxes(const float4 *lo, const float4 *hi, uint32_t n, float4 *prims) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  uint32_t s = __float_as_uint(prims[2ull * g].w);
+  float4 a = lo[s], b = hi[s];
+  prims[2ull * g + 0] = make_float4(a.x, a.y, a.z, __uint_as_float(s));
+  prims[2ull * g + 1] = make_float4(b.x, b.y, b.z, 0.f);
+}
+
+__global__ void k_gather_points(const float4 *p, const uint32_t *idx, uint32_t n, float4 *prims) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  uint32_t s = idx[g];
+  float4 a = p[s];
+  prims[g] = make_float4(a.x, a.y, a.z, __uint_as_float(s));
+}
+
+struct Box { float3 lo, hi; };
+
+template <int KIND>
+__device__ inline Box prim_box(const float4 *prims, uint32_t g) {
+  Box b;
+  if (KIND == PRIM_TRI) {
+    float3 a = f3(prims[3ull * g]), c = f3(prims[3ull * g + 1]), d = f3(prims[3ull * g + 2]);
+    b.lo = make_float3(fminf(a.x, fminf(c.x, d.x)), fminf(a.y, fminf(c.y, d.y)), fminf(a.z, fminf(c.z, d.z)));
+    b.hi = make_float3(fmaxf(a.x, fmaxf(c.x, d.x)), fmaxf(a.y, fmaxf(c.y, d.y)), fmaxf(a.z, fmaxf(c.z, d.z)));
+  } else if (KIND == PRIM_BOX) {
+    b.lo = f3(prims[2ull * g]);
+    b.hi = f3(prims[2ull * g + 1]);
+  } else {
+    b.lo = b.hi = f3(prims[g]);
+  }
+  return b;
+}
+
+template <int KIND>
+__global__ void k_refit(const float4 *prims, uint32_t n, float4 *nodes, const uint32_t *leaf_parent,
+                        uint32_t *flags) {
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n || n < 2) return;
+  Box b = prim_box<KIND>(prims, g);
+  int code = (int)leaf_parent[g];
+  for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
+    int p = code >> 1, side = code & 1;
+    float4 *np = nodes + 4ll * p;
+    reinterpret_cast<float4 *>(np + side)[0] = make_float4(b.lo.x, b.hi.x, b.lo.y, b.hi.y);
+    reinterpret_cast<float2 *>(np + 2)[side] = make_float2(b.lo.z, b.hi.z);
+    __threadfence();
+    if (atomicAdd(&flags[p], 1u) == 0) return;
+    __threadfence();
+    float4 a0 = __ldcg(np), a1 = __ldcg(np + 1), a2 = __ldcg(np + 2);
+    b.lo = make_float3(fminf(a0.x, a1.x), fminf(a0.z, a1.z), fminf(a2.x, a2.z));
+    b.hi = make_float3(fmaxf(a0.y, a1.y), fmaxf(a0.w, a1.w), fmaxf(a2.y, a2.w));
+    int pc = __ldcg(reinterpret_cast<const int *>(np + 3) + 2);
+    if (pc < 0) return;
+    code = pc;
+  }
+}
+
+__device__ inline uint32_t f2o(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline float o2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void k_bbox_init(uint32_t *acc) {
+  if (threadIdx.x < 3) acc[threadIdx.x] = 0xffffffffu;
+  else if (threadIdx.x < 6) acc[threadIdx.x] = 0u;
+}
+
+__global__ void k_bbox_tris(const float *t, uint32_t n, uint32_t *acc) {
+  float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x) {
+    const float *v = t + 3ull * i;
+    for (int k = 0; k < 3; k++) {
+      lo[k] = fminf(lo[k], v[k]);
+      hi[k] = fmaxf(hi[k], v[k]);
+    }
+  }
+  for (int k = 0; k < 3; k++) {
+    for (int o = 16; o; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&acc[k], f2o(lo[k]));
+      atomicMax(&acc[3 + k], f2o(hi[k]));
+    }
+  }
+}
+
+__global__ void k_bbox_fin(const uint32_t *acc, float4 *bb) {
+  if (threadIdx.x == 0) {
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+      lo[k] = o2f(acc[k]);
+      hi[k] = o2f(acc[3 + k]);
+      if (!(lo[k] <= hi[k])) lo[k] = hi[k] = 0.f;
+      lo[k] -= 1.f;
+      hi[k] += 1.f;
+    }
+    bb[0] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    bb[1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+  }
+}
+
+template <int KIND>
+cudaError_t finish_build(BVHBuf &b, cudaStream_t s) {
+  uint32_t n = b.n;
+  if (n >= 2) {
+    k_hierarchy<<<ceil_div(n - 1, 256), 256, 0, s>>>(b.keys, (int)n, b.nodes, b.leaf_parent);
+    cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
+    k_refit<KIND><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+
+template <int KIND>
+cudaError_t sort_codes(BVHBuf &b, uint32_t *hist, cudaStream_t s) {
+  k_set_u32<<<1, 1, 0, s>>>(b.d_n, b.n);
+  bool alt = radix_sort<2>(b.d_n, b.keys, b.idx, b.keys2, b.idx2, 63, hist, s);
+  if (alt) {
+    std::swap(b.keys, b.keys2);
+    std::swap(b.idx, b.idx2);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+BVHView BVHBuf::view() const {
+  BVHView v;
+  v.nodes = nodes;
+  v.prims = prims;
+  v.root = n >= 2 ? 0 : ~0;
+  v.n_prims = n;
+  return v;
+}
+
+cudaError_t bvh_alloc(BVHBuf &b, PrimKind kind, uint32_t cap) {
+  bvh_free(b);
+  b.kind = kind;
+  b.cap = cap < 2 ? 2 : cap;
+  int words = kind == PRIM_TRI ? 3 : (kind == PRIM_BOX ? 2 : 1);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  A((void **)&b.nodes, sizeof(float4) * 4 * (size_t)b.cap);
+  A((void **)&b.prims, sizeof(float4) * words * (size_t)b.cap);
+  A((void **)&b.leaf_parent, sizeof(uint32_t) * b.cap);
+  A((void **)&b.flags, sizeof(uint32_t) * b.cap);
+  A((void **)&b.keys, sizeof(KeyW<2>) * b.cap);
+  A((void **)&b.keys2, sizeof(KeyW<2>) * b.cap);
+  A((void **)&b.idx, sizeof(uint32_t) * b.cap);
+  A((void **)&b.idx2, sizeof(uint32_t) * b.cap);
+  A((void **)&b.d_n, sizeof(uint32_t));
+  return e;
+}
+
+void bvh_free(BVHBuf &b) {
+  cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.leaf_parent); cudaFree(b.flags);
+  cudaFree(b.keys); cudaFree(b.keys2); cudaFree(b.idx); cudaFree(b.idx2); cudaFree(b.d_n);
+  b.nodes = b.prims = nullptr;
+  b.leaf_parent = b.flags = b.idx = b.idx2 = b.d_n = nullptr;
+  b.keys = b.keys2 = nullptr;
+  b.n = b.cap = 0;
+}
+
+cudaError_t bvh_build_tris(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_face, uint32_t n,
+                           const float4 *bbox, uint32_t *hist, cudaStream_t s) {
+  b.n = n;
+  if (n == 0) return cudaSuccess;
+  k_morton_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, n, bbox, b.keys, b.idx);
+  sort_codes<PRIM_TRI>(b, hist, s);
+  k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
+  return finish_build<PRIM_TRI>(b, s);
+}
+
+cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint32_t n,
+                            const float4 *bbox, uint32_t *hist, cudaStream_t s) {
+  b.n = n;
+  if (n == 0) return cudaSuccess;
+  k_morton_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, bbox, b.keys, b.idx);
+  sort_codes<PRIM_BOX>(b, hist, s);
+  k_gather_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, b.idx, n, b.prims);
+  return finish_build<PRIM_BOX>(b, s);
+}
+
+cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaStream_t s) {
+  uint32_t n = b.n;
+  if (n == 0) return cudaSuccess;
+  k_move_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, b.prims);
+  if (n >= 2) {
+    cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
+    k_refit<PRIM_BOX><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const float4 *bbox,
+                             uint32_t *hist, cudaStream_t s) {
+  b.n = n;
+  if (n == 0) return cudaSuccess;
+  k_morton_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, n, bbox, b.keys, b.idx);
+  sort_codes<PRIM_POINT>(b, hist, s);
+  k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, b.idx, n, b.prims);
+  return finish_build<PRIM_POINT>(b, s);
+}
+
+void bbox_of_tris(const float *tri_xyz, uint32_t n, float4 *bbox, cudaStream_t s) {
+  uint32_t *acc = reinterpret_cast<uint32_t *>(bbox + 2);  // 6 words of scratch after bbox
+  k_bbox_init<<<1, 32, 0, s>>>(acc);
+  if (n) k_bbox_tris<<<kPrimGrid, 256, 0, s>>>(tri_xyz, n, acc);
+  k_bbox_fin<<<1, 32, 0, s>>>(acc, bbox);
+}
+
+}  // namespace emrt

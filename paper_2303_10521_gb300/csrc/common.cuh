@@ -1,0 +1,116 @@
+// Shared device-side definitions of the emrt CUDA library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "emrt.h"
+
+namespace emrt {
+
+// ---------------------------------------------------------------------------
+// device error word bits (read and cleared by emrt_sync)
+enum : uint32_t {
+  ERR_CAND_OVERFLOW = 1u,   // candidate scratch too small
+  ERR_PATH_OVERFLOW = 2u,   // caller's path buffer too small
+  ERR_STACK = 4u,           // traversal stack overflow
+  ERR_RAY_OVERFLOW = 8u,    // ray scratch too small (internal bug)
+};
+
+// per-call counters kept in device memory (one struct per scene)
+struct Counters {
+  uint32_t err;                            // error bits (cleared by emrt_sync)
+  uint32_t n_ray[EMRT_MAX_DEPTH + 2];      // rays entering bounce b (b >= 1)
+  uint32_t work[EMRT_MAX_DEPTH + 1];       // persistent-kernel work cursors
+  uint32_t n_cand;                         // candidates appended (may exceed capacity)
+  uint32_t n_eff;                          // candidates stored
+  uint32_t n_unique;
+  uint32_t n_accepted;
+  uint32_t tmp;
+  unsigned long long segments[EMRT_MAX_DEPTH + 1];
+  unsigned long long node_visits;
+  unsigned long long tri_tests;
+  unsigned long long occl_rays;
+};
+
+// ---------------------------------------------------------------------------
+// BVH (binary LBVH, Karras 2012) device view.
+// Node i occupies 4 float4 (64 B):
+//   [0] c0.lo.x c0.hi.x c0.lo.y c0.hi.y
+//   [1] c1.lo.x c1.hi.x c1.lo.y c1.hi.y
+//   [2] c0.lo.z c0.hi.z c1.lo.z c1.hi.z
+//   [3] (int) c0, c1, parent, 0     child >= 0: inner node, < 0: leaf ~prim
+struct BVHView {
+  const float4 *nodes;
+  const float4 *prims;  // triangles: 3 float4 (v0 with face id bits in .w,
+                        // v1, v2); boxes: 2 float4 (lo with vehicle id bits in
+                        // .w, hi); points: 1 float4 (xyz, receiver id bits)
+  int root;             // 0 (inner), ~0 (single leaf)
+  uint32_t n_prims;     // 0 = empty
+};
+
+// ray state between bounces: 48 B
+struct Ray {
+  float4 o_L;    // origin, unfolded length travelled so far (L_acc)
+  float4 d_id;   // unit direction, (tx << 24 | ray index j) bits
+  uint4 faces;   // face IDs of the reflections so far
+};
+
+struct Vec3 { float x, y, z; };
+
+__host__ __device__ inline float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ inline float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ inline float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ inline float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ inline float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+struct D3 { double x, y, z; };
+__device__ inline D3 mkd(double x, double y, double z) { D3 r; r.x = x; r.y = y; r.z = z; return r; }
+__device__ inline D3 operator+(D3 a, D3 b) { return mkd(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ inline D3 operator-(D3 a, D3 b) { return mkd(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ inline D3 operator*(D3 a, double s) { return mkd(a.x * s, a.y * s, a.z * s); }
+__device__ inline double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ inline D3 crossd(D3 a, D3 b) {
+  return mkd(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ inline double normd(D3 a) { return sqrt(dotd(a, a)); }
+__device__ inline D3 tod(float3 a) { return mkd(a.x, a.y, a.z); }
+
+__device__ inline uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp-aggregated append: every active lane that calls this gets a distinct
+// slot; one atomicAdd per converged group of lanes.
+__device__ inline uint32_t warp_append(uint32_t *counter) {
+  uint32_t m = __activemask();
+  uint32_t lane = threadIdx.x & 31;
+  uint32_t leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  return base + __popc(m & lanemask_lt());
+}
+
+// scene geometry (device views) shared by trace, acceptance and field
+struct GeomView {
+  BVHView stat;            // static triangles
+  BVHView dyn;             // vehicle boxes
+  BVHView rxb;             // receiver points
+  const double4 *face_plane;  // [F_s] unit normal, offset
+  const uint4 *face_info;     // [F_s] vertex offset, vertex count, material, 0
+  const float4 *face_vert;    // [NV] polygon vertices
+  const float4 *veh_lo;       // [V] box corners (w unused)
+  const float4 *veh_hi;
+  const float4 *veh_vel;      // [V]
+  const float4 *rx_pos;       // [R]
+  const float4 *rx_vel;
+  const float4 *tx_pos;       // [X]
+  const float4 *tx_vel;
+  uint32_t n_static_faces, n_veh, n_rx, n_tx, veh_mat;
+};
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace emrt

@@ -1,0 +1,488 @@
+// Per-path complex field (Sec. III-C), per-(tx, rx) statistics (Table III,
+// Sec. V-D) and the adjoint of the coherent sums with respect to material
+// permittivity, conductivity and transmitter position.
+//
+// One generic routine computes the field of a path for a scalar type T.  With
+// T = double it is the forward kernel; with T = Dual<N> (value plus N
+// tangents) the same arithmetic carries derivatives with respect to the
+// transmitter coordinates and the (eps_r, sigma) of every bounce, so the
+// adjoint recomputes reflection points instead of storing Jacobians.  Path
+// length and phase are accumulated in FP64 (L / lambda formed in double).
+#include "field.cuh"
+
+namespace emrt {
+
+namespace {
+
+constexpr double kC = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// scalar abstraction
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+  __device__ Dual() {}
+  __device__ Dual(double x) : v(x) {
+#pragma unroll
+    for (int i = 0; i < N; i++) d[i] = 0.0;
+  }
+};
+
+__device__ inline double val(double x) { return x; }
+template <int N> __device__ inline double val(const Dual<N> &x) { return x.v; }
+
+template <int N> __device__ inline Dual<N> operator+(const Dual<N> &a, const Dual<N> &b) {
+  Dual<N> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N> __device__ inline Dual<N> operator-(const Dual<N> &a, const Dual<N> &b) {
+  Dual<N> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N> __device__ inline Dual<N> operator-(const Dual<N> &a) {
+  Dual<N> r; r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = -a.d[i];
+  return r;
+}
+template <int N> __device__ inline Dual<N> operator*(const Dual<N> &a, const Dual<N> &b) {
+  Dual<N> r; r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <int N> __device__ inline Dual<N> operator/(const Dual<N> &a, const Dual<N> &b) {
+  Dual<N> r; r.v = a.v / b.v;
+  double ib = 1.0 / b.v;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int N> __device__ inline Dual<N> operator+(const Dual<N> &a, double b) { return a + Dual<N>(b); }
+template <int N> __device__ inline Dual<N> operator-(const Dual<N> &a, double b) { return a - Dual<N>(b); }
+template <int N> __device__ inline Dual<N> operator-(double a, const Dual<N> &b) { return Dual<N>(a) - b; }
+template <int N> __device__ inline Dual<N> operator*(const Dual<N> &a, double b) {
+  Dual<N> r; r.v = a.v * b;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = a.d[i] * b;
+  return r;
+}
+template <int N> __device__ inline Dual<N> operator*(double b, const Dual<N> &a) { return a * b; }
+template <int N> __device__ inline Dual<N> operator/(const Dual<N> &a, double b) { return a * (1.0 / b); }
+template <int N> __device__ inline Dual<N> operator/(double a, const Dual<N> &b) { return Dual<N>(a) / b; }
+
+__device__ inline double tsqrt(double x) { return sqrt(x); }
+template <int N> __device__ inline Dual<N> tsqrt(const Dual<N> &a) {
+  Dual<N> r; r.v = sqrt(a.v);
+  double h = r.v > 0.0 ? 0.5 / r.v : 0.0;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.d[i] = a.d[i] * h;
+  return r;
+}
+__device__ inline double tabs(double x) { return fabs(x); }
+template <int N> __device__ inline Dual<N> tabs(const Dual<N> &a) { return a.v < 0.0 ? -a : a; }
+__device__ inline double tfrac(double x) { return x - floor(x); }
+template <int N> __device__ inline Dual<N> tfrac(const Dual<N> &a) {
+  Dual<N> r = a; r.v = a.v - floor(a.v); return r;
+}
+__device__ inline void tsincos(double x, double &s, double &c) { sincos(x, &s, &c); }
+template <int N> __device__ inline void tsincos(const Dual<N> &x, Dual<N> &s, Dual<N> &c) {
+  double sv, cv;
+  sincos(x.v, &sv, &cv);
+  s.v = sv; c.v = cv;
+#pragma unroll
+  for (int i = 0; i < N; i++) { s.d[i] = x.d[i] * cv; c.d[i] = -x.d[i] * sv; }
+}
+
+template <typename T> struct V3 { T x, y, z; };
+template <typename T> __device__ inline V3<T> mk3(T x, T y, T z) { V3<T> r; r.x = x; r.y = y; r.z = z; return r; }
+template <typename T> __device__ inline V3<T> operator+(const V3<T> &a, const V3<T> &b) { return mk3<T>(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <typename T> __device__ inline V3<T> operator-(const V3<T> &a, const V3<T> &b) { return mk3<T>(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <typename T, typename S> __device__ inline V3<T> scale(const V3<T> &a, const S &s) { return mk3<T>(a.x * s, a.y * s, a.z * s); }
+template <typename T> __device__ inline T dot(const V3<T> &a, const V3<T> &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T> __device__ inline V3<T> cross(const V3<T> &a, const V3<T> &b) {
+  return mk3<T>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <typename T> __device__ inline V3<T> lift(double x, double y, double z) { return mk3<T>(T(x), T(y), T(z)); }
+
+template <typename T> struct Cx { T re, im; };
+template <typename T> __device__ inline Cx<T> cx(T r, T i) { Cx<T> c; c.re = r; c.im = i; return c; }
+template <typename T> __device__ inline Cx<T> operator+(const Cx<T> &a, const Cx<T> &b) { return cx<T>(a.re + b.re, a.im + b.im); }
+template <typename T> __device__ inline Cx<T> operator-(const Cx<T> &a, const Cx<T> &b) { return cx<T>(a.re - b.re, a.im - b.im); }
+template <typename T> __device__ inline Cx<T> operator*(const Cx<T> &a, const Cx<T> &b) {
+  return cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T> __device__ inline Cx<T> cscale(const Cx<T> &a, const T &s) { return cx<T>(a.re * s, a.im * s); }
+template <typename T> __device__ inline Cx<T> operator/(const Cx<T> &a, const Cx<T> &b) {
+  T den = b.re * b.re + b.im * b.im;
+  return cx<T>((a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den);
+}
+// principal square root
+template <typename T> __device__ inline Cx<T> csqrt_p(const Cx<T> &z) {
+  T r = tsqrt(z.re * z.re + z.im * z.im);
+  if (val(r) == 0.0) return cx<T>(T(0.0), T(0.0));
+  if (val(z.re) >= 0.0) {
+    T t = tsqrt((r + z.re) * 0.5);
+    return cx<T>(t, z.im / (t * 2.0));
+  }
+  T t = tsqrt((r - z.re) * 0.5);
+  if (val(z.im) >= 0.0) return cx<T>(z.im / (t * 2.0), t);
+  return cx<T>(-(z.im) / (t * 2.0), -t);
+}
+
+template <typename T> struct CV3 { Cx<T> x, y, z; };
+template <typename T> __device__ inline Cx<T> cdot(const CV3<T> &a, const V3<T> &b) {
+  return cx<T>(a.x.re * b.x + a.y.re * b.y + a.z.re * b.z, a.x.im * b.x + a.y.im * b.y + a.z.im * b.z);
+}
+
+template <typename T> __device__ inline V3<T> unitv(const V3<T> &a) {
+  T n = tsqrt(dot(a, a));
+  return scale(a, T(1.0) / n);
+}
+// vertical transverse polarisation of the ideal omnidirectional antenna
+template <typename T> __device__ inline V3<T> polar(const V3<T> &k) {
+  V3<T> p = mk3<T>(T(0.0) - k.z * k.x, T(0.0) - k.z * k.y, T(1.0) - k.z * k.z);
+  T n = tsqrt(dot(p, p));
+  if (val(n) < 1e-12) return lift<T>(1.0, 0.0, 0.0);
+  return scale(p, T(1.0) / n);
+}
+
+// ---------------------------------------------------------------------------
+struct PathGeom {
+  uint32_t k, f[EMRT_MAX_DEPTH];
+  double n[EMRT_MAX_DEPTH][3];
+  double d[EMRT_MAX_DEPTH];
+  uint32_t mat[EMRT_MAX_DEPTH];
+  float3 vel[EMRT_MAX_DEPTH];
+};
+
+// indices of a record within the scene (records written by the library
+// always are; records supplied by a caller are checked before any load)
+__device__ inline bool record_ok(const GeomView &g, const uint32_t *r) {
+  uint32_t k = r[2] & 15u, nf = g.n_static_faces + 6u * g.n_veh;
+  if (r[0] >= g.n_tx || r[1] >= g.n_rx || k > EMRT_MAX_DEPTH) return false;
+  for (uint32_t q = 0; q < k; q++)
+    if (r[3 + q] >= nf) return false;
+  return true;
+}
+
+__device__ inline void load_geom(const GeomView &g, const uint32_t *rec, PathGeom &P) {
+  uint4 a = reinterpret_cast<const uint4 *>(rec)[0], b = reinterpret_cast<const uint4 *>(rec)[1];
+  P.k = min(a.z & 15u, (uint32_t)EMRT_MAX_DEPTH);
+  uint32_t f[4] = {a.w, b.x, b.y, b.z};
+  for (uint32_t q = 0; q < P.k; q++) {
+    P.f[q] = f[q];
+    if (f[q] < g.n_static_faces) {
+      double4 p = g.face_plane[f[q]];
+      P.n[q][0] = p.x; P.n[q][1] = p.y; P.n[q][2] = p.z; P.d[q] = p.w;
+      P.mat[q] = g.face_info[f[q]].z;
+      P.vel[q] = make_float3(0.f, 0.f, 0.f);
+    } else {
+      uint32_t v = (f[q] - g.n_static_faces) / 6u, j = (f[q] - g.n_static_faces) % 6u;
+      int ax = j >> 1;
+      bool neg = (j & 1u) == 0;
+      float4 lo = g.veh_lo[v], hi = g.veh_hi[v];
+      double s = neg ? -1.0 : 1.0;
+      P.n[q][0] = ax == 0 ? s : 0.0; P.n[q][1] = ax == 1 ? s : 0.0; P.n[q][2] = ax == 2 ? s : 0.0;
+      double c = ax == 0 ? (neg ? lo.x : hi.x) : (ax == 1 ? (neg ? lo.y : hi.y) : (neg ? lo.z : hi.z));
+      P.d[q] = s * c;
+      P.mat[q] = g.veh_mat;
+      P.vel[q] = f3(g.veh_vel[v]);
+    }
+  }
+}
+
+// Field of one path.  tx: transmitter position (seeded with tangents by the
+// caller), epsr/sig: per-bounce material parameters.
+template <typename T>
+__device__ inline void path_field(const PathGeom &P, V3<T> tx, V3<double> rx, const T *epsr,
+                                  const T *sig, const double *gam, bool const_gamma, double freq,
+                                  Cx<T> &amp, T &Lout, V3<T> *kh) {
+  const uint32_t k = P.k;
+  V3<T> I[EMRT_MAX_DEPTH + 1], Q[EMRT_MAX_DEPTH + 2];
+  I[0] = tx;
+  for (uint32_t q = 0; q < k; q++) {
+    V3<T> n = lift<T>(P.n[q][0], P.n[q][1], P.n[q][2]);
+    T s = (dot(n, I[q]) - P.d[q]) * 2.0;
+    I[q + 1] = I[q] - scale(n, s);
+  }
+  Q[0] = tx;
+  Q[k + 1] = lift<T>(rx.x, rx.y, rx.z);
+  for (int q = (int)k; q >= 1; q--) {
+    V3<T> n = lift<T>(P.n[q - 1][0], P.n[q - 1][1], P.n[q - 1][2]);
+    V3<T> D = Q[q + 1] - I[q];
+    T t = (T(P.d[q - 1]) - dot(n, I[q])) / dot(n, D);
+    Q[q] = I[q] + scale(D, t);
+  }
+  T L(0.0);
+  for (uint32_t q = 0; q <= k; q++) {
+    V3<T> D = Q[q + 1] - Q[q];
+    T l = tsqrt(dot(D, D));
+    L = L + l;
+    kh[q] = scale(D, T(1.0) / l);
+  }
+  const double lam = kC / freq;
+  V3<T> p0 = polar(kh[0]);
+  CV3<T> E;
+  E.x = cx<T>(p0.x, T(0.0)); E.y = cx<T>(p0.y, T(0.0)); E.z = cx<T>(p0.z, T(0.0));
+  for (uint32_t q = 1; q <= k; q++) {
+    V3<T> n = lift<T>(P.n[q - 1][0], P.n[q - 1][1], P.n[q - 1][2]);
+    V3<T> kin = kh[q - 1], kout = kh[q];
+    T cos_t = tabs(dot(kin, n));
+    V3<T> sv = cross(kin, n);
+    if (val(dot(sv, sv)) < 1e-24) {  // normal incidence: any s orthogonal to kin
+      sv = cross(kin, lift<T>(1.0, 0.0, 0.0));
+      if (val(dot(sv, sv)) < 1e-12) sv = cross(kin, lift<T>(0.0, 1.0, 0.0));
+    }
+    sv = unitv(sv);
+    V3<T> pin = cross(sv, kin), pout = cross(sv, kout);
+    Cx<T> gs, gp;
+    if (const_gamma) {
+      gs = cx<T>(T(-gam[q - 1]), T(0.0));
+      gp = cx<T>(T(gam[q - 1]), T(0.0));
+    } else {
+      Cx<T> ec = cx<T>(epsr[q - 1], T(0.0) - sig[q - 1] * (1.0 / (2.0 * kPi * freq * kEps0)));
+      T sin2 = T(1.0) - cos_t * cos_t;
+      Cx<T> root = csqrt_p(cx<T>(ec.re - sin2, ec.im));
+      Cx<T> ct = cx<T>(cos_t, T(0.0));
+      gs = (ct - root) / (ct + root);
+      Cx<T> ecct = cscale(ec, cos_t);
+      gp = (ecct - root) / (ecct + root);
+    }
+    Cx<T> es = cdot(E, sv), ep = cdot(E, pin);
+    Cx<T> a = gs * es, b = gp * ep;
+    E.x = cscale(a, sv.x) + cscale(b, pout.x);
+    E.y = cscale(a, sv.y) + cscale(b, pout.y);
+    E.z = cscale(a, sv.z) + cscale(b, pout.z);
+  }
+  Cx<T> rcv = cdot(E, polar(kh[k]));
+  T cyc = L * (1.0 / lam);
+  T ph = tfrac(cyc) * (-2.0 * kPi);
+  T sp, cp;
+  tsincos(ph, sp, cp);
+  T sc = T(lam / (4.0 * kPi)) / L;
+  amp = cscale(rcv * cx<T>(cp, sp), sc);
+  Lout = L;
+}
+
+__global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32_t *n, uint32_t cap,
+                        double freq, double *out) {
+  uint32_t cnt = min(*n, cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    PathGeom P;
+    const uint32_t *r = rec + 8ull * i;
+    uint32_t tx = r[0], rx = r[1];
+    if (!record_ok(g, r)) {  // malformed record: no field
+      reinterpret_cast<double4 *>(out)[i] = make_double4(0.0, 0.0, 0.0, 0.0);
+      continue;
+    }
+    load_geom(g, r, P);
+    double epsr[EMRT_MAX_DEPTH], sig[EMRT_MAX_DEPTH], gam[EMRT_MAX_DEPTH];
+    for (uint32_t q = 0; q < P.k; q++) {
+      uint32_t mm = min(P.mat[q], m.n_mat - 1);
+      epsr[q] = m.eps_r[mm];
+      sig[q] = m.sigma[mm];
+      gam[q] = m.gamma ? m.gamma[mm] : 0.0;
+    }
+    float3 t3 = f3(g.tx_pos[tx]), r3 = f3(g.rx_pos[rx]);
+    V3<double> txp = mk3<double>(t3.x, t3.y, t3.z), rxp = mk3<double>(r3.x, r3.y, r3.z);
+    Cx<double> a;
+    double L;
+    V3<double> kh[EMRT_MAX_DEPTH + 1];
+    path_field<double>(P, txp, rxp, epsr, sig, gam, m.const_gamma != 0, freq, a, L, kh);
+    // Doppler: rate of change of the unfolded length (Eq. 3 generalised)
+    float3 vt = f3(g.tx_vel[tx]), vr = f3(g.rx_vel[rx]);
+    double dL = -(vt.x * kh[0].x + vt.y * kh[0].y + vt.z * kh[0].z) +
+                (vr.x * kh[P.k].x + vr.y * kh[P.k].y + vr.z * kh[P.k].z);
+    for (uint32_t q = 1; q <= P.k; q++) {
+      float3 v = P.vel[q - 1];
+      dL += v.x * (kh[q - 1].x - kh[q].x) + v.y * (kh[q - 1].y - kh[q].y) + v.z * (kh[q - 1].z - kh[q].z);
+    }
+    double4 o;
+    o.x = a.re;
+    o.y = a.im;
+    o.z = L / kC;
+    o.w = -(freq / kC) * dL;
+    reinterpret_cast<double4 *>(out)[i] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_pair_bounds(const uint32_t *rec, const uint32_t *n, uint32_t cap, uint32_t n_tx,
+                              uint32_t n_rx, uint32_t *beg, uint32_t *end) {
+  uint32_t cnt = min(*n, cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    if (rec[8ull * i] >= n_tx || rec[8ull * i + 1] >= n_rx) continue;
+    uint32_t p = rec[8ull * i] * n_rx + rec[8ull * i + 1];
+    if (i == 0 || rec[8ull * (i - 1)] * n_rx + rec[8ull * (i - 1) + 1] != p) beg[p] = i;
+    if (i + 1 == cnt || rec[8ull * (i + 1)] * n_rx + rec[8ull * (i + 1) + 1] != p) end[p] = i + 1;
+  }
+}
+
+// one warp per (tx, rx) pair; fixed-order lane-strided sums and shuffle tree
+__global__ void k_pair_reduce(const double *path_out, const uint32_t *beg, const uint32_t *end,
+                              uint32_t n_pairs, double *pair_out) {
+  uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t p = warp; p < n_pairs; p += nw) {
+    uint32_t b = beg[p], e = end[p];
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t i = b + lane; i < e; i += 32) {
+      double4 o = reinterpret_cast<const double4 *>(path_out)[i];
+      double w = o.x * o.x + o.y * o.y;
+      s[0] += o.x; s[1] += o.y; s[2] += w;
+      s[3] += w * o.w; s[4] += w * o.w * o.w;
+      s[5] += w * o.z; s[6] += w * o.z * o.z;
+    }
+    for (int k = 0; k < 7; k++)
+      for (int off = 16; off; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
+    if (lane == 0) {
+      double *o = pair_out + 8ull * p;
+      double pw = s[2];
+      double fm = pw > 0 ? s[3] / pw : 0.0, tm = pw > 0 ? s[5] / pw : 0.0;
+      double fv = pw > 0 ? s[4] / pw - fm * fm : 0.0, tv = pw > 0 ? s[6] / pw - tm * tm : 0.0;
+      o[0] = s[0]; o[1] = s[1]; o[2] = pw;
+      o[3] = fm; o[4] = sqrt(fmax(fv, 0.0));
+      o[5] = tm; o[6] = sqrt(fmax(tv, 0.0));
+      o[7] = (double)(e - b);
+    }
+  }
+}
+
+__global__ void k_rx_power(const double *pair_out, uint32_t n_tx, uint32_t n_rx, double pt,
+                           double *rx_out) {
+  uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rx) return;
+  double coh = 0.0, inc = 0.0;
+  for (uint32_t t = 0; t < n_tx; t++) {
+    const double *o = pair_out + 8ull * (t * n_rx + r);
+    coh += o[0] * o[0] + o[1] * o[1];
+    inc += o[2];
+  }
+  rx_out[2 * r] = pt * coh;
+  rx_out[2 * r + 1] = pt * inc;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: per path, tangents for tx (3) and (eps_r, sigma) of each bounce
+constexpr int kTan = 3 + 2 * EMRT_MAX_DEPTH;
+constexpr int kAdjBlock = 64;
+
+__global__ void __launch_bounds__(kAdjBlock) k_field_tangents(GeomView g, MatView m,
+                                                              const uint32_t *rec, const uint32_t *n,
+                                                              uint32_t cap, double freq,
+                                                              const double *dloss_dh, uint32_t n_rx,
+                                                              double *contrib) {
+  using D = Dual<kTan>;
+  uint32_t cnt = min(*n, cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    PathGeom P;
+    const uint32_t *r = rec + 8ull * i;
+    uint32_t tx = r[0], rx = r[1];
+    double *c = contrib + (size_t)kTan * i;
+    if (!record_ok(g, r)) {
+      for (int t = 0; t < kTan; t++) c[t] = 0.0;
+      continue;
+    }
+    load_geom(g, r, P);
+    D epsr[EMRT_MAX_DEPTH], sig[EMRT_MAX_DEPTH];
+    double gam[EMRT_MAX_DEPTH];
+    for (uint32_t q = 0; q < P.k; q++) {
+      uint32_t mm = min(P.mat[q], m.n_mat - 1);
+      epsr[q] = D(m.eps_r[mm]);
+      epsr[q].d[3 + 2 * q] = 1.0;
+      sig[q] = D(m.sigma[mm]);
+      sig[q].d[4 + 2 * q] = 1.0;
+      gam[q] = m.gamma ? m.gamma[mm] : 0.0;
+    }
+    float3 t3 = f3(g.tx_pos[tx]), r3 = f3(g.rx_pos[rx]);
+    V3<D> txp = mk3<D>(D(t3.x), D(t3.y), D(t3.z));
+    txp.x.d[0] = 1.0; txp.y.d[1] = 1.0; txp.z.d[2] = 1.0;
+    V3<double> rxp = mk3<double>(r3.x, r3.y, r3.z);
+    Cx<D> a;
+    D L;
+    V3<D> kh[EMRT_MAX_DEPTH + 1];
+    path_field<D>(P, txp, rxp, epsr, sig, gam, m.const_gamma != 0, freq, a, L, kh);
+    const double *gh = dloss_dh + 2ull * (tx * n_rx + rx);
+    double gx = gh[0], gy = gh[1];
+    for (int t = 0; t < kTan; t++) c[t] = gx * a.re.d[t] + gy * a.im.d[t];
+  }
+}
+
+// one block per gradient entry, fixed-order sum over paths
+__global__ void k_grad_reduce(GeomView g, MatView m, const uint32_t *rec, const uint32_t *n,
+                              uint32_t cap, const double *contrib, double *grad_eps,
+                              double *grad_sigma, double *grad_tx) {
+  __shared__ double sh[256];
+  uint32_t cnt = min(*n, cap);
+  uint32_t pid = blockIdx.x;  // [0, n_mat) eps, [n_mat, 2 n_mat) sigma, then tx*3+c
+  double s = 0.0;
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const uint32_t *r = rec + 8ull * i;
+    const double *c = contrib + (size_t)kTan * i;
+    if (pid < 2 * m.n_mat) {
+      uint32_t mat = pid % m.n_mat;
+      bool is_sig = pid >= m.n_mat;
+      uint32_t k = min(r[2] & 15u, (uint32_t)EMRT_MAX_DEPTH);
+      uint32_t f[4] = {r[3], r[4], r[5], r[6]};
+      for (uint32_t q = 0; q < k; q++) {
+        uint32_t fm = f[q] < g.n_static_faces ? g.face_info[f[q]].z : g.veh_mat;
+        if (min(fm, m.n_mat - 1) == mat) s += c[3 + 2 * q + (is_sig ? 1 : 0)];
+      }
+    } else {
+      uint32_t t = (pid - 2 * m.n_mat) / 3, comp = (pid - 2 * m.n_mat) % 3;
+      if (r[0] == t) s += c[comp];
+    }
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (pid < m.n_mat) grad_eps[pid] = sh[0];
+    else if (pid < 2 * m.n_mat) grad_sigma[pid - m.n_mat] = sh[0];
+    else grad_tx[pid - 2 * m.n_mat] = sh[0];
+  }
+}
+
+}  // namespace
+
+void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
+                  uint32_t cap, double freq, double *path_out, cudaStream_t s) {
+  k_field<<<152 * 8, 128, 0, s>>>(g, m, rec, n, cap, freq, path_out);
+}
+
+void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
+                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, uint32_t *seg_begin,
+                   uint32_t *seg_end, double *pair_out, double *rx_out, cudaStream_t s) {
+  uint32_t np = n_tx * n_rx;
+  cudaMemsetAsync(seg_begin, 0, sizeof(uint32_t) * np, s);
+  cudaMemsetAsync(seg_end, 0, sizeof(uint32_t) * np, s);
+  k_pair_bounds<<<152 * 8, 256, 0, s>>>(rec, n, cap, n_tx, n_rx, seg_begin, seg_end);
+  k_pair_reduce<<<ceil_div(np, 8) < 152 * 16 ? ceil_div(np, 8) : 152 * 16, 256, 0, s>>>(
+      path_out, seg_begin, seg_end, np, pair_out);
+  if (rx_out) k_rx_power<<<ceil_div(n_rx, 256), 256, 0, s>>>(pair_out, n_tx, n_rx, tx_power_w, rx_out);
+}
+
+int adjoint_grid() { return 152 * 4; }
+
+void launch_field_adjoint(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
+                          uint32_t cap, double freq, const double *dloss_dh, uint32_t n_rx,
+                          double *contrib, double *grad_eps, double *grad_sigma, double *grad_tx,
+                          cudaStream_t s) {
+  k_field_tangents<<<adjoint_grid(), kAdjBlock, 0, s>>>(g, m, rec, n, cap, freq, dloss_dh, n_rx,
+                                                        contrib);
+  uint32_t n_par = 2 * m.n_mat + 3 * g.n_tx;
+  k_grad_reduce<<<n_par, 256, 0, s>>>(g, m, rec, n, cap, contrib, grad_eps, grad_sigma, grad_tx);
+}
+
+}  // namespace emrt

@@ -1,0 +1,190 @@
+// LSD radix sort, exclusive scan (fixed grids, device-side counts).
+#include "prims.cuh"
+
+namespace emrt {
+
+namespace {
+
+__device__ inline void block_range(uint32_t n, uint32_t &lo, uint32_t &hi) {
+  // contiguous chunk per block, a multiple of the block size
+  uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+  per = (per + kPrimBlock - 1) / kPrimBlock * kPrimBlock;
+  lo = min(n, blockIdx.x * per);
+  hi = min(n, lo + per);
+}
+
+template <int W>
+__device__ inline uint32_t digit_of(const KeyW<W> &k, int pass) {
+  return (k.w[pass >> 2] >> ((pass & 3) * 8)) & 255u;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kPrimBlock) k_hist(const uint32_t *d_n, const KeyW<W> *keys,
+                                                     int pass, uint32_t *hist) {
+  __shared__ uint32_t sh[256];
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t lo, hi;
+  block_range(*d_n, lo, hi);
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += kPrimBlock)
+    atomicAdd(&sh[digit_of<W>(keys[i], pass)], 1u);
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = sh[threadIdx.x];
+}
+
+// exclusive scan of n (<= a few 100k) words in one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *v, uint32_t n, uint32_t *total) {
+  __shared__ uint32_t part[1024];
+  uint32_t per = (n + 1023) / 1024;
+  uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; i++) s += v[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += t;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (uint32_t i = lo; i < hi; i++) {
+    uint32_t t = v[i];
+    v[i] = run;
+    run += t;
+  }
+  if (threadIdx.x == 1023 && total) *total = part[1023];
+}
+
+template <int W>
+__global__ void __launch_bounds__(kPrimBlock) k_scatter(const uint32_t *d_n, const KeyW<W> *kin,
+                                                        const uint32_t *vin, KeyW<W> *kout,
+                                                        uint32_t *vout, int pass,
+                                                        const uint32_t *offs) {
+  constexpr int NW = kPrimBlock / 32;
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_tot[256];
+  __shared__ uint32_t s_cnt[NW][256];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  s_base[t] = offs[t * gridDim.x + blockIdx.x];
+  uint32_t lo, hi;
+  block_range(*d_n, lo, hi);
+  for (uint32_t r0 = lo; r0 < hi; r0 += kPrimBlock) {
+    for (int w = 0; w < NW; w++) s_cnt[w][t] = 0;
+    __syncthreads();
+    uint32_t i = r0 + t;
+    bool valid = i < hi;
+    KeyW<W> k;
+    uint32_t v = 0, dg = 256;
+    if (valid) {
+      k = kin[i];
+      v = vin[i];
+      dg = digit_of<W>(k, pass);
+    }
+    uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) s_cnt[warp][dg] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t run = 0;
+      for (int w = 0; w < NW; w++) {
+        uint32_t c = s_cnt[w][t];
+        s_cnt[w][t] = run;
+        run += c;
+      }
+      s_tot[t] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_base[dg] + s_cnt[warp][dg] + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    s_base[t] += s_tot[t];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kPrimBlock) k_scan_reduce(const uint32_t *d_n, const uint32_t *in,
+                                                            uint32_t *partial) {
+  __shared__ uint32_t sh[kPrimBlock / 32];
+  uint32_t lo, hi;
+  block_range(*d_n, lo, hi);
+  uint32_t s = 0;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += kPrimBlock) s += in[i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kPrimBlock / 32; w++) t += sh[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kPrimBlock) k_scan_down(const uint32_t *d_n, const uint32_t *in,
+                                                          uint32_t *out, const uint32_t *partial) {
+  __shared__ uint32_t sh[kPrimBlock / 32];
+  __shared__ uint32_t carry;
+  uint32_t lo, hi;
+  block_range(*d_n, lo, hi);
+  if (threadIdx.x == 0) carry = partial[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t r0 = lo; r0 < hi; r0 += kPrimBlock) {
+    uint32_t i = r0 + threadIdx.x;
+    uint32_t x = i < hi ? in[i] : 0;
+    uint32_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0, tot = 0;
+    for (int w = 0; w < kPrimBlock / 32; w++) {
+      uint32_t c = sh[w];
+      if (w < warp) wbase += c;
+      tot += c;
+    }
+    if (i < hi) out[i] = carry + wbase + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+template <int W>
+bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *keys2,
+                uint32_t *vals2, int bits, uint32_t *hist, cudaStream_t s) {
+  int passes = (bits + 7) / 8;
+  bool alt = false;
+  for (int p = 0; p < passes; p++) {
+    KeyW<W> *ki = alt ? keys2 : keys, *ko = alt ? keys : keys2;
+    uint32_t *vi = alt ? vals2 : vals, *vo = alt ? vals : vals2;
+    k_hist<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
+    k_scan_single<<<1, 1024, 0, s>>>(hist, 256 * kPrimGrid, nullptr);
+    k_scatter<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
+    alt = !alt;
+  }
+  return alt;
+}
+
+template bool radix_sort<1>(const uint32_t *, KeyW<1> *, uint32_t *, KeyW<1> *, uint32_t *,
+                            int, uint32_t *, cudaStream_t);
+template bool radix_sort<2>(const uint32_t *, KeyW<2> *, uint32_t *, KeyW<2> *, uint32_t *,
+                            int, uint32_t *, cudaStream_t);
+template bool radix_sort<4>(const uint32_t *, KeyW<4> *, uint32_t *, KeyW<4> *, uint32_t *,
+                            int, uint32_t *, cudaStream_t);
+
+void exclusive_scan(const uint32_t *d_n, const uint32_t *in, uint32_t *out, uint32_t *d_total,
+                    uint32_t *partial, cudaStream_t s) {
+  k_scan_reduce<<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, in, partial);
+  k_scan_single<<<1, 1024, 0, s>>>(partial, kPrimGrid, d_total);
+  k_scan_down<<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, in, out, partial);
+}
+
+}  // namespace emrt

@@ -1,0 +1,69 @@
+// Host launchers of the discovery and acceptance kernels.
+#pragma once
+#include "common.cuh"
+#include "prims.cuh"
+
+namespace emrt {
+
+struct KeyLayout {  // bit widths of the canonical 128-bit path key
+  int bt, br, bf, K, total;
+};
+KeyLayout key_layout(uint32_t n_tx, uint32_t n_rx, uint32_t n_faces, int K);
+
+// Primary direction table for rays offset + stride*j, j < count: float4
+// (unit direction, j bits), ordered by an octahedral direction code so that
+// neighbouring threads shoot neighbouring directions.
+void build_dir_table(uint64_t n_rays, uint64_t offset, uint64_t stride, uint32_t count,
+                     float4 *table, KeyW<1> *k0, KeyW<1> *k1, uint32_t *v0, uint32_t *v1,
+                     uint32_t *d_n, uint32_t *hist, cudaStream_t s);
+
+struct BounceLaunch {
+  GeomView g;
+  const Ray *rin;        // bounce >= 1
+  const uint32_t *n_in;  // device count of rin (bounce >= 1)
+  uint32_t n_primary;    // n_tx * count (bounce 0)
+  const float4 *dirs;
+  uint32_t count;
+  Ray *rout;
+  uint32_t *n_out;
+  uint32_t *cand;
+  uint32_t cand_cap;
+  uint32_t *n_cand;
+  uint32_t *work;
+  Counters *ctr;
+  float kappa;
+  int b, K;
+};
+void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s);
+int bounce_grid();  // persistent grid size (SMs x resident blocks)
+
+// Canonical keys of min(*n, cap) records; values = record index.
+void launch_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,
+                      KeyW<4> *keys, uint32_t *vals, uint32_t *n_eff, cudaStream_t s);
+// head[i] = 1 where sorted key i starts a run.
+void launch_heads(const KeyW<4> *keys, const uint32_t *n, uint32_t *head, cudaStream_t s);
+// uniq[pos[i]] = merged record of the run starting at i (smallest ray index).
+void launch_unique(const uint32_t *rec, const KeyW<4> *keys, const uint32_t *vals,
+                   const uint32_t *head, const uint32_t *pos, const uint32_t *n, uint32_t *uniq,
+                   cudaStream_t s);
+// Image-method acceptance and occlusion of n records in place (w2 flags).
+void launch_accept(const GeomView &g, uint32_t *rec, const uint32_t *n, Counters *ctr,
+                   cudaStream_t s);
+// flag[i] = 1 if record i is kept (valid, or every record when keep_all).
+void launch_keep_flags(const uint32_t *rec, const uint32_t *n, int keep_all, uint32_t *flag,
+                       cudaStream_t s);
+// out[pos[i]] = in[i] for flagged i with pos < cap; raises ERR_PATH_OVERFLOW
+// when *total > cap.
+void launch_scatter(const uint32_t *in, const uint32_t *n, const uint32_t *flag,
+                    const uint32_t *pos, uint32_t *out, uint32_t cap, const uint32_t *total,
+                    Counters *ctr, cudaStream_t s);
+// out[0..min(*n,cap)) = in; *n_out = *n
+void launch_copy_records(const uint32_t *in, const uint32_t *n, uint32_t *out, uint32_t cap,
+                         cudaStream_t s);
+// concatenation of two record sets into dst (count written to *n_dst)
+void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const uint32_t *b,
+                   const uint32_t *nb, uint32_t cap_b, uint32_t *dst, uint32_t dst_cap,
+                   uint32_t *n_dst, Counters *ctr, cudaStream_t s);
+void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
+
+}  // namespace emrt

@@ -1,0 +1,276 @@
+// Stack traversal of the binary LBVH: closest hit and any hit over triangles
+// (watertight test) and vehicle boxes (slab test with entry face), and the
+// reception-sphere query over the receiver points.
+//
+// Node and primitive loads are 16-byte vector loads through the read-only
+// path (ld.global.nc).  The ray/triangle test is the watertight algorithm of
+// Woop, Benthin and Wald (JCGT 2013), restated from the publication: shear
+// the triangle into ray space, evaluate the three 2D edge functions without
+// FMA contraction (so both triangles sharing an edge see the same value) and
+// re-evaluate them in double precision when one of them is exactly zero.
+#pragma once
+#include "common.cuh"
+
+namespace emrt {
+
+constexpr int kStack = 64;
+// hard bound on loop iterations per query (a safety net: a well-formed tree
+// never comes close); exceeding it records a device error and stops
+constexpr uint32_t kMaxIter = 1u << 22;
+
+struct RayQ {
+  float3 o, d, idir, ood;
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ inline float sel3(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+__device__ inline float4 ldg4(const float4 *p) { return __ldg(p); }
+
+__device__ inline void ray_setup(RayQ &r, float3 o, float3 d) {
+  r.o = o;
+  r.d = d;
+  const float tiny = 1e-30f;
+  float3 dd = make_float3(fabsf(d.x) < tiny ? copysignf(tiny, d.x) : d.x,
+                          fabsf(d.y) < tiny ? copysignf(tiny, d.y) : d.y,
+                          fabsf(d.z) < tiny ? copysignf(tiny, d.z) : d.z);
+  r.idir = make_float3(1.f / dd.x, 1.f / dd.y, 1.f / dd.z);
+  r.ood = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+  float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  float dz = sel3(d, kz);
+  if (dz < 0.f) { int t = kx; kx = ky; ky = t; }
+  r.kx = kx; r.ky = ky; r.kz = kz;
+  r.Sx = sel3(d, kx) / dz;
+  r.Sy = sel3(d, ky) / dz;
+  r.Sz = 1.f / dz;
+}
+
+// slab test of one child box against [tmin, tmax]; conservative far bound
+__device__ inline bool slab(const RayQ &r, float lx, float hx, float ly, float hy, float lz, float hz,
+                            float tmin, float tmax, float &tnear) {
+  float t0x = fmaf(lx, r.idir.x, -r.ood.x), t1x = fmaf(hx, r.idir.x, -r.ood.x);
+  float t0y = fmaf(ly, r.idir.y, -r.ood.y), t1y = fmaf(hy, r.idir.y, -r.ood.y);
+  float t0z = fmaf(lz, r.idir.z, -r.ood.z), t1z = fmaf(hz, r.idir.z, -r.ood.z);
+  float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), tmin));
+  float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+  tnear = tn;
+  return tn <= tf * 1.00000024f;
+}
+
+// Watertight ray/triangle test; on a hit with tmin < t < tmax returns t.
+__device__ inline bool tri_hit(const RayQ &r, float3 v0, float3 v1, float3 v2, float tmin,
+                               float tmax, float &t) {
+  float3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
+  float Akz = sel3(A, r.kz), Bkz = sel3(B, r.kz), Ckz = sel3(C, r.kz);
+  float Ax = __fsub_rn(sel3(A, r.kx), __fmul_rn(r.Sx, Akz));
+  float Ay = __fsub_rn(sel3(A, r.ky), __fmul_rn(r.Sy, Akz));
+  float Bx = __fsub_rn(sel3(B, r.kx), __fmul_rn(r.Sx, Bkz));
+  float By = __fsub_rn(sel3(B, r.ky), __fmul_rn(r.Sy, Bkz));
+  float Cx = __fsub_rn(sel3(C, r.kx), __fmul_rn(r.Sx, Ckz));
+  float Cy = __fsub_rn(sel3(C, r.ky), __fmul_rn(r.Sy, Ckz));
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.f || V == 0.f || W == 0.f) {
+    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+  float det = U + V + W;
+  if (det == 0.f) return false;
+  float Az = r.Sz * Akz, Bz = r.Sz * Bkz, Cz = r.Sz * Ckz;
+  float T = U * Az + V * Bz + W * Cz;
+  float adet = fabsf(det);
+  float aT = det < 0.f ? -T : T;
+  if (aT <= tmin * adet || aT >= tmax * adet) return false;
+  t = T / det;
+  return t > tmin && t < tmax;
+}
+
+struct TravStats {
+  uint32_t nodes = 0, tris = 0;
+  bool overflow = false;
+};
+#define EMRT_ITER_GUARD(st)            \
+  if (++iter > kMaxIter) {             \
+    st.overflow = true;                \
+    return hit;                        \
+  }
+
+// Closest hit (ANY = false) or any hit (ANY = true) over the triangle BVH with
+// t in (tmin, tmax).  Triangles of faces ex0/ex1 are skipped.  On a hit
+// tmax and face are updated.  Ties in t go to the lower face ID.
+template <bool ANY>
+__device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, float &tmax,
+                                  uint32_t &face, uint32_t ex0, uint32_t ex1, int *stk, float *stt,
+                                  TravStats &st) {
+  if (b.n_prims == 0) return false;
+  bool hit = false;
+  int sp = 0;
+  int node = b.root;
+  uint32_t iter = 0;
+  for (;;) {
+    EMRT_ITER_GUARD(st)
+    if (node >= 0) {
+      const float4 *np = b.nodes + 4ll * node;
+      float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+      st.nodes++;
+      float tn0, tn1;
+      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
+      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        int nearc = c0, farc = c1;
+        float tfar = tn1;
+        if (tn1 < tn0) { nearc = c1; farc = c0; tfar = tn0; }
+        if (sp < kStack) { stk[sp] = farc; stt[sp] = tfar; sp++; }
+        else st.overflow = true;
+        node = nearc;
+        continue;
+      }
+      if (h0) { node = c0; continue; }
+      if (h1) { node = c1; continue; }
+    } else {
+      uint32_t g = (uint32_t)(~node);
+      const float4 *tp = b.prims + 3ull * g;
+      float4 a = ldg4(tp), bb = ldg4(tp + 1), c = ldg4(tp + 2);
+      st.tris++;
+      uint32_t f = __float_as_uint(a.w);
+      float t;
+      // closest hit: widen the bound slightly so that an exact tie can go to
+      // the lower face ID; any hit: strictly inside (tmin, tmax)
+      if (f != ex0 && f != ex1 &&
+          tri_hit(r, f3(a), f3(bb), f3(c), tmin, ANY ? tmax : tmax * 1.0000001f, t)) {
+        if (t < tmax || (!ANY && t == tmax && f < face)) {
+          tmax = t;
+          face = f;
+          hit = true;
+          if (ANY) return true;
+        }
+      }
+    }
+    // pop the next subtree that can still hold a closer hit
+    for (;;) {
+      if (sp == 0) return hit;
+      sp--;
+      if (stt[sp] <= tmax) break;
+    }
+    node = stk[sp];
+  }
+}
+
+// Vehicle boxes: closest (or any) entry hit with t in (tmin, tmax).  Box v is
+// skipped when exv0 or exv1 equals v.  face = F_s + 6 v + entry face.
+template <bool ANY>
+__device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, float &tmax,
+                                   uint32_t &face, uint32_t fs, uint32_t exv0, uint32_t exv1,
+                                   int *stk, float *stt, TravStats &st) {
+  if (b.n_prims == 0) return false;
+  bool hit = false;
+  int sp = 0;
+  int node = b.root;
+  uint32_t iter = 0;
+  for (;;) {
+    EMRT_ITER_GUARD(st)
+    if (node >= 0) {
+      const float4 *np = b.nodes + 4ll * node;
+      float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+      float tn0, tn1;
+      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
+      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        int nearc = c0, farc = c1;
+        float tfar = tn1;
+        if (tn1 < tn0) { nearc = c1; farc = c0; tfar = tn0; }
+        if (sp < kStack) { stk[sp] = farc; stt[sp] = tfar; sp++; }
+        else st.overflow = true;
+        node = nearc;
+        continue;
+      }
+      if (h0) { node = c0; continue; }
+      if (h1) { node = c1; continue; }
+    } else {
+      uint32_t g = (uint32_t)(~node);
+      float4 lo = ldg4(b.prims + 2ull * g), hi = ldg4(b.prims + 2ull * g + 1);
+      uint32_t v = __float_as_uint(lo.w);
+      if (v != exv0 && v != exv1) {
+        float tx0 = (lo.x - r.o.x) * r.idir.x, tx1 = (hi.x - r.o.x) * r.idir.x;
+        float ty0 = (lo.y - r.o.y) * r.idir.y, ty1 = (hi.y - r.o.y) * r.idir.y;
+        float tz0 = (lo.z - r.o.z) * r.idir.z, tz1 = (hi.z - r.o.z) * r.idir.z;
+        float nx = fminf(tx0, tx1), ny = fminf(ty0, ty1), nz = fminf(tz0, tz1);
+        float tn = fmaxf(nx, fmaxf(ny, nz));
+        float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+        if (tn <= tf && tn > tmin && tn < tmax) {
+          int axis = (tn == nx) ? 0 : ((tn == ny) ? 1 : 2);
+          float dax = axis == 0 ? r.d.x : (axis == 1 ? r.d.y : r.d.z);
+          tmax = tn;
+          face = fs + 6u * v + 2u * axis + (dax > 0.f ? 0u : 1u);
+          hit = true;
+          if (ANY) return true;
+        }
+      }
+    }
+    for (;;) {
+      if (sp == 0) return hit;
+      sp--;
+      if (stt[sp] <= tmax) break;
+    }
+    node = stk[sp];
+  }
+}
+
+// Reception spheres: for every receiver p with closest-approach parameter
+// s = d.(p - o) in (0, t_end] and distance to the ray <= kappa (L + s), calls
+// emit(receiver id).  rmax bounds kappa (L + t_end).
+template <typename F>
+__device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, float L, float kappa,
+                                float rmax, int *stk, float *stt, TravStats &st, F &&emit) {
+  if (b.n_prims == 0) return;
+  int sp = 0;
+  int node = b.root;
+  uint32_t iter = 0;
+  const bool hit = false;
+  for (;;) {
+    if (++iter > kMaxIter) {
+      st.overflow = true;
+      return;
+    }
+    (void)hit;
+    if (node >= 0) {
+      const float4 *np = b.nodes + 4ll * node;
+      float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+      float tn0, tn1;
+      bool h0 = slab(r, n0.x - rmax, n0.y + rmax, n0.z - rmax, n0.w + rmax, n2.x - rmax,
+                     n2.y + rmax, 0.f, t_end, tn0);
+      bool h1 = slab(r, n1.x - rmax, n1.y + rmax, n1.z - rmax, n1.w + rmax, n2.z - rmax,
+                     n2.w + rmax, 0.f, t_end, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        if (sp < kStack) { stk[sp] = c1; sp++; }
+        else st.overflow = true;
+        node = c0;
+        continue;
+      }
+      if (h0) { node = c0; continue; }
+      if (h1) { node = c1; continue; }
+    } else {
+      float4 p = ldg4(b.prims + (uint32_t)(~node));
+      float3 w = f3(p) - r.o;
+      float s = dot3(w, r.d);
+      if (s > 0.f && s <= t_end) {
+        float3 q = w - r.d * s;
+        float rad = kappa * (L + s);
+        if (dot3(q, q) <= rad * rad) emit(__float_as_uint(p.w));
+      }
+    }
+    if (sp == 0) return;
+    node = stk[--sp];
+  }
+}
+
+}  // namespace emrt

@@ -1,0 +1,214 @@
+"""Python front end of the emrt C-ABI: device memory and streams come from
+PyTorch; every computation runs in libemrt.so's CUDA kernels.
+
+    sc = Scene(scenes.city_scene())           # static LBVH built once
+    sc.update(sc_desc.frame(k))               # per frame: vehicles, Rx, Tx
+    paths = sc.trace()                         # plain discovery + acceptance
+    ch = sc.channel(paths, 3.5e9)              # per-path field, per-Rx stats
+    sc.revalidate(paths)                       # cached frame
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev(a, dtype, device) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        t = a.to(device=device, dtype=dtype)
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).to(device, non_blocking=False)
+    return t.contiguous()
+
+
+def _u32(a, device):
+    return _dev(np.asarray(a, np.uint32).view(np.int32), torch.int32, device)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+class Paths:
+    """Caller-owned path set on the device: ``rec`` int32 [capacity, 8]
+    (uint32 records, see include/emrt.h) and ``count`` int32 [1]."""
+
+    def __init__(self, capacity: int, device):
+        self.capacity = int(capacity)
+        self.rec = torch.empty((max(self.capacity, 1), N.PATH_WORDS), dtype=torch.int32,
+                               device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def c(self) -> N.PathsC:
+        return N.PathsC(self.rec.data_ptr(), self.capacity, self.count.data_ptr())
+
+    def n(self) -> int:
+        return int(self.count.item())
+
+    def records(self) -> np.ndarray:
+        """uint32 [n, 8] copy on the host (n clamped to the capacity)."""
+        n = min(self.n(), self.capacity)
+        return self.rec[:n].cpu().numpy().view(np.uint32)
+
+
+@dataclass
+class ChannelResult:
+    path: torch.Tensor   # [capacity, 4] float64: Re a, Im a, tau, f_D
+    pair: torch.Tensor   # [n_tx, n_rx, 8] float64
+    rx: torch.Tensor     # [n_rx, 2] float64 W: coherent, incoherent
+
+
+class Scene:
+    """A scene on one GPU: static geometry (with its LBVH), per-frame
+    dynamic state, scratch buffers.  Wraps ``emrt_scene``."""
+
+    def __init__(self, scene, device=None, max_rx: Optional[int] = None,
+                 max_tx: Optional[int] = None, rebuild_every: int = 10, stream=None):
+        self.lib = N.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.desc = scene
+        d = self.device
+        self._static = dict(
+            off=_u32(scene.face_off, d), xyz=_dev(scene.face_xyz, torch.float32, d),
+            mat=_u32(scene.face_mat, d), tri=_dev(scene.tri_xyz, torch.float32, d),
+            tface=_u32(scene.tri_face, d), half=_dev(scene.veh_half, torch.float32, d))
+        s = self._static
+        fr0 = scene.frame(0)
+        self.max_rx = int(max_rx or len(fr0.rx_pos))
+        self.max_tx = int(max_tx or len(fr0.tx_pos))
+        desc = N.SceneDesc(scene.n_static_faces, _ptr(s["off"]), _ptr(s["xyz"]), _ptr(s["mat"]),
+                           int(scene.tri_xyz.shape[0]), _ptr(s["tri"]), _ptr(s["tface"]),
+                           scene.n_vehicles, _ptr(s["half"]), int(scene.veh_mat),
+                           self.max_rx, self.max_tx, int(rebuild_every))
+        h = C.c_void_p()
+        torch.cuda.synchronize(d)
+        N.check(self.lib.emrt_scene_create(C.byref(desc), _stream(stream), C.byref(h)),
+                "emrt_scene_create")
+        self.h = h
+        self.n_rx = self.n_tx = 0
+        self.materials(scene.eps_r, scene.sigma, scene.gamma)
+        self._frame = None
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                torch.cuda.synchronize(self.device)
+            except Exception:
+                pass
+            self.lib.emrt_scene_destroy(h)
+            self.h = None
+
+    # ------------------------------------------------------------------
+    def materials(self, eps_r, sigma, gamma=None):
+        d = self.device
+        self.eps_r = _dev(eps_r, torch.float64, d)
+        self.sigma = _dev(sigma, torch.float64, d)
+        self.gamma = _dev(gamma if gamma is not None else np.zeros(len(eps_r)), torch.float64, d)
+
+    def _mat(self, const_gamma=False, eps_r=None, sigma=None):
+        e = self.eps_r if eps_r is None else eps_r
+        s = self.sigma if sigma is None else sigma
+        return N.Materials(int(e.numel()), _ptr(e), _ptr(s), _ptr(self.gamma), int(const_gamma))
+
+    def update(self, frame, stream=None):
+        """Per-frame dynamic state from a scenes.Frame (numpy or torch)."""
+        d = self.device
+        t = {k: _dev(getattr(frame, k), torch.float32, d)
+             for k in ("veh_pos", "veh_vel", "rx_pos", "rx_vel", "tx_pos", "tx_vel")}
+        self._frame = t
+        self.n_rx, self.n_tx = int(t["rx_pos"].shape[0]), int(t["tx_pos"].shape[0])
+        N.check(self.lib.emrt_scene_update_dynamic(
+            self.h, _ptr(t["veh_pos"]), _ptr(t["veh_vel"]), _ptr(t["rx_pos"]), _ptr(t["rx_vel"]),
+            self.n_rx, _ptr(t["tx_pos"]), _ptr(t["tx_vel"]), self.n_tx, _stream(stream)),
+            "emrt_scene_update_dynamic")
+
+    def trace_async(self, out: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
+                    keep_rejected=False, sort_rays=False, stream=None):
+        p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
+                          int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
+                          int(stride), int(count),
+                          (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
+                          (N.TRACE_SORT_RAYS if sort_rays else 0))
+        pc = out.c()
+        N.check(self.lib.emrt_trace(self.h, C.byref(p), C.byref(pc), _stream(stream)),
+                "emrt_trace")
+
+    def trace(self, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
+              keep_rejected=False, capacity=None, stream=None, retries=3) -> Paths:
+        """Plain discovery; grows scratch and output on capacity errors."""
+        cap = capacity or max(4096, 8 * self.n_tx * self.n_rx)
+        for _ in range(retries + 1):
+            out = Paths(cap, self.device)
+            self.trace_async(out, n_rays, max_depth, offset, stride, count, keep_rejected,
+                             stream=stream)
+            try:
+                self.last_stats = self.sync(stream)
+                return out
+            except N.EmrtError as e:
+                if e.code != 4:
+                    raise
+                cap = max(cap, int(out.n()) + 1024)
+        raise N.EmrtError(4, "emrt_trace (after retries)")
+
+    def revalidate(self, cache: Paths, keep=False, stream=None):
+        pc = cache.c()
+        N.check(self.lib.emrt_revalidate(self.h, C.byref(pc),
+                                         N.REVALIDATE_KEEP if keep else 0, _stream(stream)),
+                "emrt_revalidate")
+
+    def merge(self, cache: Paths, fresh: Paths, stream=None):
+        a, b = cache.c(), fresh.c()
+        N.check(self.lib.emrt_cache_merge(self.h, C.byref(a), C.byref(b), _stream(stream)),
+                "emrt_cache_merge")
+
+    def channel(self, paths: Paths, freq: float, tx_power_w: Optional[float] = None,
+                const_gamma=False, eps_r=None, sigma=None, out: Optional[ChannelResult] = None,
+                stream=None) -> ChannelResult:
+        d = self.device
+        if out is None:
+            out = ChannelResult(
+                torch.empty((max(paths.capacity, 1), 4), dtype=torch.float64, device=d),
+                torch.empty((self.n_tx, self.n_rx, 8), dtype=torch.float64, device=d),
+                torch.empty((self.n_rx, 2), dtype=torch.float64, device=d))
+        m = self._mat(const_gamma, eps_r, sigma)
+        co = N.ChannelOut(out.path.data_ptr(), out.pair.data_ptr(), out.rx.data_ptr())
+        pc = paths.c()
+        pt = self.desc.tx_power_w if tx_power_w is None else tx_power_w
+        N.check(self.lib.emrt_channel(self.h, C.byref(pc), C.byref(m), float(freq), float(pt),
+                                      C.byref(co), _stream(stream)), "emrt_channel")
+        return out
+
+    def channel_backward(self, paths: Paths, freq: float, dloss_dh: torch.Tensor,
+                         const_gamma=False, eps_r=None, sigma=None, stream=None):
+        d = self.device
+        m = self._mat(const_gamma, eps_r, sigma)
+        ge = torch.empty(int(m.n_mat), dtype=torch.float64, device=d)
+        gs = torch.empty_like(ge)
+        gt = torch.empty((self.n_tx, 3), dtype=torch.float64, device=d)
+        g = dloss_dh.to(device=d, dtype=torch.float64).contiguous()
+        pc = paths.c()
+        N.check(self.lib.emrt_channel_backward(self.h, C.byref(pc), C.byref(m), float(freq),
+                                               _ptr(g), _ptr(ge), _ptr(gs), _ptr(gt),
+                                               _stream(stream)), "emrt_channel_backward")
+        return ge, gs, gt
+
+    def sync(self, stream=None) -> dict:
+        st = N.Stats()
+        code = self.lib.emrt_sync(self.h, _stream(stream), C.byref(st))
+        out = {f: getattr(st, f) for f, _ in N.Stats._fields_}
+        out["segments"] = list(st.segments)
+        self.last_stats = out
+        N.check(code, "emrt_sync")
+        return out

@@ -195,7 +195,7 @@ def _hull_ccw(pts):
     return lower[:-1] + upper[:-1]
 
 
-def _random_footprint(rng, cx, cy, half, n_lo=10, n_hi=16):
+def _random_footprint(rng, cx, cy, half, n_lo=12, n_hi=17):
     """Random convex polygon (about n vertices) inside the square
     [cx-half, cx+half] x [cy-half, cy+half]; float32 vertices, CCW."""
     for _ in range(100):
@@ -203,7 +203,7 @@ def _random_footprint(rng, cx, cy, half, n_lo=10, n_hi=16):
         ang = np.sort(rng.uniform(0, 2 * np.pi, n))
         a, b = rng.uniform(0.65, 1.0, 2) * half
         rot = rng.uniform(0, np.pi)
-        r = rng.uniform(0.9, 1.0, n)
+        r = rng.uniform(0.97, 1.0, n)
         x = a * r * np.cos(ang)
         y = b * r * np.sin(ang)
         xr = x * np.cos(rot) - y * np.sin(rot)

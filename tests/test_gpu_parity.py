@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle on the
+same seeded inputs (element by element), plus closed forms."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import (compare_acceptance, compare_candidates, compare_field, rec_to_paths,
+                     C_LIGHT)
+from paper_2303_10521_gb300 import scenes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def engine():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_10521_gb300 import engine as E
+    return E
+
+
+def _gpu(E, sc, frame=None, **kw):
+    g = E.Scene(sc, **kw)
+    g.update(frame if frame is not None else sc.frame(0))
+    return g
+
+
+def _field(g, paths, freq, **kw):
+    ch = g.channel(paths, freq, **kw)
+    n = paths.n()
+    po = ch.path[:n].cpu().numpy()
+    return po[:, 0] + 1j * po[:, 1], po[:, 2], po[:, 3], ch
+
+
+# ---------------------------------------------------------------------------
+def test_friis_two_ray_single_wall_closed_forms(engine):
+    f = 3.5e9
+    k = 2 * math.pi * f / C_LIGHT
+    lam = C_LIGHT / f
+    # free space
+    sc = S.custom_scene([], [], (0, 0, 10), (250.0, 40.0, 1.5), freq=f)
+    g = _gpu(engine, sc)
+    p = g.trace(n_rays=200_000, max_depth=2)
+    recs = rec_to_paths(p.records())
+    assert len(recs) == 1 and recs["depth"][0] == 0
+    a, tau, fd, _ = _field(g, p, f)
+    d = float(np.linalg.norm(np.float32([250.0, 40.0, 1.5]).astype(float) - [0, 0, 10]))
+    expect = lam / (4 * math.pi * d) * np.exp(-1j * k * d)
+    assert abs(a[0] - expect) <= 1e-9 * abs(expect)
+    # two-ray ground
+    ground = S.rect_xy(-2e3, -2e3, 2e3, 2e3)
+    sc = S.custom_scene([ground], [S.MAT_GROUND], (0, 0, 30), (300.0, 0.0, 1.5), freq=f)
+    g = _gpu(engine, sc)
+    p = g.trace(n_rays=400_000, max_depth=2)
+    recs = rec_to_paths(p.records())
+    assert sorted(recs["depth"].tolist()) == [0, 1]
+    a, tau, fd, ch = _field(g, p, f)
+    o = oracle.OracleScene(sc, sc.frame(0))
+    a_o, tau_o, fd_o = oracle.field(o, recs, f)
+    r = compare_field(a, tau, fd, a_o, tau_o, fd_o)
+    assert r["ok"], r
+    h = ch.pair[0, 0].cpu().numpy()
+    assert complex(h[0], h[1]) == pytest.approx(complex(a_o.sum()), rel=1e-9)
+    # single wall, s polarised
+    wall = S.rect_wall_x(20.0, -100, 100, -50, 50, facing=-1)
+    sc = S.custom_scene([wall], [S.MAT_CONCRETE], (0, 0, 5), (3.0, 40.0, 5.0), freq=28e9)
+    g = _gpu(engine, sc)
+    p = g.trace(n_rays=400_000, max_depth=1)
+    recs = rec_to_paths(p.records())
+    assert sorted(recs["depth"].tolist()) == [0, 1]
+    a, tau, fd, _ = _field(g, p, 28e9)
+    o = oracle.OracleScene(sc, sc.frame(0))
+    r = compare_field(a, tau, fd, *oracle.field(o, recs, 28e9))
+    assert r["ok"], r
+
+
+def test_toy_scene_full_parity(engine):
+    """Static toy scene, 100k rays, 2 reflections: discovery, acceptance,
+    field and per-receiver reduction against the oracle."""
+    sc = S.toy_scene(seed=0)
+    fr = sc.frame(0)
+    g = _gpu(engine, sc)
+    o = oracle.OracleScene(sc, fr)
+    allc = g.trace(keep_rejected=True)
+    gu = rec_to_paths(allc.records())
+    cands, ray_marg, _ = oracle.trace(o, sc.n_rays, sc.max_depth)
+    rc = compare_candidates(gu, cands, ray_marg)
+    assert not rc["missing"] and not rc["extra_bad"], rc
+    ra = compare_acceptance(o, gu)
+    assert ra["n_diff_unflagged"] == 0, ra
+    acc = g.trace()
+    ga = rec_to_paths(acc.records())
+    assert len(ga) == ra["n_acc_gpu"]
+    # canonical order
+    k = oracle.key_fields(ga)
+    assert all(tuple(k[i]) < tuple(k[i + 1]) for i in range(len(k) - 1))
+    a, tau, fd, ch = _field(g, acc, sc.freqs[0])
+    a_o, tau_o, fd_o = oracle.field(o, ga, sc.freqs[0])
+    rf = compare_field(a, tau, fd, a_o, tau_o, fd_o)
+    assert rf["ok"], rf
+    st = oracle.reduce(ga, a_o, tau_o, fd_o, 1, len(fr.rx_pos))
+    pair = ch.pair.cpu().numpy()
+    h_g = pair[..., 0] + 1j * pair[..., 1]
+    h_o = st[..., 0] + 1j * st[..., 1]
+    # per pair, the coherent sum may differ by the per-path tolerance summed
+    sum_abs = np.zeros(h_o.shape)
+    np.add.at(sum_abs, (ga["tx"].astype(int), ga["rx"].astype(int)), np.abs(a_o))
+    assert np.all(np.abs(h_g - h_o) <= 1e-4 * sum_abs + 1e-30)
+    assert pair[..., 7] == pytest.approx(st[..., 7])
+    assert pair[..., 2] == pytest.approx(st[..., 2], rel=1e-6)
+    assert pair[..., 3] == pytest.approx(st[..., 3], abs=1e-6)
+    assert pair[..., 5] == pytest.approx(st[..., 5], rel=1e-9, abs=1e-15)
+    coh, inc = oracle.rx_power(st, sc.tx_power_w)
+    rx = ch.rx.cpu().numpy()
+    assert rx[:, 0] == pytest.approx(coh, rel=1e-6)
+    assert rx[:, 1] == pytest.approx(inc, rel=1e-6)
+
+
+@pytest.mark.parametrize("stride,offset", [(97, 5), (211, 0)])
+def test_district_subsample_parity(engine, stride, offset):
+    """District (400 buildings, 200 vehicles, 1000 Rx, 2 Tx, K = 3) on a
+    strided subset of the 1M rays, traced identically on both sides."""
+    sc = S.district_scene(seed=0)
+    fr = sc.frame(0)
+    g = _gpu(engine, sc)
+    o = oracle.OracleScene(sc, fr)
+    allc = g.trace(stride=stride, offset=offset, keep_rejected=True)
+    gu = rec_to_paths(allc.records())
+    cands, ray_marg, _ = oracle.trace(o, sc.n_rays, sc.max_depth, offset=offset, stride=stride)
+    rc = compare_candidates(gu, cands, ray_marg)
+    assert not rc["missing"] and not rc["extra_bad"], {k: v for k, v in rc.items() if k != "bad"}
+    ra = compare_acceptance(o, gu)
+    assert ra["n_diff_unflagged"] == 0, ra
+    acc = g.trace(stride=stride, offset=offset)
+    ga = rec_to_paths(acc.records())
+    a, tau, fd, _ = _field(g, acc, 3.5e9)
+    rf = compare_field(a, tau, fd, *oracle.field(o, ga, 3.5e9))
+    assert rf["ok"], rf
+
+
+def test_revalidation_and_merge(engine):
+    """Cached frame: paths discovered at frame 0 revalidated with the poses of
+    frame 3, flag by flag against the oracle; merge is a sorted union."""
+    sc = S.district_scene(seed=1)
+    g = _gpu(engine, sc)
+    p0 = g.trace(stride=53)
+    n0 = p0.n()
+    assert n0 > 100
+    fr3 = sc.frame(3)
+    g.update(fr3)
+    g.revalidate(p0, keep=True)
+    recs = rec_to_paths(p0.records())
+    assert len(recs) == n0
+    o3 = oracle.OracleScene(sc, fr3)
+    ra = compare_acceptance(o3, recs)
+    assert ra["n_diff_unflagged"] == 0, ra
+    g.revalidate(p0)
+    kept = rec_to_paths(p0.records())
+    assert len(kept) == int((recs["flag"] & 1).sum())
+    assert oracle.key_fields(kept).tolist() == oracle.key_fields(recs[(recs["flag"] & 1) == 1]).tolist()
+    fresh = g.trace(stride=53, offset=7)
+    fk = rec_to_paths(fresh.records())
+    cache = engine.Paths(len(kept) + len(fk) + 16, g.device)
+    cache.rec[:len(kept)] = p0.rec[:len(kept)]
+    cache.count.fill_(len(kept))
+    g.merge(cache, fresh)
+    merged = rec_to_paths(cache.records())
+    want = sorted(set(map(tuple, oracle.key_fields(kept))) | set(map(tuple, oracle.key_fields(fk))))
+    assert [tuple(r) for r in oracle.key_fields(merged)] == want
+
+
+def test_dynamic_frames_vehicle_paths(engine):
+    """Several frames of the district: vehicle faces appear in paths, the
+    vehicle BVH is refitted and rebuilt, and Doppler matches the oracle."""
+    sc = S.district_scene(seed=2)
+    g = engine.Scene(sc, rebuild_every=3)
+    seen_vehicle = False
+    for k in (0, 1, 2, 3, 4):
+        fr = sc.frame(k)
+        g.update(fr)
+        p = g.trace(stride=101, offset=k)
+        ga = rec_to_paths(p.records())
+        o = oracle.OracleScene(sc, fr)
+        ra = compare_acceptance(o, ga)
+        assert ra["n_diff_unflagged"] == 0, ra
+        a, tau, fd, _ = _field(g, p, 3.5e9)
+        rf = compare_field(a, tau, fd, *oracle.field(o, ga, 3.5e9))
+        assert rf["ok"], rf
+        f = ga["face"]
+        seen_vehicle |= bool(((f >= sc.n_static_faces) & (f != oracle.NO_FACE)).any())
+    assert seen_vehicle
+
+
+def test_constant_gamma_mode(engine):
+    sc = S.toy_scene(seed=3)
+    g = _gpu(engine, sc)
+    p = g.trace(n_rays=50_000)
+    ga = rec_to_paths(p.records())
+    a, tau, fd, _ = _field(g, p, 3.5e9, const_gamma=True)
+    o = oracle.OracleScene(sc, sc.frame(0), const_gamma=True)
+    rf = compare_field(a, tau, fd, *oracle.field(o, ga, 3.5e9))
+    assert rf["ok"], rf
+
+
+def test_edge_cases(engine):
+    E = engine
+    # K = 0 (line of sight only), single receiver, ragged ray count
+    sc = S.toy_scene(seed=0)
+    fr = sc.frame(0)
+    fr1 = dataclasses.replace(fr, rx_pos=fr.rx_pos[:1], rx_vel=fr.rx_vel[:1])
+    g = _gpu(E, sc, fr1)
+    p = g.trace(n_rays=12_345, max_depth=0, count=1001)
+    ga = rec_to_paths(p.records())
+    assert (ga["depth"] == 0).all() and len(ga) <= 1
+    o = oracle.OracleScene(sc, fr1)
+    assert len(ga) == len(oracle.enumerate_paths(o, 0))
+    # no static faces at all
+    sc2 = S.custom_scene([], [], (0, 0, 5), [(10, 0, 5), (0, 30, 1)])
+    g2 = _gpu(E, sc2)
+    p2 = g2.trace(n_rays=10_000, max_depth=4)
+    assert p2.n() == 2
+    # capacity error surfaces through emrt_sync with the required count
+    g3 = _gpu(E, sc)
+    small = E.Paths(2, g3.device)
+    g3.trace_async(small, n_rays=100_000, max_depth=2)
+    with pytest.raises(E.N.EmrtError) as ei:
+        g3.sync()
+    assert ei.value.code == 4
+    assert small.n() > 2
+
+
+def test_invalid_arguments(engine):
+    E = engine
+    sc = S.toy_scene(seed=0)
+    g = E.Scene(sc)
+    out = E.Paths(16, g.device)
+    with pytest.raises(E.N.EmrtError) as ei:   # trace before any update
+        g.trace_async(out)
+    assert ei.value.code == 6
+    g.update(sc.frame(0))
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.trace_async(out, max_depth=5)
+    assert ei.value.code == 1
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.trace_async(out, stride=0)
+    assert ei.value.code == 1
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.trace_async(out, n_rays=100, offset=100)
+    assert ei.value.code == 1

@@ -439,3 +439,20 @@ def test_fermat_gradient_of_path_length():
         q1 = pts[i, 0]
         k0 = (q1 - fr.tx_pos[0].astype(float)) / np.linalg.norm(q1 - fr.tx_pos[0].astype(float))
         assert g == pytest.approx(-k0[0], abs=1e-6)
+
+
+def test_table1_constant_mode_two_ray_sum():
+    """Constant-coefficient mode with a vertically polarised ground bounce:
+    the bounce enters the coherent sum with +gamma (a scaled perfect
+    conductor keeps the p component's sign)."""
+    g = {r[0]: float(r[1]) for r in _read_golden("table1_constant_gamma.txt")}
+    f = 3.5e9
+    D, ht, hr = 40.0, 12.0, 1.5
+    ground = S.rect_xy(-1e3, -1e3, 1e3, 1e3, 0.0)
+    sc, o = _one((0, 0, ht), (D, 0, hr), [ground], [S.MAT_GROUND], const_gamma=True, freq=f)
+    paths = oracle.enumerate_paths(o, 1)
+    a, _, _ = oracle.field(o, paths, f)
+    d1, d2 = math.hypot(D, ht - hr), math.hypot(D, ht + hr)
+    k = 2 * math.pi * f / C
+    h = _lam(f) / (4 * math.pi) * (np.exp(-1j * k * d1) / d1 + g["wall"] * np.exp(-1j * k * d2) / d2)
+    assert abs(a.sum() - h) <= 1e-10 * abs(h)
