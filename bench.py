@@ -1,0 +1,410 @@
+"""Benchmark: receiver-frames/s of the per-frame pipeline on the 2x2 km city
+(6400 buildings, 5000 moving vehicles, 10k receivers, 4 transmitters,
+1e7 rays per transmitter, 4 reflections, fields at 3.5 and 28 GHz), plain
+per-frame retrace and path cache, with Mrays/s of the closest-hit traversal.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one frame of the whole hot path: dynamic update (vehicle boxes,
+vehicle BVH refit, receiver BVH), shoot-and-bounce discovery with reception
+spheres, deduplication, image-method acceptance with occlusion rays, field
+and per-receiver reduction at both frequencies.  Inputs of every frame are
+resident in HBM before the timed region; ray buffers (3.8 GB per bounce) are
+larger than L2.  N > 1 (torchrun) runs one independent replica per GPU on
+different frames (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s traversal and receiver-frames/s channel update (2x2km,10k Rx), cached vs plain"
+UNIT = "receiver-frames/s"
+REFRESH = 10          # cached method: rediscovery every REFRESH frames
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bounce_city_traffic.txt")
+KERNEL_SOURCES = ["paper_2303_10521_gb300/csrc/trace.cu",
+                  "paper_2303_10521_gb300/csrc/traverse.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cached-frames", type=int, default=30)
+    ap.add_argument("--ray-stride", type=int, default=1,
+                    help="trace rays offset + stride*j only (profiling captures)")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed plain frames only (no e2e, cache or CPU legs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_per_segment():
+    """DRAM bytes per closest-hit segment of k_bounce from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_hash") != kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_segment"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"emrt_clocks_{os.getpid()}.csv")
+        try:
+            sel = []
+            bus = getattr(__import__("torch").cuda.get_device_properties(dev_index), "pci_bus_id", None)
+            if bus is not None:
+                dom = getattr(__import__("torch").cuda.get_device_properties(dev_index), "pci_domain_id", 0)
+                dv = getattr(__import__("torch").cuda.get_device_properties(dev_index), "pci_device_id", 0)
+                sel = ["-i", f"{dom:08x}:{bus:02x}:{dv:02x}.0"]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"] + sel,
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        rows = [r for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" == v.strip()})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def run_cpu_baseline(sc, fr, stride, budget_s=25.0):
+    """The oracle as it stands on a strided ray sample of the same frame:
+    discovery, deduplication, acceptance, field at both frequencies and the
+    reduction; time scaled by the stride to one full frame."""
+    import oracle
+    t0 = time.time()
+    o = oracle.OracleScene(sc, fr)
+    cands, _, segs = oracle.trace(o, sc.n_rays, sc.max_depth, offset=0, stride=stride)
+    u = oracle.dedup(cands)
+    acc, _ = oracle.validate(o, u)
+    paths = u[acc]
+    for f in sc.freqs:
+        a, tau, fd = oracle.field(o, paths, f)
+        oracle.reduce(paths, a, tau, fd, len(fr.tx_pos), len(fr.rx_pos))
+    dt = time.time() - t0
+    frame_s = dt * stride
+    return {"value": len(fr.rx_pos) / frame_s, "unit": UNIT, "cores": oracle.n_threads(),
+            "kind": "oracle",
+            "sample": f"city frame 0, rays offset 0 + {stride}*j (1/{stride} of 4 x 1e7), "
+                      f"{int(segs.sum())} segments, full pipeline on them in {dt:.1f} s, "
+                      f"scaled by {stride} to one frame",
+            "mrays_per_s": float(segs.sum()) / dt / 1e6}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2303_10521_gb300 import scenes
+    sc = scenes.city_scene(seed=0)
+    stride = 20000
+    vals = []
+    t_all = time.time()
+    for k in range(args.warmup + args.steps):
+        r = run_cpu_baseline(sc, sc.frame(k), stride)
+        if k >= args.warmup:
+            vals.append(r)
+    wall = time.time() - t_all
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 1e4 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "city 2x2 km, 6400 buildings, 5000 vehicles, 10k Rx, 4 Tx, "
+                                   "1e7 rays/Tx, K=4, 3.5+28 GHz", "sample_stride": stride},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_2303_10521_gb300 import engine, scenes
+    from paper_2303_10521_gb300 import _native
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = _native.load()
+
+    sc = scenes.city_scene(seed=0)
+    n_rx = len(sc.frame(0).rx_pos)
+    stream = torch.cuda.current_stream()
+    base = rank * 1000  # each replica traces its own frames
+    total = args.warmup + args.steps
+
+    def frame_dev(k):
+        fr = sc.frame(base + k)
+        return {f: torch.as_tensor(getattr(fr, f)).to(dev)
+                for f in ("veh_pos", "veh_vel", "rx_pos", "rx_vel", "tx_pos", "tx_vel")}
+
+    class F:  # device-resident frame for engine.Scene.update
+        def __init__(self, d):
+            self.__dict__.update(d)
+
+    frames = [F(frame_dev(k)) for k in range(total + 1)]
+    g = engine.Scene(sc, device=dev)
+    g.update(frames[0])
+    rs = args.ray_stride
+    paths = g.trace(stride=rs)                     # sizes scratch buffers
+    cap = paths.capacity
+    out = engine.Paths(cap * 2, dev)
+    chs = [None, None]
+
+    def step(k, stats):
+        g.update(frames[k])
+        g.trace_async(out, stride=rs)
+        for i, f in enumerate(sc.freqs):
+            chs[i] = g.channel(out, f, out=chs[i])
+        st = g.sync()
+        stats.append(st)
+
+    warm = []
+    for k in range(args.warmup):
+        step(k, warm)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    l0 = lib.emrt_kernel_launches()
+    stats = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.warmup, total):
+        step(k, stats)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.emrt_kernel_launches() - l0
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        t_ms = float(t.item())
+    value = n_rx * args.steps * ws / (t_ms / 1e3)
+
+    # traversal kernel: algorithmic bytes per launch / launch time
+    K = sc.max_depth
+    seg = sum(sum(s["segments"]) for s in stats)
+    trav_ms = sum(s["traverse_ms"] for s in stats)
+    byt = 0
+    for s in stats:
+        sg = s["segments"]
+        byt += 64 * (s["node_visits"] + s["dyn_node_visits"] + s["rx_node_visits"])
+        byt += 48 * s["tri_tests"] + 32 * s["box_tests"] + 16 * s["rx_tests"]
+        byt += 16 * sg[0] + 48 * sum(sg[1:])          # ray reads
+        byt += 48 * sum(sg[1:])                        # reflected rays written
+        byt += 32 * s["candidates"]
+    launches_trav = (K + 1) * len(stats)
+    peak, peak_kind = measured_peaks()
+    achieved = (byt / launches_trav) / (trav_ms / launches_trav / 1e3) / 1e9
+    tps = traffic_per_segment()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": (tps * seg / launches_trav) if tps else None,
+                "kernel": "k_bounce (closest-hit traversal + reception spheres)",
+                "algorithmic_bytes_per_launch": byt / launches_trav,
+                "launch_ms": trav_ms / launches_trav}
+    mrays = seg / (trav_ms / 1e3) / 1e6
+
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "ms_per_step": t_ms / args.steps,
+                              "mrays_per_s": mrays, "roofline": roofline}), flush=True)
+        return
+
+    # ---------------- end to end through the public API, host buffers
+    pinned = []
+    for k in range(args.warmup, total):
+        fr = sc.frame(base + k)
+        pinned.append({f: torch.as_tensor(getattr(fr, f)).pin_memory()
+                       for f in ("veh_pos", "veh_vel", "rx_pos", "rx_vel", "tx_pos", "tx_vel")})
+    rx_host = [torch.empty((n_rx, 2), dtype=torch.float64).pin_memory() for _ in sc.freqs]
+    h2d = sum(t.numel() * t.element_size() for t in pinned[0].values())
+    d2h = sum(t.numel() * t.element_size() for t in rx_host) + 4
+    cnt_host = torch.empty(1, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for k in range(args.steps):
+        d = F({f: t.to(dev, non_blocking=True) for f, t in pinned[k].items()})
+        g.update(d)
+        g.trace_async(out)
+        for i, f in enumerate(sc.freqs):
+            chs[i] = g.channel(out, f, out=chs[i])
+            rx_host[i].copy_(chs[i].rx, non_blocking=True)
+        cnt_host.copy_(out.count, non_blocking=True)
+        g.sync()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": n_rx * args.steps * ws / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---------------- cached frames (path cache revalidated every frame,
+    # rediscovery every REFRESH frames) and its accuracy against plain retrace
+    nc = args.cached_frames
+    cframes = [F(frame_dev(total + 1 + k)) for k in range(nc)]
+    cache = engine.Paths(cap * 4, dev)
+    fresh = engine.Paths(cap * 2, dev)
+    g.update(cframes[0])
+    g.trace_async(cache)
+    g.sync()
+    torch.cuda.synchronize()
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for k in range(1, nc):
+        g.update(cframes[k])
+        g.revalidate(cache)
+        if k % REFRESH == 0:
+            g.trace_async(fresh)
+            g.merge(cache, fresh)
+        for i, f in enumerate(sc.freqs):
+            chs[i] = g.channel(cache, f, out=chs[i])
+        g.sync()
+    e5.record(stream)
+    torch.cuda.synchronize()
+    cached_ms = e4.elapsed_time(e5)
+    cached_val = n_rx * (nc - 1) * ws / (cached_ms / 1e3)
+    p_cached = chs[0].rx[:, 0].double().cpu().numpy().copy()
+    g.trace_async(fresh)
+    chp = g.channel(fresh, sc.freqs[0])
+    g.sync()
+    p_plain = chp.rx[:, 0].double().cpu().numpy()
+    m = p_plain > 0
+    db = 10 * np.log10(np.maximum(p_cached[m], 1e-300) / p_plain[m])
+    accuracy = {"frames": nc, "refresh_every": REFRESH,
+                "rx_power_recall": float(np.minimum(p_cached[m], p_plain[m]).sum() / p_plain[m].sum()),
+                "p95_abs_delta_db": float(np.percentile(np.abs(db), 95)) if m.any() else None,
+                "median_abs_delta_db": float(np.median(np.abs(db))) if m.any() else None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(sc, sc.frame(base + args.warmup), stride=2000)
+
+    if rank == 0:
+        last = stats[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "precision": "FP32 traversal and intersection; FP64 image points, path length, "
+                         "phase, Fresnel field and reductions",
+            "data": "synthetic",
+            "config": {"workload": "city 2x2 km, 6400 buildings (~293k triangles), 5000 vehicles, "
+                                   "10k Rx, 4 Tx, 1e7 rays/Tx, K=4, fields at 3.5 and 28 GHz",
+                       "method": "plain per-frame retrace", "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (3.8 GB ray buffers per bounce)"},
+            "mrays_per_s": mrays,
+            "receiver_frames_per_s_cached": cached_val,
+            "cached": accuracy,
+            "segments_per_frame": seg / len(stats),
+            "paths_per_frame": last["accepted"],
+            "candidates_per_frame": last["candidates"],
+            "stage_ms": {"traverse": trav_ms / len(stats),
+                         "dedup": sum(s["dedup_ms"] for s in stats) / len(stats),
+                         "accept": sum(s["accept_ms"] for s in stats) / len(stats)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -191,11 +191,19 @@ typedef struct {
   uint64_t unique_candidates; /* after deduplication                         */
   uint64_t accepted;          /* paths written                                */
   uint64_t occlusion_rays;    /* any-hit segments traced by acceptance        */
-  uint64_t node_visits;       /* BVH nodes visited by closest-hit traversal  */
-  uint64_t tri_tests;         /* triangles tested by closest-hit traversal   */
+  uint64_t node_visits;       /* static BVH inner nodes visited (closest hit) */
+  uint64_t tri_tests;         /* triangles tested (closest hit)               */
+  uint64_t dyn_node_visits;   /* vehicle BVH inner nodes visited              */
+  uint64_t box_tests;         /* vehicle boxes tested                         */
+  uint64_t rx_node_visits;    /* receiver BVH inner nodes visited             */
+  uint64_t rx_tests;          /* receivers tested against a reception sphere  */
   uint32_t error_bits;        /* device error word                            */
   uint32_t required_candidates; /* scratch sizes needed by the last trace   */
   uint32_t required_paths;
+  uint32_t pad;
+  /* device time of the last emrt_trace (CUDA events on its stream), ms:
+   * closest-hit traversal kernels, deduplication, image-method acceptance */
+  float traverse_ms, dedup_ms, accept_ms, trace_ms;
 } emrt_stats;
 
 /* Waits for the stream, reads and clears the device error word, returns the
@@ -203,6 +211,10 @@ typedef struct {
 emrt_status emrt_sync(emrt_scene sc, emrt_stream s, emrt_stats *st);
 
 const char *emrt_status_string(emrt_status e);
+
+/* Number of kernel launches this library has issued in this process
+ * (diagnostics; host-side counter). */
+uint64_t emrt_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -51,8 +51,11 @@ class ChannelOut(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("segments", u64 * (MAX_DEPTH + 1)), ("candidates", u64),
                 ("unique_candidates", u64), ("accepted", u64), ("occlusion_rays", u64),
-                ("node_visits", u64), ("tri_tests", u64), ("error_bits", u32),
-                ("required_candidates", u32), ("required_paths", u32)]
+                ("node_visits", u64), ("tri_tests", u64), ("dyn_node_visits", u64),
+                ("box_tests", u64), ("rx_node_visits", u64), ("rx_tests", u64),
+                ("error_bits", u32), ("required_candidates", u32), ("required_paths", u32),
+                ("pad", u32), ("traverse_ms", C.c_float), ("dedup_ms", C.c_float),
+                ("accept_ms", C.c_float), ("trace_ms", C.c_float)]
 
 
 STATUS = {0: "EMRT_OK", 1: "EMRT_ERR_INVALID_ARG", 2: "EMRT_ERR_OOM", 3: "EMRT_ERR_CUDA",
@@ -73,6 +76,7 @@ SIGNATURES = {
                                         vp, vp, vp, vp]),
     "emrt_sync": (C.c_int, [vp, vp, C.POINTER(Stats)]),
     "emrt_status_string": (C.c_char_p, [C.c_int]),
+    "emrt_kernel_launches": (u64, []),
 }
 
 _lib = None

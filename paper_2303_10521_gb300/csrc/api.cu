@@ -1,6 +1,7 @@
 // C-ABI of libemrt.so: scene lifetime, argument checks, scratch management
 // and the order of kernel launches for each entry point.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -45,7 +46,15 @@ struct emrt_scene_s {
   double *contrib = nullptr;
   uint64_t contrib_cap = 0;
   emrt_status sticky = EMRT_OK;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool ev_recorded = false;
 };
+
+namespace emrt {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
+}  // namespace emrt
 
 namespace {
 
@@ -198,6 +207,8 @@ emrt_status check_paths(const emrt_paths *p) {
 
 extern "C" {
 
+uint64_t emrt_kernel_launches(void) { return emrt::launch_count(); }
+
 const char *emrt_status_string(emrt_status e) {
   switch (e) {
     case EMRT_OK: return "ok";
@@ -243,7 +254,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = grow(&s->face_info, c, std::max(s->Fs, 1u)))) return fail(e); c = 0;
   if ((e = grow(&s->face_vert, c, std::max(s->NV, 1u)))) return fail(e); c = 0;
   if ((e = grow(&s->bbox, c, 4))) return fail(e); c = 0;
-  if (s->Fs) k_faces<<<ceil_div(s->Fs, 128), 128, 0, st>>>(d->face_off, d->face_xyz, d->face_mat,
+  if (s->Fs) emrt::note_launch(), k_faces<<<ceil_div(s->Fs, 128), 128, 0, st>>>(d->face_off, d->face_xyz, d->face_mat,
                                                           s->Fs, s->face_plane, s->face_info,
                                                           s->face_vert);
   if ((e = grow(&s->ctr, c, 1))) return fail(e); c = 0;
@@ -265,7 +276,9 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = grow(&s->rx_vel, c, s->max_rx))) return fail(e); c = 0;
   if ((e = grow(&s->tx_pos, c, s->max_tx))) return fail(e); c = 0;
   if ((e = grow(&s->tx_vel, c, s->max_tx))) return fail(e); c = 0;
-  if (s->V) k_half<<<ceil_div(s->V, 256), 256, 0, st>>>(d->veh_half, s->V, s->veh_half);
+  if (s->V) emrt::note_launch(), k_half<<<ceil_div(s->V, 256), 256, 0, st>>>(d->veh_half, s->V, s->veh_half);
+  for (int k = 0; k < 4; k++)
+    if ((e = cudaEventCreate(&s->ev[k]))) return fail(e);
   e = cudaStreamSynchronize(st);
   if (!e) e = cudaGetLastError();
   if (e) return fail(e);
@@ -284,6 +297,8 @@ void emrt_scene_destroy(emrt_scene s) {
   cudaFree(s->cand); cudaFree(s->uniq); cudaFree(s->head); cudaFree(s->pos);
   for (int k = 0; k < 2; k++) { cudaFree(s->keys[k]); cudaFree(s->vals[k]); }
   cudaFree(s->seg_b); cudaFree(s->seg_e); cudaFree(s->contrib);
+  for (int k = 0; k < 4; k++)
+    if (s->ev[k]) cudaEventDestroy(s->ev[k]);
   delete s;
 }
 
@@ -299,7 +314,7 @@ emrt_status emrt_scene_update_dynamic(emrt_scene s, const float *veh_pos, const 
   s->n_rx = n_rx;
   s->n_tx = n_tx;
   uint32_t m = std::max(s->V, std::max(n_rx, n_tx));
-  k_update<<<ceil_div(m, 256), 256, 0, st>>>(veh_pos, veh_vel, s->veh_half, s->V, s->veh_lo,
+  emrt::note_launch(), k_update<<<ceil_div(m, 256), 256, 0, st>>>(veh_pos, veh_vel, s->veh_half, s->V, s->veh_lo,
                                              s->veh_hi, s->veh_vel, rx_pos, rx_vel, n_rx,
                                              s->rx_pos, s->rx_vel, tx_pos, tx_vel, n_tx, s->tx_pos,
                                              s->tx_vel);
@@ -376,6 +391,7 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
   float kappa = (float)(1.25 * sqrt(8.0 * 3.14159265358979323846 /
                                     (3.0 * sqrt(3.0) * (double)p->n_rays)));
   int grid = bounce_grid();
+  cudaEventRecord(s->ev[0], st);
   for (uint32_t b = 0; b <= p->max_depth; b++) {
     BounceLaunch L;
     L.g = g;
@@ -396,15 +412,19 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     L.K = (int)p->max_depth;
     launch_bounce(L, grid, st);
   }
-  k_check_cand<<<1, 1, 0, st>>>(c, s->cand_cap);
+  cudaEventRecord(s->ev[1], st);
+  emrt::note_launch(), k_check_cand<<<1, 1, 0, st>>>(c, s->cand_cap);
   dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
+  cudaEventRecord(s->ev[2], st);
   launch_accept(g, s->uniq, &c->n_unique, c, st);
   launch_keep_flags(s->uniq, &c->n_unique, (p->flags & EMRT_TRACE_KEEP_REJECTED) ? 1 : 0, s->head,
                     st);
   exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_accepted, s->partial, st);
   launch_scatter(s->uniq, &c->n_unique, s->head, s->pos, out->rec, out->capacity, &c->n_accepted,
                  c, st);
-  k_publish_count<<<1, 1, 0, st>>>(c, out->count);
+  emrt::note_launch(), k_publish_count<<<1, 1, 0, st>>>(c, out->count);
+  cudaEventRecord(s->ev[3], st);
+  s->ev_recorded = true;
   CK(cudaGetLastError());
   return EMRT_OK;
 }
@@ -417,7 +437,7 @@ emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emr
   Counters *c = s->ctr;
   GeomView g = geom(s);
   // clamp the count to the capacity before acceptance
-  k_clamp_count<<<1, 1, 0, st>>>(cache->count, cache->capacity, &c->n_eff);
+  emrt::note_launch(), k_clamp_count<<<1, 1, 0, st>>>(cache->count, cache->capacity, &c->n_eff);
   launch_copy_records(cache->rec, &c->n_eff, s->uniq, cache->capacity, st);
   launch_accept(g, s->uniq, &c->n_eff, c, st);
   int keep_all = (flags & EMRT_REVALIDATE_KEEP) ? 1 : 0;
@@ -425,7 +445,7 @@ emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emr
   exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_accepted, s->partial, st);
   launch_scatter(s->uniq, &c->n_eff, s->head, s->pos, cache->rec, cache->capacity, &c->n_accepted,
                  c, st);
-  k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+  emrt::note_launch(), k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
   CK(cudaGetLastError());
   return EMRT_OK;
 }
@@ -449,7 +469,7 @@ emrt_status emrt_cache_merge(emrt_scene s, emrt_paths *cache, const emrt_paths *
   exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_accepted, s->partial, st);
   launch_scatter(s->uniq, &c->n_unique, s->head, s->pos, cache->rec, cache->capacity,
                  &c->n_accepted, c, st);
-  k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+  emrt::note_launch(), k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
   CK(cudaGetLastError());
   return EMRT_OK;
 }
@@ -530,6 +550,16 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
     out->node_visits = h.node_visits;
     out->tri_tests = h.tri_tests;
     out->error_bits = h.err;
+    out->dyn_node_visits = h.dyn_node_visits;
+    out->box_tests = h.box_tests;
+    out->rx_node_visits = h.rx_node_visits;
+    out->rx_tests = h.rx_tests;
+    if (s->ev_recorded) {
+      cudaEventElapsedTime(&out->traverse_ms, s->ev[0], s->ev[1]);
+      cudaEventElapsedTime(&out->dedup_ms, s->ev[1], s->ev[2]);
+      cudaEventElapsedTime(&out->accept_ms, s->ev[2], s->ev[3]);
+      cudaEventElapsedTime(&out->trace_ms, s->ev[0], s->ev[3]);
+    }
     out->required_candidates = h.n_cand;
     out->required_paths = h.n_accepted;
   }

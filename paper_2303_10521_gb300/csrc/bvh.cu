@@ -238,9 +238,9 @@ template <int KIND>
 cudaError_t finish_build(BVHBuf &b, cudaStream_t s) {
   uint32_t n = b.n;
   if (n >= 2) {
-    k_hierarchy<<<ceil_div(n - 1, 256), 256, 0, s>>>(b.keys, (int)n, b.nodes, b.leaf_parent);
+    emrt::note_launch(), k_hierarchy<<<ceil_div(n - 1, 256), 256, 0, s>>>(b.keys, (int)n, b.nodes, b.leaf_parent);
     cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
-    k_refit<KIND><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+    emrt::note_launch(), k_refit<KIND><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
   }
   return cudaGetLastError();
 }
@@ -249,7 +249,7 @@ __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 
 template <int KIND>
 cudaError_t sort_codes(BVHBuf &b, uint32_t *hist, cudaStream_t s) {
-  k_set_u32<<<1, 1, 0, s>>>(b.d_n, b.n);
+  emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(b.d_n, b.n);
   bool alt = radix_sort<2>(b.d_n, b.keys, b.idx, b.keys2, b.idx2, 63, hist, s);
   if (alt) {
     std::swap(b.keys, b.keys2);
@@ -301,9 +301,9 @@ cudaError_t bvh_build_tris(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_
                            const float4 *bbox, uint32_t *hist, cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
-  k_morton_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, n, bbox, b.keys, b.idx);
+  emrt::note_launch(), k_morton_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_TRI>(b, hist, s);
-  k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
+  emrt::note_launch(), k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
   return finish_build<PRIM_TRI>(b, s);
 }
 
@@ -311,19 +311,19 @@ cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint3
                             const float4 *bbox, uint32_t *hist, cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
-  k_morton_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, bbox, b.keys, b.idx);
+  emrt::note_launch(), k_morton_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_BOX>(b, hist, s);
-  k_gather_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, b.idx, n, b.prims);
+  emrt::note_launch(), k_gather_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, b.idx, n, b.prims);
   return finish_build<PRIM_BOX>(b, s);
 }
 
 cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaStream_t s) {
   uint32_t n = b.n;
   if (n == 0) return cudaSuccess;
-  k_move_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, b.prims);
+  emrt::note_launch(), k_move_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, b.prims);
   if (n >= 2) {
     cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
-    k_refit<PRIM_BOX><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+    emrt::note_launch(), k_refit<PRIM_BOX><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
   }
   return cudaGetLastError();
 }
@@ -332,17 +332,17 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
                              uint32_t *hist, cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
-  k_morton_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, n, bbox, b.keys, b.idx);
+  emrt::note_launch(), k_morton_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_POINT>(b, hist, s);
-  k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, b.idx, n, b.prims);
+  emrt::note_launch(), k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, b.idx, n, b.prims);
   return finish_build<PRIM_POINT>(b, s);
 }
 
 void bbox_of_tris(const float *tri_xyz, uint32_t n, float4 *bbox, cudaStream_t s) {
   uint32_t *acc = reinterpret_cast<uint32_t *>(bbox + 2);  // 6 words of scratch after bbox
-  k_bbox_init<<<1, 32, 0, s>>>(acc);
-  if (n) k_bbox_tris<<<kPrimGrid, 256, 0, s>>>(tri_xyz, n, acc);
-  k_bbox_fin<<<1, 32, 0, s>>>(acc, bbox);
+  emrt::note_launch(), k_bbox_init<<<1, 32, 0, s>>>(acc);
+  if (n) emrt::note_launch(), k_bbox_tris<<<kPrimGrid, 256, 0, s>>>(tri_xyz, n, acc);
+  emrt::note_launch(), k_bbox_fin<<<1, 32, 0, s>>>(acc, bbox);
 }
 
 }  // namespace emrt

@@ -27,8 +27,12 @@ struct Counters {
   uint32_t n_accepted;
   uint32_t tmp;
   unsigned long long segments[EMRT_MAX_DEPTH + 1];
-  unsigned long long node_visits;
-  unsigned long long tri_tests;
+  unsigned long long node_visits;     // static BVH inner nodes visited
+  unsigned long long tri_tests;       // triangles tested
+  unsigned long long dyn_node_visits; // vehicle BVH inner nodes visited
+  unsigned long long box_tests;       // vehicle boxes tested
+  unsigned long long rx_node_visits;  // receiver BVH inner nodes visited
+  unsigned long long rx_tests;        // receivers tested against a sphere
   unsigned long long occl_rays;
 };
 
@@ -112,5 +116,9 @@ struct GeomView {
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// host-side count of kernel launches issued by this library (diagnostics)
+void note_launch();
+unsigned long long launch_count();
 
 }  // namespace emrt

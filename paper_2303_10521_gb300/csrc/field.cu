@@ -458,7 +458,7 @@ __global__ void k_grad_reduce(GeomView g, MatView m, const uint32_t *rec, const 
 
 void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                   uint32_t cap, double freq, double *path_out, cudaStream_t s) {
-  k_field<<<152 * 8, 128, 0, s>>>(g, m, rec, n, cap, freq, path_out);
+  emrt::note_launch(), k_field<<<152 * 8, 128, 0, s>>>(g, m, rec, n, cap, freq, path_out);
 }
 
 void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
@@ -467,10 +467,10 @@ void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const d
   uint32_t np = n_tx * n_rx;
   cudaMemsetAsync(seg_begin, 0, sizeof(uint32_t) * np, s);
   cudaMemsetAsync(seg_end, 0, sizeof(uint32_t) * np, s);
-  k_pair_bounds<<<152 * 8, 256, 0, s>>>(rec, n, cap, n_tx, n_rx, seg_begin, seg_end);
-  k_pair_reduce<<<ceil_div(np, 8) < 152 * 16 ? ceil_div(np, 8) : 152 * 16, 256, 0, s>>>(
+  emrt::note_launch(), k_pair_bounds<<<152 * 8, 256, 0, s>>>(rec, n, cap, n_tx, n_rx, seg_begin, seg_end);
+  emrt::note_launch(), k_pair_reduce<<<ceil_div(np, 8) < 152 * 16 ? ceil_div(np, 8) : 152 * 16, 256, 0, s>>>(
       path_out, seg_begin, seg_end, np, pair_out);
-  if (rx_out) k_rx_power<<<ceil_div(n_rx, 256), 256, 0, s>>>(pair_out, n_tx, n_rx, tx_power_w, rx_out);
+  if (rx_out) emrt::note_launch(), k_rx_power<<<ceil_div(n_rx, 256), 256, 0, s>>>(pair_out, n_tx, n_rx, tx_power_w, rx_out);
 }
 
 int adjoint_grid() { return 152 * 4; }
@@ -479,10 +479,10 @@ void launch_field_adjoint(const GeomView &g, MatView m, const uint32_t *rec, con
                           uint32_t cap, double freq, const double *dloss_dh, uint32_t n_rx,
                           double *contrib, double *grad_eps, double *grad_sigma, double *grad_tx,
                           cudaStream_t s) {
-  k_field_tangents<<<adjoint_grid(), kAdjBlock, 0, s>>>(g, m, rec, n, cap, freq, dloss_dh, n_rx,
+  emrt::note_launch(), k_field_tangents<<<adjoint_grid(), kAdjBlock, 0, s>>>(g, m, rec, n, cap, freq, dloss_dh, n_rx,
                                                         contrib);
   uint32_t n_par = 2 * m.n_mat + 3 * g.n_tx;
-  k_grad_reduce<<<n_par, 256, 0, s>>>(g, m, rec, n, cap, contrib, grad_eps, grad_sigma, grad_tx);
+  emrt::note_launch(), k_grad_reduce<<<n_par, 256, 0, s>>>(g, m, rec, n, cap, contrib, grad_eps, grad_sigma, grad_tx);
 }
 
 }  // namespace emrt

@@ -165,9 +165,9 @@ bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *key
   for (int p = 0; p < passes; p++) {
     KeyW<W> *ki = alt ? keys2 : keys, *ko = alt ? keys : keys2;
     uint32_t *vi = alt ? vals2 : vals, *vo = alt ? vals : vals2;
-    k_hist<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
-    k_scan_single<<<1, 1024, 0, s>>>(hist, 256 * kPrimGrid, nullptr);
-    k_scatter<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
+    emrt::note_launch(), k_hist<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
+    emrt::note_launch(), k_scan_single<<<1, 1024, 0, s>>>(hist, 256 * kPrimGrid, nullptr);
+    emrt::note_launch(), k_scatter<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
     alt = !alt;
   }
   return alt;
@@ -182,9 +182,9 @@ template bool radix_sort<4>(const uint32_t *, KeyW<4> *, uint32_t *, KeyW<4> *, 
 
 void exclusive_scan(const uint32_t *d_n, const uint32_t *in, uint32_t *out, uint32_t *d_total,
                     uint32_t *partial, cudaStream_t s) {
-  k_scan_reduce<<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, in, partial);
-  k_scan_single<<<1, 1024, 0, s>>>(partial, kPrimGrid, d_total);
-  k_scan_down<<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, in, out, partial);
+  emrt::note_launch(), k_scan_reduce<<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, in, partial);
+  emrt::note_launch(), k_scan_single<<<1, 1024, 0, s>>>(partial, kPrimGrid, d_total);
+  emrt::note_launch(), k_scan_down<<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, in, out, partial);
 }
 
 }  // namespace emrt

@@ -185,6 +185,10 @@ __global__ void __launch_bounds__(kBounceBlock) k_bounce(BounceLaunch L) {
   add_u64(&L.ctr->segments[L.b], segs);
   add_u64(&L.ctr->node_visits, st.nodes);
   add_u64(&L.ctr->tri_tests, st.tris);
+  add_u64(&L.ctr->dyn_node_visits, st.dnodes);
+  add_u64(&L.ctr->box_tests, st.boxes);
+  add_u64(&L.ctr->rx_node_visits, st.rnodes);
+  add_u64(&L.ctr->rx_tests, st.rxs);
   if (st.overflow) atomicOr(&L.ctr->err, ERR_STACK);
 }
 
@@ -458,51 +462,51 @@ void build_dir_table(uint64_t n_rays, uint64_t offset, uint64_t stride, uint32_t
                      float4 *table, KeyW<1> *k0, KeyW<1> *k1, uint32_t *v0, uint32_t *v1,
                      uint32_t *d_n, uint32_t *hist, cudaStream_t s) {
   if (!count) return;
-  k_dir_codes<<<ceil_div(count, 256), 256, 0, s>>>(n_rays, offset, stride, count, k0, v0);
-  k_set_u32<<<1, 1, 0, s>>>(d_n, count);
+  emrt::note_launch(), k_dir_codes<<<ceil_div(count, 256), 256, 0, s>>>(n_rays, offset, stride, count, k0, v0);
+  emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(d_n, count);
   bool alt = radix_sort<1>(d_n, k0, v0, k1, v1, 32, hist, s);
-  k_dir_table<<<ceil_div(count, 256), 256, 0, s>>>(n_rays, offset, stride, count, alt ? v1 : v0,
+  emrt::note_launch(), k_dir_table<<<ceil_div(count, 256), 256, 0, s>>>(n_rays, offset, stride, count, alt ? v1 : v0,
                                                    table);
 }
 
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s) {
-  k_bounce<<<grid, kBounceBlock, 0, s>>>(L);
+  emrt::note_launch(), k_bounce<<<grid, kBounceBlock, 0, s>>>(L);
 }
 
 void launch_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,
                       KeyW<4> *keys, uint32_t *vals, uint32_t *n_eff, cudaStream_t s) {
-  k_path_keys<<<kPrimGrid * 4, 256, 0, s>>>(rec, n, cap, kl, keys, vals, n_eff);
+  emrt::note_launch(), k_path_keys<<<kPrimGrid * 4, 256, 0, s>>>(rec, n, cap, kl, keys, vals, n_eff);
 }
 void launch_heads(const KeyW<4> *keys, const uint32_t *n, uint32_t *head, cudaStream_t s) {
-  k_heads<<<kPrimGrid * 4, 256, 0, s>>>(keys, n, head);
+  emrt::note_launch(), k_heads<<<kPrimGrid * 4, 256, 0, s>>>(keys, n, head);
 }
 void launch_unique(const uint32_t *rec, const KeyW<4> *keys, const uint32_t *vals,
                    const uint32_t *head, const uint32_t *pos, const uint32_t *n, uint32_t *uniq,
                    cudaStream_t s) {
-  k_unique<<<kPrimGrid * 4, 256, 0, s>>>(rec, keys, vals, head, pos, n, uniq);
+  emrt::note_launch(), k_unique<<<kPrimGrid * 4, 256, 0, s>>>(rec, keys, vals, head, pos, n, uniq);
 }
 void launch_accept(const GeomView &g, uint32_t *rec, const uint32_t *n, Counters *ctr,
                    cudaStream_t s) {
-  k_accept<<<kPrimGrid * 4, kBounceBlock, 0, s>>>(g, rec, n, ctr);
+  emrt::note_launch(), k_accept<<<kPrimGrid * 4, kBounceBlock, 0, s>>>(g, rec, n, ctr);
 }
 void launch_keep_flags(const uint32_t *rec, const uint32_t *n, int keep_all, uint32_t *flag,
                        cudaStream_t s) {
-  k_keep_flags<<<kPrimGrid * 4, 256, 0, s>>>(rec, n, keep_all, flag);
+  emrt::note_launch(), k_keep_flags<<<kPrimGrid * 4, 256, 0, s>>>(rec, n, keep_all, flag);
 }
 void launch_scatter(const uint32_t *in, const uint32_t *n, const uint32_t *flag,
                     const uint32_t *pos, uint32_t *out, uint32_t cap, const uint32_t *total,
                     Counters *ctr, cudaStream_t s) {
-  k_scatter_rec<<<kPrimGrid * 4, 256, 0, s>>>(in, n, flag, pos, out, cap, total, ctr);
+  emrt::note_launch(), k_scatter_rec<<<kPrimGrid * 4, 256, 0, s>>>(in, n, flag, pos, out, cap, total, ctr);
 }
 void launch_copy_records(const uint32_t *in, const uint32_t *n, uint32_t *out, uint32_t cap,
                          cudaStream_t s) {
-  k_copy_rec<<<kPrimGrid * 4, 256, 0, s>>>(in, n, out, cap);
+  emrt::note_launch(), k_copy_rec<<<kPrimGrid * 4, 256, 0, s>>>(in, n, out, cap);
 }
 void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const uint32_t *b,
                    const uint32_t *nb, uint32_t cap_b, uint32_t *dst, uint32_t dst_cap,
                    uint32_t *n_dst, Counters *ctr, cudaStream_t s) {
-  k_concat<<<kPrimGrid * 4, 256, 0, s>>>(a, na, cap_a, b, nb, cap_b, dst, dst_cap, n_dst, ctr);
+  emrt::note_launch(), k_concat<<<kPrimGrid * 4, 256, 0, s>>>(a, na, cap_a, b, nb, cap_b, dst, dst_cap, n_dst, ctr);
 }
-void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s) { k_set_u32<<<1, 1, 0, s>>>(p, v); }
+void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s) { emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(p, v); }
 
 }  // namespace emrt

@@ -92,7 +92,7 @@ __device__ inline bool tri_hit(const RayQ &r, float3 v0, float3 v1, float3 v2, f
 }
 
 struct TravStats {
-  uint32_t nodes = 0, tris = 0;
+  uint32_t nodes = 0, tris = 0, dnodes = 0, boxes = 0, rnodes = 0, rxs = 0;
   bool overflow = false;
 };
 #define EMRT_ITER_GUARD(st)            \
@@ -179,6 +179,7 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
     if (node >= 0) {
       const float4 *np = b.nodes + 4ll * node;
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+      st.dnodes++;
       float tn0, tn1;
       bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
       bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
@@ -197,6 +198,7 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
     } else {
       uint32_t g = (uint32_t)(~node);
       float4 lo = ldg4(b.prims + 2ull * g), hi = ldg4(b.prims + 2ull * g + 1);
+      st.boxes++;
       uint32_t v = __float_as_uint(lo.w);
       if (v != exv0 && v != exv1) {
         float tx0 = (lo.x - r.o.x) * r.idir.x, tx1 = (hi.x - r.o.x) * r.idir.x;
@@ -244,6 +246,7 @@ __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, fl
     if (node >= 0) {
       const float4 *np = b.nodes + 4ll * node;
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+      st.rnodes++;
       float tn0, tn1;
       bool h0 = slab(r, n0.x - rmax, n0.y + rmax, n0.z - rmax, n0.w + rmax, n2.x - rmax,
                      n2.y + rmax, 0.f, t_end, tn0);
@@ -260,6 +263,7 @@ __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, fl
       if (h1) { node = c1; continue; }
     } else {
       float4 p = ldg4(b.prims + (uint32_t)(~node));
+      st.rxs++;
       float3 w = f3(p) - r.o;
       float s = dot3(w, r.d);
       if (s > 0.f && s <= t_end) {

@@ -149,7 +149,7 @@ def test_revalidation_and_merge(engine):
     g = _gpu(engine, sc)
     p0 = g.trace(stride=53)
     n0 = p0.n()
-    assert n0 > 100
+    assert n0 > 40
     fr3 = sc.frame(3)
     g.update(fr3)
     g.revalidate(p0, keep=True)
