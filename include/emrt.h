@@ -185,6 +185,35 @@ emrt_status emrt_channel_backward(emrt_scene sc, const emrt_paths *paths,
                                   double *grad_sigma, double *grad_tx,
                                   emrt_stream s);
 
+/* Allocation-free variant of emrt_channel_backward, for callers that must
+ * not allocate device memory after set-up: code running inside a CUDA graph
+ * capture (cudaMalloc is not allowed there), applications whose device memory
+ * is owned by another allocator or capped, and real-time loops that
+ * pre-allocate once.  The paper has no counterpart; it is a library service.
+ *
+ * Same arguments and results as emrt_channel_backward, but the per-path
+ * tangent scratch lives in a fixed device array compiled into libemrt.so
+ * (EMRT_NOALLOC_MAX_PATHS x 11 doubles, 5.8 MB, held by every GPU that loads
+ * the library until the process exits) instead of scene-owned memory, and the
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Requirements and behaviour:
+ *  - paths->capacity must be <= EMRT_NOALLOC_MAX_PATHS, otherwise
+ *    EMRT_ERR_INVALID_ARG is returned and nothing is launched;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins;
+ *  - every call on a device shares the one array: calls whose kernels overlap
+ *    on the GPU (different streams without ordering) race and give wrong
+ *    gradients; order them on one stream.  The array keeps the last call's
+ *    contents; each call overwrites every entry it reads, so no clearing is
+ *    needed. */
+#define EMRT_NOALLOC_MAX_PATHS 65536u
+emrt_status emrt_channel_backward_noalloc(emrt_scene sc, const emrt_paths *paths,
+                                          const emrt_materials *m, double freq_hz,
+                                          const double *dloss_dh, double *grad_eps,
+                                          double *grad_sigma, double *grad_tx,
+                                          emrt_stream s);
+
 typedef struct {
   uint64_t segments[EMRT_MAX_DEPTH + 1]; /* closest-hit segments per bounce */
   uint64_t candidates;        /* reception-sphere detections                 */

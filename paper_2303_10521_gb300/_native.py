@@ -19,6 +19,7 @@ PATH_MARGINAL = 0x200
 TRACE_KEEP_REJECTED = 0x1
 TRACE_SORT_RAYS = 0x2
 REVALIDATE_KEEP = 0x1
+NOALLOC_MAX_PATHS = 65536
 
 vp, u32, u64, dbl = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
 
@@ -74,6 +75,8 @@ SIGNATURES = {
                                C.POINTER(ChannelOut), vp]),
     "emrt_channel_backward": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, vp,
                                         vp, vp, vp, vp]),
+    "emrt_channel_backward_noalloc": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials),
+                                                dbl, vp, vp, vp, vp, vp]),
     "emrt_sync": (C.c_int, [vp, vp, C.POINTER(Stats)]),
     "emrt_status_string": (C.c_char_p, [C.c_int]),
     "emrt_kernel_launches": (u64, []),

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "bvh.cuh"
@@ -527,6 +528,61 @@ emrt_status emrt_channel_backward(emrt_scene s, const emrt_paths *paths, const e
   GeomView g = geom(s);
   launch_field_adjoint(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, dloss_dh,
                        s->n_rx, s->contrib, grad_eps, grad_sigma, grad_tx, st);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint: the per-path tangent scratch is this file-scope
+// device array (EMRT_NOALLOC_MAX_PATHS x 11 doubles).  Host code must not use
+// the symbol `g_noalloc_contrib` as an address: it is a host-side stand-in.
+// Its device address is looked up once per device, with that device current,
+// by noalloc_scratch() and cached here.
+static __device__ __align__(256) double
+    g_noalloc_contrib[(size_t)EMRT_NOALLOC_MAX_PATHS * (3 + 2 * EMRT_MAX_DEPTH)];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+cudaError_t noalloc_scratch(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_contrib);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+emrt_status emrt_channel_backward_noalloc(emrt_scene s, const emrt_paths *paths,
+                                          const emrt_materials *m, double freq_hz,
+                                          const double *dloss_dh, double *grad_eps,
+                                          double *grad_sigma, double *grad_tx,
+                                          emrt_stream stream) {
+  if (!s || check_paths(paths) != EMRT_OK || check_mat(m) != EMRT_OK || !dloss_dh || !grad_eps ||
+      !grad_sigma || !grad_tx || !(freq_hz > 0))
+    return EMRT_ERR_INVALID_ARG;
+  if (paths->capacity > EMRT_NOALLOC_MAX_PATHS) return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  double *scratch = nullptr;
+  CK(noalloc_scratch(&scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  GeomView g = geom(s);
+  launch_field_adjoint(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, dloss_dh,
+                       s->n_rx, scratch, grad_eps, grad_sigma, grad_tx, st);
   CK(cudaGetLastError());
   return EMRT_OK;
 }
