@@ -231,8 +231,11 @@ typedef struct {
   uint32_t required_paths;
   uint32_t pad;
   /* device time of the last emrt_trace (CUDA events on its stream), ms:
-   * closest-hit traversal kernels, deduplication, image-method acceptance */
-  float traverse_ms, dedup_ms, accept_ms, trace_ms;
+   * discovery stage (traversal kernels and ray sorts), deduplication,
+   * image-method acceptance, whole call, and the closest-hit traversal
+   * kernels alone (sum over bounces) */
+  float traverse_ms, dedup_ms, accept_ms, trace_ms, bounce_ms;
+  uint32_t pad2;
 } emrt_stats;
 
 /* Waits for the stream, reads and clears the device error word, returns the

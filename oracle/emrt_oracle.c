@@ -14,7 +14,9 @@
  *  - a closest-hit tie goes to the lower face ID;
  *  - the reception radius is r(L) = 1.25 * sqrt(8 pi / (3 sqrt(3) N)) * L,
  *    the hexagonal covering angle of N directions widened by the measured
- *    excess of the Fibonacci lattice near its poles;
+ *    excess of the Fibonacci lattice near its poles; a receiver is detected
+ *    when the traced segment passes within r(L) of it (L at the segment
+ *    point nearest to the receiver);
  *  - antennas are ideal omnidirectional and vertically polarised:
  *    p(k) = normalise(z - (z.k) k);
  *  - time convention exp(+j w t): propagation is exp(-j k L);
@@ -297,20 +299,19 @@ static void trace_one(trace_ctx *C, int tx, uint64_t j, pbuf *out, uint8_t *marg
     double e_end = eps + C->eps_rel * (isfinite(best_t) ? best_t : 0.0);
     int seg_marg = isfinite(near_t) && near_t <= best_t + e_end;
     if (seg_marg && first_marg == 255) first_marg = b;
-    /* reception spheres on the segment (0, best_t] */
+    /* reception spheres: a receiver is detected when the traced segment
+     * [0, best_t] (a ray when nothing is hit) passes within r(L) of it, with
+     * L the unfolded length at the segment point nearest to the receiver */
     for (int r = 0; r < s->nrx; r++) {
       v3 w = sub(s->rx[r], o);
       double sp = dot(w, d);
-      double dist = norm(sub(w, scl(d, sp)));
-      double rad = C->kappa * (Lacc + sp);
-      double e = eps + C->eps_rel * fmax(sp, 0.0);
-      int in_seg = sp > 0.0 && sp <= best_t;
-      int near_end = fabs(sp) < e || (isfinite(best_t) && fabs(sp - best_t) < e);
-      int inside = in_seg && dist <= rad;
+      double sc = fmin(fmax(sp, 0.0), best_t);
+      double dist = norm(sub(w, scl(d, sc)));
+      double rad = C->kappa * (Lacc + sc);
+      double e = eps + C->eps_rel * sc;
+      int inside = dist <= rad;
       int near_sphere = fabs(dist - rad) < e;
-      if (!inside && !((near_sphere && (in_seg || near_end)) ||
-                       (near_end && dist <= rad + e)))
-        continue;
+      if (!inside && !near_sphere) continue;
       orc_path rec;
       memset(&rec, 0, sizeof(rec));
       rec.tx = (uint32_t)tx;
@@ -320,7 +321,7 @@ static void trace_one(trace_ctx *C, int tx, uint64_t j, pbuf *out, uint8_t *marg
       for (int k = b; k < ORC_MAX_DEPTH; k++) rec.face[k] = 0xffffffffu;
       rec.ray = (uint32_t)j;
       if (!inside) rec.flag = 2;
-      else if (near_sphere || near_end || first_marg != 255) rec.flag = 1;
+      else if (near_sphere || first_marg != 255) rec.flag = 1;
       else rec.flag = 0;
       pb_push(out, &rec);
     }

@@ -56,7 +56,8 @@ class Stats(C.Structure):
                 ("box_tests", u64), ("rx_node_visits", u64), ("rx_tests", u64),
                 ("error_bits", u32), ("required_candidates", u32), ("required_paths", u32),
                 ("pad", u32), ("traverse_ms", C.c_float), ("dedup_ms", C.c_float),
-                ("accept_ms", C.c_float), ("trace_ms", C.c_float)]
+                ("accept_ms", C.c_float), ("trace_ms", C.c_float), ("bounce_ms", C.c_float),
+                ("pad2", u32)]
 
 
 STATUS = {0: "EMRT_OK", 1: "EMRT_ERR_INVALID_ARG", 2: "EMRT_ERR_OOM", 3: "EMRT_ERR_CUDA",

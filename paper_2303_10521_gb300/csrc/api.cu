@@ -28,26 +28,33 @@ struct emrt_scene_s {
   bool updated = false;
   Counters *ctr = nullptr;
   uint32_t *hist = nullptr, *partial = nullptr;
-  // primary direction table cache
-  uint64_t dt_n = 0, dt_off = 0, dt_stride = 0;
-  uint32_t dt_count = 0;
-  float4 *dirs = nullptr;
-  uint32_t dirs_cap = 0;
-  // ray ping-pong buffers
+  // primary direction tables, one per recently used ray set (LRU)
+  struct DirTable {
+    uint64_t n = 0, off = 0, stride = 0, cap = 0, last_use = 0;
+    uint32_t count = 0;
+    float4 *dirs = nullptr;
+  } dt[4];
+  uint64_t dt_clock = 0;
+  uint32_t *dt_scratch = nullptr;  // key/value scratch for building a table
+  uint64_t dt_scratch_cap = 0;
+  // ray ping-pong buffers and the coherence-sort scratch
   Ray *rays[2] = {nullptr, nullptr};
   uint64_t ray_cap = 0;
+  KeyW<1> *rkeys[2] = {nullptr, nullptr};
+  uint32_t *rvals[2] = {nullptr, nullptr};
+  uint64_t rsort_cap = 0;
   // candidate and path scratch
   uint32_t cand_cap = 0, want_cand = 0;
   uint32_t *cand = nullptr, *uniq = nullptr, *head = nullptr, *pos = nullptr;
   KeyW<4> *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
-  // reduction / adjoint scratch
-  uint32_t *seg_b = nullptr, *seg_e = nullptr;
-  uint32_t pair_cap = 0;
+  // adjoint scratch
   double *contrib = nullptr;
   uint64_t contrib_cap = 0;
   emrt_status sticky = EMRT_OK;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t evb[2 * (EMRT_MAX_DEPTH + 1)] = {};  // around each k_bounce launch
+  uint32_t ev_bounces = 0;
   bool ev_recorded = false;
 };
 
@@ -191,7 +198,7 @@ void dedup(emrt_scene_s *s, const uint32_t *src, const uint32_t *n, uint32_t cap
   Counters *c = s->ctr;
   launch_path_keys(src, n, cap, kl, s->keys[0], s->vals[0], &c->n_eff, st);
   bool alt = radix_sort<4>(&c->n_eff, s->keys[0], s->vals[0], s->keys[1], s->vals[1], kl.total,
-                           s->hist, st);
+                           s->hist, st, cap);
   KeyW<4> *ks = s->keys[alt ? 1 : 0];
   uint32_t *vs = s->vals[alt ? 1 : 0];
   launch_heads(ks, &c->n_eff, s->head, st);
@@ -280,6 +287,8 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if (s->V) emrt::note_launch(), k_half<<<ceil_div(s->V, 256), 256, 0, st>>>(d->veh_half, s->V, s->veh_half);
   for (int k = 0; k < 4; k++)
     if ((e = cudaEventCreate(&s->ev[k]))) return fail(e);
+  for (int k = 0; k < 2 * (EMRT_MAX_DEPTH + 1); k++)
+    if ((e = cudaEventCreate(&s->evb[k]))) return fail(e);
   e = cudaStreamSynchronize(st);
   if (!e) e = cudaGetLastError();
   if (e) return fail(e);
@@ -293,13 +302,18 @@ void emrt_scene_destroy(emrt_scene s) {
   bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb);
   cudaFree(s->veh_half); cudaFree(s->veh_lo); cudaFree(s->veh_hi); cudaFree(s->veh_vel);
   cudaFree(s->rx_pos); cudaFree(s->rx_vel); cudaFree(s->tx_pos); cudaFree(s->tx_vel);
-  cudaFree(s->ctr); cudaFree(s->hist); cudaFree(s->partial); cudaFree(s->dirs);
+  cudaFree(s->ctr); cudaFree(s->hist); cudaFree(s->partial);
+  for (auto &t : s->dt) cudaFree(t.dirs);
+  cudaFree(s->dt_scratch);
   cudaFree(s->rays[0]); cudaFree(s->rays[1]);
+  for (int k = 0; k < 2; k++) { cudaFree(s->rkeys[k]); cudaFree(s->rvals[k]); }
   cudaFree(s->cand); cudaFree(s->uniq); cudaFree(s->head); cudaFree(s->pos);
   for (int k = 0; k < 2; k++) { cudaFree(s->keys[k]); cudaFree(s->vals[k]); }
-  cudaFree(s->seg_b); cudaFree(s->seg_e); cudaFree(s->contrib);
+  cudaFree(s->contrib);
   for (int k = 0; k < 4; k++)
     if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+  for (int k = 0; k < 2 * (EMRT_MAX_DEPTH + 1); k++)
+    if (s->evb[k]) cudaEventDestroy(s->evb[k]);
   delete s;
 }
 
@@ -349,28 +363,28 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
   if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   Counters *c = s->ctr;
-  // primary direction table (recomputed when the ray set changes)
-  if (!s->dirs || s->dt_n != p->n_rays || s->dt_off != p->ray_offset ||
-      s->dt_stride != p->ray_stride || s->dt_count != count) {
-    uint64_t cap = s->dirs_cap;
-    CK(grow(&s->dirs, cap, count));
-    s->dirs_cap = (uint32_t)cap;
-    KeyW<1> *k0, *k1;
-    uint32_t *v0, *v1;
-    CK(cudaMalloc(&k0, sizeof(KeyW<1>) * count * 2));
-    CK(cudaMalloc(&v0, sizeof(uint32_t) * count * 2));
-    k1 = k0 + count;
-    v1 = v0 + count;
-    build_dir_table(p->n_rays, p->ray_offset, p->ray_stride, (uint32_t)count, s->dirs, k0, k1, v0,
-                    v1, &c->tmp, s->hist, st);
-    cudaStreamSynchronize(st);
-    cudaFree(k0);
-    cudaFree(v0);
-    s->dt_n = p->n_rays;
-    s->dt_off = p->ray_offset;
-    s->dt_stride = p->ray_stride;
-    s->dt_count = (uint32_t)count;
+  // primary direction table of this ray set (built once, kept in an LRU of 4)
+  emrt_scene_s::DirTable *tab = nullptr;
+  for (auto &t : s->dt)
+    if (t.dirs && t.n == p->n_rays && t.off == p->ray_offset && t.stride == p->ray_stride &&
+        t.count == count)
+      tab = &t;
+  if (!tab) {
+    tab = &s->dt[0];
+    for (auto &t : s->dt)
+      if (t.last_use < tab->last_use) tab = &t;
+    CK(grow(&tab->dirs, tab->cap, count));
+    CK(grow(&s->dt_scratch, s->dt_scratch_cap, 4 * count));
+    KeyW<1> *k0 = reinterpret_cast<KeyW<1> *>(s->dt_scratch), *k1 = k0 + count;
+    uint32_t *v0 = s->dt_scratch + 2 * count, *v1 = v0 + count;
+    build_dir_table(p->n_rays, p->ray_offset, p->ray_stride, (uint32_t)count, tab->dirs, k0, k1,
+                    v0, v1, &c->tmp, s->hist, st);
+    tab->n = p->n_rays;
+    tab->off = p->ray_offset;
+    tab->stride = p->ray_stride;
+    tab->count = (uint32_t)count;
   }
+  tab->last_use = ++s->dt_clock;
   uint64_t nrays = count * s->n_tx;
   if (p->max_depth > 0 && nrays > s->ray_cap) {
     cudaFree(s->rays[0]);
@@ -380,6 +394,21 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     CK(cudaMalloc(&s->rays[0], sizeof(Ray) * nrays));
     CK(cudaMalloc(&s->rays[1], sizeof(Ray) * nrays));
     s->ray_cap = nrays;
+  }
+  bool sort_rays = (p->flags & EMRT_TRACE_SORT_RAYS) && p->max_depth > 0;
+  if (sort_rays && nrays > s->rsort_cap) {
+    for (int k = 0; k < 2; k++) {
+      cudaFree(s->rkeys[k]);
+      cudaFree(s->rvals[k]);
+      s->rkeys[k] = nullptr;
+      s->rvals[k] = nullptr;
+    }
+    s->rsort_cap = 0;
+    for (int k = 0; k < 2; k++) {
+      CK(cudaMalloc(&s->rkeys[k], sizeof(KeyW<1>) * nrays));
+      CK(cudaMalloc(&s->rvals[k], sizeof(uint32_t) * nrays));
+    }
+    s->rsort_cap = nrays;
   }
   uint64_t want = std::max<uint64_t>(s->want_cand,
                                      std::max<uint64_t>(1u << 16, 4ull * s->n_tx * s->n_rx * (p->max_depth + 1)));
@@ -397,9 +426,16 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     BounceLaunch L;
     L.g = g;
     L.rin = b ? s->rays[(b - 1) & 1] : nullptr;
+    L.order = nullptr;
+    if (b > 0 && sort_rays) {  // reorder reflected rays for coherent traversal
+      launch_ray_keys(L.rin, &c->n_ray[b], s->bbox, s->rkeys[0], s->rvals[0], st);
+      bool alt = radix_sort<1>(&c->n_ray[b], s->rkeys[0], s->rvals[0], s->rkeys[1], s->rvals[1],
+                               32, s->hist, st, nrays);
+      L.order = s->rvals[alt ? 1 : 0];
+    }
     L.n_in = &c->n_ray[b];
     L.n_primary = (uint32_t)nrays;
-    L.dirs = s->dirs;
+    L.dirs = tab->dirs;
     L.count = (uint32_t)count;
     L.rout = s->rays[b & 1];
     L.n_out = &c->n_ray[b + 1];
@@ -411,8 +447,11 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     L.kappa = kappa;
     L.b = (int)b;
     L.K = (int)p->max_depth;
+    cudaEventRecord(s->evb[2 * b], st);
     launch_bounce(L, grid, st);
+    cudaEventRecord(s->evb[2 * b + 1], st);
   }
+  s->ev_bounces = p->max_depth + 1;
   cudaEventRecord(s->ev[1], st);
   emrt::note_launch(), k_check_cand<<<1, 1, 0, st>>>(c, s->cand_cap);
   dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
@@ -500,17 +539,10 @@ emrt_status emrt_channel(emrt_scene s, const emrt_paths *paths, const emrt_mater
   if (!s->updated) return EMRT_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
   GeomView g = geom(s);
-  uint64_t np = (uint64_t)s->n_tx * s->n_rx;
-  if (np > s->pair_cap) {
-    uint64_t c = 0;
-    CK(grow(&s->seg_b, c, np)); c = 0;
-    CK(grow(&s->seg_e, c, np));
-    s->pair_cap = (uint32_t)np;
-  }
   launch_field(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, out->path_out,
                st);
   launch_reduce(paths->rec, paths->count, paths->capacity, out->path_out, s->n_tx, s->n_rx,
-                tx_power_w, s->seg_b, s->seg_e, out->pair_out, out->rx_out, st);
+                tx_power_w, out->pair_out, out->rx_out, st);
   CK(cudaGetLastError());
   return EMRT_OK;
 }
@@ -615,6 +647,12 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
       cudaEventElapsedTime(&out->dedup_ms, s->ev[1], s->ev[2]);
       cudaEventElapsedTime(&out->accept_ms, s->ev[2], s->ev[3]);
       cudaEventElapsedTime(&out->trace_ms, s->ev[0], s->ev[3]);
+      out->bounce_ms = 0.f;
+      for (uint32_t b = 0; b < s->ev_bounces; b++) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, s->evb[2 * b], s->evb[2 * b + 1]);
+        out->bounce_ms += t;
+      }
     }
     out->required_candidates = h.n_cand;
     out->required_paths = h.n_accepted;

@@ -250,7 +250,7 @@ __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 template <int KIND>
 cudaError_t sort_codes(BVHBuf &b, uint32_t *hist, cudaStream_t s) {
   emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(b.d_n, b.n);
-  bool alt = radix_sort<2>(b.d_n, b.keys, b.idx, b.keys2, b.idx2, 63, hist, s);
+  bool alt = radix_sort<2>(b.d_n, b.keys, b.idx, b.keys2, b.idx2, 63, hist, s, b.n);
   if (alt) {
     std::swap(b.keys, b.keys2);
     std::swap(b.idx, b.idx2);

@@ -315,44 +315,33 @@ __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_pair_bounds(const uint32_t *rec, const uint32_t *n, uint32_t cap, uint32_t n_tx,
-                              uint32_t n_rx, uint32_t *beg, uint32_t *end) {
+// Per (tx, rx) statistics: the thread holding the first path of a run of
+// equal (tx, rx) in the canonical order sums the run sequentially (fixed
+// order, deterministic); pairs without paths keep the zeros written before.
+__global__ void k_pair_seq(const uint32_t *rec, const uint32_t *n, uint32_t cap, uint32_t n_tx,
+                           uint32_t n_rx, const double *path_out, double *pair_out) {
   uint32_t cnt = min(*n, cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-    if (rec[8ull * i] >= n_tx || rec[8ull * i + 1] >= n_rx) continue;
-    uint32_t p = rec[8ull * i] * n_rx + rec[8ull * i + 1];
-    if (i == 0 || rec[8ull * (i - 1)] * n_rx + rec[8ull * (i - 1) + 1] != p) beg[p] = i;
-    if (i + 1 == cnt || rec[8ull * (i + 1)] * n_rx + rec[8ull * (i + 1) + 1] != p) end[p] = i + 1;
-  }
-}
-
-// one warp per (tx, rx) pair; fixed-order lane-strided sums and shuffle tree
-__global__ void k_pair_reduce(const double *path_out, const uint32_t *beg, const uint32_t *end,
-                              uint32_t n_pairs, double *pair_out) {
-  uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t p = warp; p < n_pairs; p += nw) {
-    uint32_t b = beg[p], e = end[p];
+    uint32_t tx = rec[8ull * i], rx = rec[8ull * i + 1];
+    if (tx >= n_tx || rx >= n_rx) continue;
+    if (i > 0 && rec[8ull * (i - 1)] == tx && rec[8ull * (i - 1) + 1] == rx) continue;
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (uint32_t i = b + lane; i < e; i += 32) {
-      double4 o = reinterpret_cast<const double4 *>(path_out)[i];
+    uint32_t e = i;
+    for (; e < cnt && rec[8ull * e] == tx && rec[8ull * e + 1] == rx; e++) {
+      double4 o = reinterpret_cast<const double4 *>(path_out)[e];
       double w = o.x * o.x + o.y * o.y;
       s[0] += o.x; s[1] += o.y; s[2] += w;
       s[3] += w * o.w; s[4] += w * o.w * o.w;
       s[5] += w * o.z; s[6] += w * o.z * o.z;
     }
-    for (int k = 0; k < 7; k++)
-      for (int off = 16; off; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
-    if (lane == 0) {
-      double *o = pair_out + 8ull * p;
-      double pw = s[2];
-      double fm = pw > 0 ? s[3] / pw : 0.0, tm = pw > 0 ? s[5] / pw : 0.0;
-      double fv = pw > 0 ? s[4] / pw - fm * fm : 0.0, tv = pw > 0 ? s[6] / pw - tm * tm : 0.0;
-      o[0] = s[0]; o[1] = s[1]; o[2] = pw;
-      o[3] = fm; o[4] = sqrt(fmax(fv, 0.0));
-      o[5] = tm; o[6] = sqrt(fmax(tv, 0.0));
-      o[7] = (double)(e - b);
-    }
+    double *o = pair_out + 8ull * (tx * n_rx + rx);
+    double pw = s[2];
+    double fm = pw > 0 ? s[3] / pw : 0.0, tm = pw > 0 ? s[5] / pw : 0.0;
+    double fv = pw > 0 ? s[4] / pw - fm * fm : 0.0, tv = pw > 0 ? s[6] / pw - tm * tm : 0.0;
+    o[0] = s[0]; o[1] = s[1]; o[2] = pw;
+    o[3] = fm; o[4] = sqrt(fmax(fv, 0.0));
+    o[5] = tm; o[6] = sqrt(fmax(tv, 0.0));
+    o[7] = (double)(e - i);
   }
 }
 
@@ -462,15 +451,13 @@ void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint3
 }
 
 void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
-                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, uint32_t *seg_begin,
-                   uint32_t *seg_end, double *pair_out, double *rx_out, cudaStream_t s) {
+                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, double *pair_out,
+                   double *rx_out, cudaStream_t s) {
   uint32_t np = n_tx * n_rx;
-  cudaMemsetAsync(seg_begin, 0, sizeof(uint32_t) * np, s);
-  cudaMemsetAsync(seg_end, 0, sizeof(uint32_t) * np, s);
-  emrt::note_launch(), k_pair_bounds<<<152 * 8, 256, 0, s>>>(rec, n, cap, n_tx, n_rx, seg_begin, seg_end);
-  emrt::note_launch(), k_pair_reduce<<<ceil_div(np, 8) < 152 * 16 ? ceil_div(np, 8) : 152 * 16, 256, 0, s>>>(
-      path_out, seg_begin, seg_end, np, pair_out);
-  if (rx_out) emrt::note_launch(), k_rx_power<<<ceil_div(n_rx, 256), 256, 0, s>>>(pair_out, n_tx, n_rx, tx_power_w, rx_out);
+  cudaMemsetAsync(pair_out, 0, sizeof(double) * 8 * np, s);
+  emrt::note_launch(), k_pair_seq<<<152 * 8, 256, 0, s>>>(rec, n, cap, n_tx, n_rx, path_out, pair_out);
+  if (rx_out)
+    emrt::note_launch(), k_rx_power<<<ceil_div(n_rx, 256), 256, 0, s>>>(pair_out, n_tx, n_rx, tx_power_w, rx_out);
 }
 
 int adjoint_grid() { return 152 * 4; }

@@ -12,13 +12,14 @@ struct MatView {
 // per-path (Re a, Im a, tau, f_D) for min(*n, cap) canonical records
 void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                   uint32_t cap, double freq, double *path_out, cudaStream_t s);
-// per (tx, rx) statistics and per-receiver powers; seg_begin/seg_end are
-// scratch of n_tx * n_rx words each
+// per (tx, rx) statistics (zeros for pairs without paths) and per-receiver
+// powers; records must be in canonical order
 void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
-                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, uint32_t *seg_begin,
-                   uint32_t *seg_end, double *pair_out, double *rx_out, cudaStream_t s);
-// adjoint: grad (2 n_mat + 3 n_tx doubles, layout eps | sigma | tx xyz),
-// partial: per-block scratch of grid * (2 n_mat + 3 n_tx) doubles
+                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, double *pair_out,
+                   double *rx_out, cudaStream_t s);
+// adjoint: gradients w.r.t. eps_r [n_mat], sigma [n_mat], tx position
+// [n_tx][3]; `partial` is per-path scratch of cap * (3 + 2 EMRT_MAX_DEPTH)
+// doubles (tangent contributions), reduced per parameter in a fixed order
 void launch_field_adjoint(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                           uint32_t cap, double freq, const double *dloss_dh, uint32_t n_rx,
                           double *partial, double *grad_eps, double *grad_sigma, double *grad_tx,

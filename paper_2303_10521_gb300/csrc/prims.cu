@@ -1,4 +1,6 @@
 // LSD radix sort, exclusive scan (fixed grids, device-side counts).
+#include <algorithm>
+
 #include "prims.cuh"
 
 namespace emrt {
@@ -29,7 +31,39 @@ __global__ void __launch_bounds__(kPrimBlock) k_hist(const uint32_t *d_n, const 
   for (uint32_t i = lo + threadIdx.x; i < hi; i += kPrimBlock)
     atomicAdd(&sh[digit_of<W>(keys[i], pass)], 1u);
   __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = sh[threadIdx.x];
+  hist[blockIdx.x * 256 + threadIdx.x] = sh[threadIdx.x];
+}
+
+// Digit offsets from the block-major histogram hist[b][d] (G blocks):
+// offs[b][d] = sum_{d' < d} total[d'] + sum_{b' < b} hist[b'][d].  1024
+// threads: four groups of 256 (one thread per digit) split the G rows, so
+// every row access is a coalesced 1 KB load.
+__global__ void __launch_bounds__(1024) k_digit_offsets(uint32_t *hist, int G) {
+  __shared__ uint32_t part[4][256];
+  __shared__ uint32_t base[256];
+  const int d = threadIdx.x & 255, grp = threadIdx.x >> 8;
+  const int per = (G + 3) / 4, b0 = min(G, grp * per), b1 = min(G, b0 + per);
+  uint32_t s = 0;
+#pragma unroll 4
+  for (int b = b0; b < b1; b++) s += hist[b * 256 + d];
+  part[grp][d] = s;
+  __syncthreads();
+  if (grp == 0) base[d] = part[0][d] + part[1][d] + part[2][d] + part[3][d];
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    uint32_t t = (grp == 0 && d >= off) ? base[d - off] : 0;
+    __syncthreads();
+    if (grp == 0) base[d] += t;
+    __syncthreads();
+  }
+  uint32_t run = base[d] - (part[0][d] + part[1][d] + part[2][d] + part[3][d]);
+  for (int q = 0; q < grp; q++) run += part[q][d];
+#pragma unroll 4
+  for (int b = b0; b < b1; b++) {
+    uint32_t t = hist[b * 256 + d];
+    hist[b * 256 + d] = run;
+    run += t;
+  }
 }
 
 // exclusive scan of n (<= a few 100k) words in one block of 1024 threads
@@ -66,7 +100,7 @@ __global__ void __launch_bounds__(kPrimBlock) k_scatter(const uint32_t *d_n, con
   __shared__ uint32_t s_tot[256];
   __shared__ uint32_t s_cnt[NW][256];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  s_base[t] = offs[t * gridDim.x + blockIdx.x];
+  s_base[t] = offs[blockIdx.x * 256 + t];
   uint32_t lo, hi;
   block_range(*d_n, lo, hi);
   for (uint32_t r0 = lo; r0 < hi; r0 += kPrimBlock) {
@@ -159,26 +193,28 @@ __global__ void __launch_bounds__(kPrimBlock) k_scan_down(const uint32_t *d_n, c
 
 template <int W>
 bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *keys2,
-                uint32_t *vals2, int bits, uint32_t *hist, cudaStream_t s) {
+                uint32_t *vals2, int bits, uint32_t *hist, cudaStream_t s, uint64_t max_n) {
   int passes = (bits + 7) / 8;
+  // blocks: about 8 tiles of 256 keys each for the largest possible count
+  int G = (int)std::min<uint64_t>(kPrimGrid, std::max<uint64_t>(1, (max_n + 2047) / 2048));
   bool alt = false;
   for (int p = 0; p < passes; p++) {
     KeyW<W> *ki = alt ? keys2 : keys, *ko = alt ? keys : keys2;
     uint32_t *vi = alt ? vals2 : vals, *vo = alt ? vals : vals2;
-    emrt::note_launch(), k_hist<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
-    emrt::note_launch(), k_scan_single<<<1, 1024, 0, s>>>(hist, 256 * kPrimGrid, nullptr);
-    emrt::note_launch(), k_scatter<W><<<kPrimGrid, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
+    emrt::note_launch(), k_hist<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
+    emrt::note_launch(), k_digit_offsets<<<1, 1024, 0, s>>>(hist, G);
+    emrt::note_launch(), k_scatter<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
     alt = !alt;
   }
   return alt;
 }
 
 template bool radix_sort<1>(const uint32_t *, KeyW<1> *, uint32_t *, KeyW<1> *, uint32_t *,
-                            int, uint32_t *, cudaStream_t);
+                            int, uint32_t *, cudaStream_t, uint64_t);
 template bool radix_sort<2>(const uint32_t *, KeyW<2> *, uint32_t *, KeyW<2> *, uint32_t *,
-                            int, uint32_t *, cudaStream_t);
+                            int, uint32_t *, cudaStream_t, uint64_t);
 template bool radix_sort<4>(const uint32_t *, KeyW<4> *, uint32_t *, KeyW<4> *, uint32_t *,
-                            int, uint32_t *, cudaStream_t);
+                            int, uint32_t *, cudaStream_t, uint64_t);
 
 void exclusive_scan(const uint32_t *d_n, const uint32_t *in, uint32_t *out, uint32_t *d_total,
                     uint32_t *partial, cudaStream_t s) {

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBounceBlock) k_bounce(BounceLaunch L) {
       o = f3(g.tx_pos[tx]);
       Lacc = 0.f;
     } else {
-      Ray R = L.rin[i];
+      Ray R = L.rin[L.order ? L.order[i] : i];
       o = f3(R.o_L);
       Lacc = R.o_L.w;
       d = f3(R.d_id);
@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(kBounceBlock) k_bounce(BounceLaunch L) {
               fmaxf(d.y * (rlo.y - o.y), d.y * (rhi.y - o.y)) +
               fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
     }
-    if (t_end > 0.f) {
+    {
+      t_end = fmaxf(t_end, 0.f);
       float rmax = L.kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
       const int b = L.b;
       query_rx(g.rxb, q, t_end, Lacc, L.kappa, rmax, stk, stt, st, [&](uint32_t rx) {
@@ -428,6 +429,29 @@ __global__ void k_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, 
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 
+__device__ inline uint32_t spread7(uint32_t v) {  // 7 bits -> every third bit
+  uint32_t x = v & 0x7fu;
+  x = (x | (x << 8)) & 0x0000f00fu;
+  x = (x | (x << 4)) & 0x000c30c3u;
+  x = (x | (x << 2)) & 0x00249249u;
+  return x;
+}
+
+__global__ void k_ray_keys(const Ray *r, const uint32_t *n, const float4 *bb, KeyW<1> *keys,
+                           uint32_t *vals) {
+  uint32_t cnt = *n;
+  float4 lo = bb[0], hi = bb[1];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    float4 o = r[i].o_L, d = r[i].d_id;
+    uint32_t c[3];
+    float q[3] = {(o.x - lo.x) / (hi.x - lo.x), (o.y - lo.y) / (hi.y - lo.y), (o.z - lo.z) / (hi.z - lo.z)};
+    for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 127.f);
+    uint32_t m = spread7(c[0]) << 2 | spread7(c[1]) << 1 | spread7(c[2]);
+    keys[i].w[0] = m << 11 | (oct_code(make_float3(d.x, d.y, d.z)) >> 21);
+    vals[i] = i;
+  }
+}
+
 int g_bounce_grid = 0;
 
 }  // namespace
@@ -464,9 +488,14 @@ void build_dir_table(uint64_t n_rays, uint64_t offset, uint64_t stride, uint32_t
   if (!count) return;
   emrt::note_launch(), k_dir_codes<<<ceil_div(count, 256), 256, 0, s>>>(n_rays, offset, stride, count, k0, v0);
   emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(d_n, count);
-  bool alt = radix_sort<1>(d_n, k0, v0, k1, v1, 32, hist, s);
+  bool alt = radix_sort<1>(d_n, k0, v0, k1, v1, 32, hist, s, count);
   emrt::note_launch(), k_dir_table<<<ceil_div(count, 256), 256, 0, s>>>(n_rays, offset, stride, count, alt ? v1 : v0,
                                                    table);
+}
+
+void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1> *keys,
+                     uint32_t *vals, cudaStream_t s) {
+  emrt::note_launch(), k_ray_keys<<<kPrimGrid * 8, 256, 0, s>>>(r, n, bbox, keys, vals);
 }
 
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s) {

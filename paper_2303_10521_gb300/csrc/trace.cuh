@@ -20,6 +20,7 @@ void build_dir_table(uint64_t n_rays, uint64_t offset, uint64_t stride, uint32_t
 struct BounceLaunch {
   GeomView g;
   const Ray *rin;        // bounce >= 1
+  const uint32_t *order; // optional permutation of rin (coherence sort)
   const uint32_t *n_in;  // device count of rin (bounce >= 1)
   uint32_t n_primary;    // n_tx * count (bounce 0)
   const float4 *dirs;
@@ -36,6 +37,11 @@ struct BounceLaunch {
 };
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s);
 int bounce_grid();  // persistent grid size (SMs x resident blocks)
+
+// Coherence keys of the *n rays: origin cell (7-bit Morton per axis in the
+// scene box) then direction bin (11 bits of the octahedral code).
+void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1> *keys,
+                     uint32_t *vals, cudaStream_t s);
 
 // Canonical keys of min(*n, cap) records; values = record index.
 void launch_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,

@@ -226,9 +226,9 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
   }
 }
 
-// Reception spheres: for every receiver p with closest-approach parameter
-// s = d.(p - o) in (0, t_end] and distance to the ray <= kappa (L + s), calls
-// emit(receiver id).  rmax bounds kappa (L + t_end).
+// Reception spheres: for every receiver p whose distance to the segment
+// o + s d, s in [0, t_end], is <= kappa (L + s) at the segment point nearest
+// to p, calls emit(receiver id).  rmax bounds kappa (L + t_end).
 template <typename F>
 __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, float L, float kappa,
                                 float rmax, int *stk, float *stt, TravStats &st, F &&emit) {
@@ -265,12 +265,10 @@ __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, fl
       float4 p = ldg4(b.prims + (uint32_t)(~node));
       st.rxs++;
       float3 w = f3(p) - r.o;
-      float s = dot3(w, r.d);
-      if (s > 0.f && s <= t_end) {
-        float3 q = w - r.d * s;
-        float rad = kappa * (L + s);
-        if (dot3(q, q) <= rad * rad) emit(__float_as_uint(p.w));
-      }
+      float s = fminf(fmaxf(dot3(w, r.d), 0.f), t_end);
+      float3 q = w - r.d * s;
+      float rad = kappa * (L + s);
+      if (dot3(q, q) <= rad * rad) emit(__float_as_uint(p.w));
     }
     if (sp == 0) return;
     node = stk[--sp];

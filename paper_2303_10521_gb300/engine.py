@@ -135,7 +135,7 @@ class Scene:
             "emrt_scene_update_dynamic")
 
     def trace_async(self, out: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
-                    keep_rejected=False, sort_rays=False, stream=None):
+                    keep_rejected=False, sort_rays=True, stream=None):
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
@@ -146,13 +146,14 @@ class Scene:
                 "emrt_trace")
 
     def trace(self, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
-              keep_rejected=False, capacity=None, stream=None, retries=3) -> Paths:
+              keep_rejected=False, capacity=None, stream=None, retries=3,
+              sort_rays=True) -> Paths:
         """Plain discovery; grows scratch and output on capacity errors."""
         cap = capacity or max(4096, 8 * self.n_tx * self.n_rx)
         for _ in range(retries + 1):
             out = Paths(cap, self.device)
             self.trace_async(out, n_rays, max_depth, offset, stride, count, keep_rejected,
-                             stream=stream)
+                             sort_rays=sort_rays, stream=stream)
             try:
                 self.last_stats = self.sync(stream)
                 return out
