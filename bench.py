@@ -391,7 +391,7 @@ def main():
         g.update(cframes[k])
         g.trace_async(fresh, sort_rays=sort_rays)
         pp = g.channel(fresh, sc.freqs[0]).rx[:, 0].cpu().numpy()
-        g.trace_async(fresh, n_rays=sc.n_rays - 1, sort_rays=sort_rays)
+        g.trace_async(fresh, n_rays=int(sc.n_rays * 0.9), sort_rays=sort_rays)
         pq = g.channel(fresh, sc.freqs[0]).rx[:, 0].cpu().numpy()
         g.sync()
         acc_c.append(agree(cached_rx[k - 1].cpu().numpy(), pp))
@@ -404,8 +404,9 @@ def main():
                    "power_recall_min": float(acc_c[:, 0].min()),
                    "frac_rx_over_0p5db": float(acc_c[:, 1].mean()),
                    "median_abs_db": float(acc_c[:, 2].mean())},
-        "plain_other_ray_set": {"note": "plain retrace with N - 1 rays (a different, equally dense "
-                                        "Fibonacci set) against the same reference",
+        "plain_other_ray_set": {"note": "plain retrace with 0.9 N rays (another Fibonacci set of "
+                                        "similar density) against the same reference: the "
+                                        "ray-set variability of the plain method itself",
                                 "power_recall_mean": float(acc_p[:, 0].mean()),
                                 "power_recall_min": float(acc_p[:, 0].min()),
                                 "frac_rx_over_0p5db": float(acc_p[:, 1].mean()),

@@ -242,6 +242,41 @@ typedef struct {
  * first error recorded since the last emrt_sync and fills *st if non-NULL. */
 emrt_status emrt_sync(emrt_scene sc, emrt_stream s, emrt_stats *st);
 
+/* ---------------------------------------------------------------------
+ * Batched discovery over many scenes of uneven size (spec: batching;
+ * the paper runs one scene at a time).  One persistent traversal launch per
+ * bounce serves the rays of every scene of the batch; deduplication,
+ * acceptance and the scatter to each scene's output follow once.  The launch
+ * sequence is captured into a CUDA graph on the first emrt_batch_trace and
+ * replayed afterwards.  Limits: <= 64 scenes, <= 16 transmitters per scene,
+ * <= 2^22 rays per transmitter. */
+typedef struct emrt_batch_s *emrt_batch;
+
+#define EMRT_BATCH_AUTOTUNE 0x1u /* time every traversal variant (block size x
+                                    rays fetched per warp, coherence sort on or
+                                    off) on this batch and keep the fastest;
+                                    the choice is cached in the JSON file
+                                    $EMRT_AUTOTUNE_CACHE (default
+                                    $HOME/.emrt_autotune.json) and reused */
+
+/* scenes[i] must have been updated (emrt_scene_update_dynamic) and keeps its
+ * transmitter count for the life of the batch; params[i] and outs[i] are the
+ * ray set and the caller-owned output of scene i (as for emrt_trace).  The
+ * arrays are copied; the scenes and output buffers must outlive the batch.
+ * Allocates the batch's scratch and direction tables; synchronises. */
+emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n,
+                              const emrt_trace_params *params, emrt_paths *outs,
+                              uint32_t flags, emrt_stream s, emrt_batch *out);
+/* Discovery, deduplication and acceptance for every scene with the current
+ * poses (the same result as emrt_trace on each scene).  Asynchronous; the
+ * first call captures the graph. */
+emrt_status emrt_batch_trace(emrt_batch b, emrt_stream s);
+/* Waits and reports errors as emrt_sync (stats summed over the batch). */
+emrt_status emrt_batch_sync(emrt_batch b, emrt_stream s, emrt_stats *st);
+/* Human-readable traversal variant chosen for the batch. */
+emrt_status emrt_batch_config(emrt_batch b, char *buf, uint32_t len);
+void emrt_batch_destroy(emrt_batch b);
+
 const char *emrt_status_string(emrt_status e);
 
 /* Number of kernel launches this library has issued in this process

@@ -20,6 +20,7 @@ TRACE_KEEP_REJECTED = 0x1
 TRACE_SORT_RAYS = 0x2
 REVALIDATE_KEEP = 0x1
 NOALLOC_MAX_PATHS = 65536
+BATCH_AUTOTUNE = 0x1
 
 vp, u32, u64, dbl = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
 
@@ -79,6 +80,12 @@ SIGNATURES = {
     "emrt_channel_backward_noalloc": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials),
                                                 dbl, vp, vp, vp, vp, vp]),
     "emrt_sync": (C.c_int, [vp, vp, C.POINTER(Stats)]),
+    "emrt_batch_create": (C.c_int, [C.POINTER(vp), u32, C.POINTER(TraceParams),
+                                    C.POINTER(PathsC), u32, vp, C.POINTER(vp)]),
+    "emrt_batch_trace": (C.c_int, [vp, vp]),
+    "emrt_batch_sync": (C.c_int, [vp, vp, C.POINTER(Stats)]),
+    "emrt_batch_config": (C.c_int, [vp, C.c_char_p, u32]),
+    "emrt_batch_destroy": (None, [vp]),
     "emrt_status_string": (C.c_char_p, [C.c_int]),
     "emrt_kernel_launches": (u64, []),
 }

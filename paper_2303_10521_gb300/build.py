@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libemrt.so")
-UNITS = ["prims.cu", "bvh.cu", "trace.cu", "field.cu", "api.cu"]
+UNITS = ["prims.cu", "bvh.cu", "trace.cu", "field.cu", "api.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,53 +10,9 @@
 #include "bvh.cuh"
 #include "field.cuh"
 #include "trace.cuh"
+#include "scene.cuh"
 
 using namespace emrt;
-
-struct emrt_scene_s {
-  int device = 0;
-  uint32_t Fs = 0, T = 0, V = 0, NV = 0, max_rx = 0, max_tx = 0, veh_mat = 0;
-  uint32_t rebuild_every = 10, n_updates = 0;
-  double4 *face_plane = nullptr;
-  uint4 *face_info = nullptr;
-  float4 *face_vert = nullptr;
-  float4 *bbox = nullptr;  // [4]: lo, hi, scratch
-  BVHBuf stat, dyn, rxb;
-  float4 *veh_half = nullptr, *veh_lo = nullptr, *veh_hi = nullptr, *veh_vel = nullptr;
-  float4 *rx_pos = nullptr, *rx_vel = nullptr, *tx_pos = nullptr, *tx_vel = nullptr;
-  uint32_t n_rx = 0, n_tx = 0;
-  bool updated = false;
-  Counters *ctr = nullptr;
-  uint32_t *hist = nullptr, *partial = nullptr;
-  // primary direction tables, one per recently used ray set (LRU)
-  struct DirTable {
-    uint64_t n = 0, off = 0, stride = 0, cap = 0, last_use = 0;
-    uint32_t count = 0;
-    float4 *dirs = nullptr;
-  } dt[4];
-  uint64_t dt_clock = 0;
-  uint32_t *dt_scratch = nullptr;  // key/value scratch for building a table
-  uint64_t dt_scratch_cap = 0;
-  // ray ping-pong buffers and the coherence-sort scratch
-  Ray *rays[2] = {nullptr, nullptr};
-  uint64_t ray_cap = 0;
-  KeyW<1> *rkeys[2] = {nullptr, nullptr};
-  uint32_t *rvals[2] = {nullptr, nullptr};
-  uint64_t rsort_cap = 0;
-  // candidate and path scratch
-  uint32_t cand_cap = 0, want_cand = 0;
-  uint32_t *cand = nullptr, *uniq = nullptr, *head = nullptr, *pos = nullptr;
-  KeyW<4> *keys[2] = {nullptr, nullptr};
-  uint32_t *vals[2] = {nullptr, nullptr};
-  // adjoint scratch
-  double *contrib = nullptr;
-  uint64_t contrib_cap = 0;
-  emrt_status sticky = EMRT_OK;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t evb[2 * (EMRT_MAX_DEPTH + 1)] = {};  // around each k_bounce launch
-  uint32_t ev_bounces = 0;
-  bool ev_recorded = false;
-};
 
 namespace emrt {
 static std::atomic<unsigned long long> g_launches{0};
@@ -149,29 +105,6 @@ __global__ void k_check_cand(Counters *c, uint32_t cap) {
 __global__ void k_publish_count(const Counters *c, uint32_t *count) { *count = c->n_accepted; }
 
 __global__ void k_clamp_count(const uint32_t *n, uint32_t cap, uint32_t *out) { *out = min(*n, cap); }
-
-GeomView geom(const emrt_scene_s *s) {
-  GeomView g;
-  g.stat = s->stat.view();
-  g.dyn = s->dyn.view();
-  g.rxb = s->rxb.view();
-  g.face_plane = s->face_plane;
-  g.face_info = s->face_info;
-  g.face_vert = s->face_vert;
-  g.veh_lo = s->veh_lo;
-  g.veh_hi = s->veh_hi;
-  g.veh_vel = s->veh_vel;
-  g.rx_pos = s->rx_pos;
-  g.rx_vel = s->rx_vel;
-  g.tx_pos = s->tx_pos;
-  g.tx_vel = s->tx_vel;
-  g.n_static_faces = s->Fs;
-  g.n_veh = s->V;
-  g.n_rx = s->n_rx;
-  g.n_tx = s->n_tx;
-  g.veh_mat = s->veh_mat;
-  return g;
-}
 
 cudaError_t ensure_cand(emrt_scene_s *s, uint64_t need) {
   if (need <= s->cand_cap && s->cand) return cudaSuccess;

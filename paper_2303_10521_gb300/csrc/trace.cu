@@ -95,8 +95,15 @@ __device__ inline void add_u64(unsigned long long *p, unsigned long long v) {
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(p, v);
 }
 
-__global__ void __launch_bounds__(kBounceBlock) k_bounce(BounceLaunch L) {
-  const GeomView &g = L.g;
+// Closest-hit traversal of one bounce for every ray (persistent threads: each
+// warp takes FETCH rays at a time from a global cursor).  BATCH: rays of many
+// scenes, each ray's scene read from the table; otherwise the single scene in
+// L.g.  Per ray: nearest hit over the static triangles and the vehicle
+// boxes, reception-sphere detections on the traced segment (appended as
+// candidates), and the specular continuation (appended to the next buffer).
+template <bool BATCH, int BLOCK, int FETCH>
+__global__ void __launch_bounds__(BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
+                                                  uint32_t n_scenes) {
   int stk[kStack];
   float stt[kStack];
   TravStats st;
@@ -104,82 +111,108 @@ __global__ void __launch_bounds__(kBounceBlock) k_bounce(BounceLaunch L) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t n_items = L.b == 0 ? L.n_primary : *L.n_in;
   float3 rlo, rhi;
-  rx_bounds(g.rxb, rlo, rhi);
+  if (!BATCH) rx_bounds(L.g.rxb, rlo, rhi);
   const uint32_t NO = EMRT_NO_FACE;
   for (;;) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(L.work, 32u);
+    if (lane == 0) base = atomicAdd(L.work, (uint32_t)FETCH);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_items) break;
-    uint32_t i = base + lane;
-    if (i >= n_items) continue;
-    segs++;
-    float3 o, d;
-    float Lacc;
-    uint32_t tx, j;
-    uint32_t fc[EMRT_MAX_DEPTH] = {NO, NO, NO, NO};
-    if (L.b == 0) {
-      tx = i / L.count;
-      uint32_t k = i - tx * L.count;
-      float4 dj = L.dirs[k];
-      d = f3(dj);
-      j = __float_as_uint(dj.w);
-      o = f3(g.tx_pos[tx]);
-      Lacc = 0.f;
-    } else {
-      Ray R = L.rin[L.order ? L.order[i] : i];
-      o = f3(R.o_L);
-      Lacc = R.o_L.w;
-      d = f3(R.d_id);
-      uint32_t id = __float_as_uint(R.d_id.w);
-      tx = id >> 24;
-      j = id & 0xffffffu;
-      fc[0] = R.faces.x; fc[1] = R.faces.y; fc[2] = R.faces.z; fc[3] = R.faces.w;
-    }
-    uint32_t prev = L.b > 0 ? fc[L.b - 1] : NO;
-    RayQ q;
-    ray_setup(q, o, d);
-    float tbest = FLT_MAX;
-    uint32_t face = NO;
-    trace_tris<false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
-    uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
-    trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
-    bool hit = face != NO;
-    float t_end;
-    if (hit) {
-      t_end = tbest;
-    } else {  // escaped: the furthest projection of the receiver bounds
-      t_end = fmaxf(d.x * (rlo.x - o.x), d.x * (rhi.x - o.x)) +
-              fmaxf(d.y * (rlo.y - o.y), d.y * (rhi.y - o.y)) +
-              fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
-    }
-    {
+    for (uint32_t sub = 0; sub < (uint32_t)FETCH; sub += 32) {
+      uint32_t i = base + sub + lane;
+      if (i >= n_items) break;
+      segs++;
+      float3 o, d;
+      float Lacc;
+      uint32_t tx, j, sc = 0;
+      uint32_t fc[EMRT_MAX_DEPTH] = {NO, NO, NO, NO};
+      if (L.b == 0) {
+        uint32_t local = i, count = L.count;
+        const float4 *dirs = L.dirs;
+        if (BATCH) {  // scene of a primary item: last scene whose range starts <= i
+          uint32_t lo = 0, hi = n_scenes;
+          while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (tab[mid].prim_begin <= i) lo = mid;
+            else hi = mid;
+          }
+          sc = lo;
+          local = i - tab[sc].prim_begin;
+          count = tab[sc].count;
+          dirs = tab[sc].dirs;
+        }
+        tx = local / count;
+        uint32_t k = local - tx * count;
+        float4 dj = dirs[k];
+        d = f3(dj);
+        j = __float_as_uint(dj.w);
+        o = f3((BATCH ? tab[sc].g : L.g).tx_pos[tx]);
+        Lacc = 0.f;
+      } else {
+        Ray R = L.rin[L.order ? L.order[i] : i];
+        o = f3(R.o_L);
+        Lacc = R.o_L.w;
+        d = f3(R.d_id);
+        uint32_t id = __float_as_uint(R.d_id.w);
+        if (BATCH) {
+          sc = id >> 26;
+          tx = (id >> 22) & 15u;
+          j = id & 0x3fffffu;
+        } else {
+          tx = id >> 24;
+          j = id & 0xffffffu;
+        }
+        fc[0] = R.faces.x; fc[1] = R.faces.y; fc[2] = R.faces.z; fc[3] = R.faces.w;
+      }
+      const GeomView &g = BATCH ? tab[sc].g : L.g;
+      const float kappa = BATCH ? tab[sc].kappa : L.kappa;
+      const int K = BATCH ? (int)tab[sc].K : L.K;
+      if (BATCH) rx_bounds(g.rxb, rlo, rhi);
+      uint32_t prev = L.b > 0 ? fc[L.b - 1] : NO;
+      RayQ q;
+      ray_setup(q, o, d);
+      float tbest = FLT_MAX;
+      uint32_t face = NO;
+      trace_tris<false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+      uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
+      trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
+      bool hit = face != NO;
+      float t_end;
+      if (hit) {
+        t_end = tbest;
+      } else {  // escaped: the furthest projection of the receiver bounds
+        t_end = fmaxf(d.x * (rlo.x - o.x), d.x * (rhi.x - o.x)) +
+                fmaxf(d.y * (rlo.y - o.y), d.y * (rhi.y - o.y)) +
+                fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
+      }
       t_end = fmaxf(t_end, 0.f);
-      float rmax = L.kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
-      const int b = L.b;
-      query_rx(g.rxb, q, t_end, Lacc, L.kappa, rmax, stk, stt, st, [&](uint32_t rx) {
+      float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
+      const uint32_t b = (uint32_t)L.b;
+      const uint32_t w0 = BATCH ? (sc << 8 | tx) : tx;
+      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, [&](uint32_t rx) {
         uint32_t slot = warp_append(L.n_cand);
         if (slot < L.cand_cap) {
           uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
-          c[0] = make_uint4(tx, rx, (uint32_t)b, fc[0]);
+          c[0] = make_uint4(w0, rx, b, fc[0]);
           c[1] = make_uint4(fc[1], fc[2], fc[3], j);
         }
       });
-    }
-    if (hit && L.b < L.K) {
-      float3 n = face_normal_f(g, face);
-      float3 p = o + d * tbest;
-      float dn = 2.f * dot3(d, n);
-      float3 r = d - n * dn;
-      float inv = rsqrtf(dot3(r, r));
-      r = r * inv;
-      fc[L.b] = face;
-      uint32_t slot = warp_append(L.n_out);
-      Ray R;
-      R.o_L = make_float4(p.x, p.y, p.z, Lacc + tbest);
-      R.d_id = make_float4(r.x, r.y, r.z, __uint_as_float(tx << 24 | j));
-      R.faces = make_uint4(fc[0], fc[1], fc[2], fc[3]);
-      L.rout[slot] = R;
+      if (hit && L.b < K) {
+        float3 n = face_normal_f(g, face);
+        float3 p = o + d * tbest;
+        float dn = 2.f * dot3(d, n);
+        float3 r = d - n * dn;
+        float inv = rsqrtf(dot3(r, r));
+        r = r * inv;
+        fc[L.b] = face;
+        uint32_t slot = warp_append(L.n_out);
+        Ray R;
+        R.o_L = make_float4(p.x, p.y, p.z, Lacc + tbest);
+        uint32_t id = BATCH ? (sc << 26 | tx << 22 | j) : (tx << 24 | j);
+        R.d_id = make_float4(r.x, r.y, r.z, __uint_as_float(id));
+        R.faces = make_uint4(fc[0], fc[1], fc[2], fc[3]);
+        L.rout[slot] = R;
+      }
     }
   }
   __syncwarp();
@@ -213,7 +246,8 @@ __global__ void k_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap
     uint32_t depth = a.z & 15u;
     uint32_t f[4] = {a.w, b.x, b.y, b.z};
     U128 k = {0ull, 0ull};
-    push_bits(k, a.x, kl.bt);
+    push_bits(k, a.x >> 8, kl.bs);   // scene (batched records; 0 bits otherwise)
+    push_bits(k, a.x & 255u, kl.bt);
     push_bits(k, a.y, kl.br);
     push_bits(k, depth, 3);
     for (int q = 0; q < kl.K; q++) push_bits(k, q < (int)depth ? f[q] : 0u, kl.bf);
@@ -308,8 +342,10 @@ __device__ inline double inface_margin(const GeomView &g, uint32_t f, D3 P, D3 n
 
 constexpr double kMargin = 1e-4;
 
-__global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView g, uint32_t *rec,
-                                                         const uint32_t *n, Counters *ctr) {
+template <bool BATCH>
+__global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView G, const BatchScene *__restrict__ tab,
+                                                         uint32_t *rec, const uint32_t *n,
+                                                         Counters *ctr) {
   int stk[kStack];
   float stt[kStack];
   TravStats st;
@@ -321,7 +357,9 @@ __global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView g, uint32_t *r
     uint4 a = r[0], b = r[1];
     uint32_t k = a.z & 15u;
     uint32_t f[EMRT_MAX_DEPTH] = {a.w, b.x, b.y, b.z};
-    bool ok = k <= EMRT_MAX_DEPTH && a.x < g.n_tx && a.y < g.n_rx;
+    const uint32_t sc = BATCH ? (a.x >> 8) : 0u, tx = BATCH ? (a.x & 255u) : a.x;
+    const GeomView &g = BATCH ? tab[sc].g : G;
+    bool ok = k <= EMRT_MAX_DEPTH && tx < g.n_tx && a.y < g.n_rx;
     uint32_t nf = g.n_static_faces + 6u * g.n_veh;
     for (uint32_t q = 0; ok && q < k; q++) ok = f[q] < nf && (q == 0 || f[q] != f[q - 1]);
     bool marg = false;
@@ -330,7 +368,7 @@ __global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView g, uint32_t *r
       D3 I[EMRT_MAX_DEPTH + 1];
       D3 nn[EMRT_MAX_DEPTH];
       double dd[EMRT_MAX_DEPTH];
-      I[0] = tod(f3(g.tx_pos[a.x]));
+      I[0] = tod(f3(g.tx_pos[tx]));
       for (uint32_t q = 0; q < k; q++) {
         plane_of(g, f[q], nn[q], dd[q]);
         I[q + 1] = I[q] - nn[q] * (2.0 * (dotd(nn[q], I[q]) - dd[q]));
@@ -429,6 +467,50 @@ __global__ void k_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, 
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 
+__global__ void k_batch_first(const uint32_t *rec, const uint32_t *n, const uint32_t *flag,
+                              const uint32_t *pos, uint32_t *first, uint32_t *cnt) {
+  uint32_t c = *n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    uint32_t sc = rec[8ull * i] >> 8;
+    if (sc >= kBatchMaxScenes) continue;
+    atomicMin(&first[sc], pos[i]);
+    atomicAdd(&cnt[sc], 1u);
+  }
+}
+
+__global__ void k_batch_write(const BatchScene *tab, uint32_t n_scenes, const uint32_t *rec,
+                              const uint32_t *n, const uint32_t *flag, const uint32_t *pos,
+                              const uint32_t *first, const uint32_t *cnt, Counters *ctr) {
+  uint32_t c = *n;
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_scenes) {
+    *tab[t].out_count = cnt[t];
+    if (cnt[t] > tab[t].out_cap) atomicOr(&ctr->err, ERR_PATH_OVERFLOW);
+  }
+  for (uint32_t i = t; i < c; i += gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    const uint4 *src = reinterpret_cast<const uint4 *>(rec + 8ull * i);
+    uint4 a = src[0], b = src[1];
+    uint32_t sc = a.x >> 8;
+    if (sc >= n_scenes) continue;
+    uint32_t p = pos[i] - first[sc];
+    if (p >= tab[sc].out_cap) continue;
+    a.x &= 255u;
+    uint4 *dst = reinterpret_cast<uint4 *>(tab[sc].out_rec + 8ull * p);
+    dst[0] = a;
+    dst[1] = b;
+  }
+}
+
+__global__ void k_batch_init(uint32_t *first, uint32_t *cnt) {
+  uint32_t t = threadIdx.x;
+  if (t < kBatchMaxScenes) {
+    first[t] = 0xffffffffu;
+    cnt[t] = 0u;
+  }
+}
+
 __device__ inline uint32_t spread7(uint32_t v) {  // 7 bits -> every third bit
   uint32_t x = v & 0x7fu;
   x = (x | (x << 8)) & 0x0000f00fu;
@@ -438,7 +520,7 @@ __device__ inline uint32_t spread7(uint32_t v) {  // 7 bits -> every third bit
 }
 
 __global__ void k_ray_keys(const Ray *r, const uint32_t *n, const float4 *bb, KeyW<1> *keys,
-                           uint32_t *vals) {
+                           uint32_t *vals, bool batched) {
   uint32_t cnt = *n;
   float4 lo = bb[0], hi = bb[1];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
@@ -447,7 +529,9 @@ __global__ void k_ray_keys(const Ray *r, const uint32_t *n, const float4 *bb, Ke
     float q[3] = {(o.x - lo.x) / (hi.x - lo.x), (o.y - lo.y) / (hi.y - lo.y), (o.z - lo.z) / (hi.z - lo.z)};
     for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 127.f);
     uint32_t m = spread7(c[0]) << 2 | spread7(c[1]) << 1 | spread7(c[2]);
-    keys[i].w[0] = m << 11 | (oct_code(make_float3(d.x, d.y, d.z)) >> 21);
+    uint32_t oc = oct_code(make_float3(d.x, d.y, d.z));
+    keys[i].w[0] = batched ? ((__float_as_uint(d.w) >> 26) << 26 | (m >> 1) << 6 | oc >> 26)
+                           : (m << 11 | oc >> 21);
     vals[i] = i;
   }
 }
@@ -456,18 +540,19 @@ int g_bounce_grid = 0;
 
 }  // namespace
 
-KeyLayout key_layout(uint32_t n_tx, uint32_t n_rx, uint32_t n_faces, int K) {
+KeyLayout key_layout(uint32_t n_tx, uint32_t n_rx, uint32_t n_faces, int K, uint32_t n_scenes) {
   auto bits = [](uint32_t v) {  // bits to hold 0..v-1
     int b = 0;
     while (b < 32 && (1ull << b) < (unsigned long long)v) b++;
     return b;
   };
   KeyLayout kl;
+  kl.bs = n_scenes > 1 ? bits(n_scenes) : 0;
   kl.bt = bits(n_tx);
   kl.br = bits(n_rx);
   kl.bf = bits(n_faces);
   kl.K = K;
-  kl.total = kl.bt + kl.br + 3 + K * kl.bf;
+  kl.total = kl.bs + kl.bt + kl.br + 3 + K * kl.bf;
   return kl;
 }
 
@@ -476,10 +561,64 @@ int bounce_grid() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bounce, kBounceBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bounce<false, kBounceBlock, 32>,
+                                                  kBounceBlock, 0);
     g_bounce_grid = sms * (per > 0 ? per : 1);
   }
   return g_bounce_grid;
+}
+
+namespace {
+struct Variant {
+  const char *name;
+  int block;
+  void (*kern)(BounceLaunch, const BatchScene *, uint32_t);
+  int grid;
+};
+Variant g_variants[] = {
+    {"block64_fetch32", 64, k_bounce<true, 64, 32>, 0},
+    {"block128_fetch32", 128, k_bounce<true, 128, 32>, 0},
+    {"block256_fetch32", 256, k_bounce<true, 256, 32>, 0},
+    {"block128_fetch128", 128, k_bounce<true, 128, 128>, 0},
+    {"block256_fetch64", 256, k_bounce<true, 256, 64>, 0},
+    {"block64_fetch128", 64, k_bounce<true, 64, 128>, 0},
+};
+constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
+}  // namespace
+
+int n_bounce_variants() { return kNumVariants; }
+const char *bounce_variant_name(int v) { return g_variants[v].name; }
+int bounce_variant_grid(int v) {
+  Variant &V = g_variants[v];
+  if (!V.grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, V.kern, V.block, 0);
+    V.grid = sms * (per > 0 ? per : 1);
+  }
+  return V.grid;
+}
+
+void launch_bounce_batched(int variant, const BounceLaunch &L, const BatchScene *tab,
+                           uint32_t n_scenes, cudaStream_t s) {
+  Variant &V = g_variants[variant];
+  emrt::note_launch(), V.kern<<<bounce_variant_grid(variant), V.block, 0, s>>>(L, tab, n_scenes);
+}
+
+void launch_accept_batched(const BatchScene *tab, uint32_t *rec, const uint32_t *n, Counters *ctr,
+                           cudaStream_t s) {
+  GeomView none{};
+  emrt::note_launch(), k_accept<true><<<kPrimGrid * 4, kBounceBlock, 0, s>>>(none, tab, rec, n, ctr);
+}
+
+void launch_batch_scatter(const BatchScene *tab, uint32_t n_scenes, const uint32_t *rec,
+                          const uint32_t *n, const uint32_t *flag, const uint32_t *pos,
+                          uint32_t *first, uint32_t *cnt, Counters *ctr, cudaStream_t s) {
+  emrt::note_launch(), k_batch_init<<<1, kBatchMaxScenes, 0, s>>>(first, cnt);
+  emrt::note_launch(), k_batch_first<<<kPrimGrid * 4, 256, 0, s>>>(rec, n, flag, pos, first, cnt);
+  emrt::note_launch(), k_batch_write<<<kPrimGrid * 4, 256, 0, s>>>(tab, n_scenes, rec, n, flag, pos,
+                                                                  first, cnt, ctr);
 }
 
 void build_dir_table(uint64_t n_rays, uint64_t offset, uint64_t stride, uint32_t count,
@@ -494,12 +633,12 @@ void build_dir_table(uint64_t n_rays, uint64_t offset, uint64_t stride, uint32_t
 }
 
 void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1> *keys,
-                     uint32_t *vals, cudaStream_t s) {
-  emrt::note_launch(), k_ray_keys<<<kPrimGrid * 8, 256, 0, s>>>(r, n, bbox, keys, vals);
+                     uint32_t *vals, cudaStream_t s, bool batched) {
+  emrt::note_launch(), k_ray_keys<<<kPrimGrid * 8, 256, 0, s>>>(r, n, bbox, keys, vals, batched);
 }
 
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s) {
-  emrt::note_launch(), k_bounce<<<grid, kBounceBlock, 0, s>>>(L);
+  emrt::note_launch(), k_bounce<false, kBounceBlock, 32><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);
 }
 
 void launch_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,
@@ -516,7 +655,7 @@ void launch_unique(const uint32_t *rec, const KeyW<4> *keys, const uint32_t *val
 }
 void launch_accept(const GeomView &g, uint32_t *rec, const uint32_t *n, Counters *ctr,
                    cudaStream_t s) {
-  emrt::note_launch(), k_accept<<<kPrimGrid * 4, kBounceBlock, 0, s>>>(g, rec, n, ctr);
+  emrt::note_launch(), k_accept<false><<<kPrimGrid * 4, kBounceBlock, 0, s>>>(g, nullptr, rec, n, ctr);
 }
 void launch_keep_flags(const uint32_t *rec, const uint32_t *n, int keep_all, uint32_t *flag,
                        cudaStream_t s) {

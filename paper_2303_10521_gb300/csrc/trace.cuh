@@ -6,9 +6,10 @@
 namespace emrt {
 
 struct KeyLayout {  // bit widths of the canonical 128-bit path key
-  int bt, br, bf, K, total;
+  int bs, bt, br, bf, K, total;  // bs: scene bits (batches), 0 otherwise
 };
-KeyLayout key_layout(uint32_t n_tx, uint32_t n_rx, uint32_t n_faces, int K);
+KeyLayout key_layout(uint32_t n_tx, uint32_t n_rx, uint32_t n_faces, int K,
+                     uint32_t n_scenes = 1);
 
 // Primary direction table for rays offset + stride*j, j < count: float4
 // (unit direction, j bits), ordered by an octahedral direction code so that
@@ -38,10 +39,45 @@ struct BounceLaunch {
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s);
 int bounce_grid();  // persistent grid size (SMs x resident blocks)
 
+// One scene of a batch (device table entry).  Batched rays pack
+// scene (6 bits) | tx (4 bits) | ray index (22 bits); batched candidate and
+// path records carry scene << 8 | tx in word 0 until they are written to the
+// scene's own output.
+struct BatchScene {
+  GeomView g;
+  const float4 *dirs;     // primary direction table of this scene
+  uint32_t count;         // rays per transmitter
+  uint32_t prim_begin;    // first global primary item of this scene
+  uint32_t n_primary;     // n_tx * count
+  uint32_t K;             // reflections
+  float kappa;            // reception radius factor
+  uint32_t *out_rec;      // caller's output records
+  uint32_t out_cap;
+  uint32_t *out_count;
+};
+constexpr uint32_t kBatchMaxScenes = 64, kBatchMaxTx = 16, kBatchMaxCount = 1u << 22;
+
+// Batched traversal variants (block size x rays fetched per warp); the
+// autotuner picks one.  variant in [0, n_bounce_variants()).
+int n_bounce_variants();
+const char *bounce_variant_name(int v);
+int bounce_variant_grid(int v);
+void launch_bounce_batched(int variant, const BounceLaunch &L, const BatchScene *tab,
+                           uint32_t n_scenes, cudaStream_t s);
+void launch_accept_batched(const BatchScene *tab, uint32_t *rec, const uint32_t *n, Counters *ctr,
+                           cudaStream_t s);
+// writes kept, sorted batched records to each scene's output (positions
+// relative to the scene's first kept record); first[] and cnt[] are
+// kBatchMaxScenes words of scratch
+void launch_batch_scatter(const BatchScene *tab, uint32_t n_scenes, const uint32_t *rec,
+                          const uint32_t *n, const uint32_t *flag, const uint32_t *pos,
+                          uint32_t *first, uint32_t *cnt, Counters *ctr, cudaStream_t s);
+
 // Coherence keys of the *n rays: origin cell (7-bit Morton per axis in the
 // scene box) then direction bin (11 bits of the octahedral code).
+// batched: scene (6 bits) | origin cell (20 bits) | direction bin (6 bits)
 void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1> *keys,
-                     uint32_t *vals, cudaStream_t s);
+                     uint32_t *vals, cudaStream_t s, bool batched = false);
 
 // Canonical keys of min(*n, cap) records; values = record index.
 void launch_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,

@@ -213,3 +213,60 @@ class Scene:
         self.last_stats = out
         N.check(code, "emrt_sync")
         return out
+
+
+class Batch:
+    """Batched discovery over several Scenes (wraps ``emrt_batch``): one
+    traversal launch per bounce for all scenes, replayed from a CUDA graph."""
+
+    def __init__(self, scenes, params=None, capacity=None, autotune=False, stream=None):
+        self.lib = N.load()
+        self.scenes = list(scenes)
+        n = len(self.scenes)
+        self.device = self.scenes[0].device
+        self.outs = []
+        ps = []
+        for i, sc in enumerate(self.scenes):
+            p = dict(n_rays=sc.desc.n_rays, max_depth=sc.desc.max_depth, offset=0, stride=1,
+                     count=0)
+            if params is not None:
+                p.update(params[i])
+            ps.append(N.TraceParams(int(p["max_depth"]), int(p["n_rays"]), int(p["offset"]),
+                                    int(p["stride"]), int(p["count"]), 0))
+            cap = capacity[i] if isinstance(capacity, (list, tuple)) else \
+                (capacity or max(4096, 8 * sc.n_tx * sc.n_rx))
+            self.outs.append(Paths(cap, self.device))
+        self._params = (N.TraceParams * n)(*ps)
+        self._outs = (N.PathsC * n)(*[o.c() for o in self.outs])
+        self._scenes = (C.c_void_p * n)(*[sc.h.value for sc in self.scenes])
+        h = C.c_void_p()
+        N.check(self.lib.emrt_batch_create(self._scenes, n, self._params, self._outs,
+                                           N.BATCH_AUTOTUNE if autotune else 0, _stream(stream),
+                                           C.byref(h)), "emrt_batch_create")
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                torch.cuda.synchronize(self.device)
+            except Exception:
+                pass
+            self.lib.emrt_batch_destroy(h)
+            self.h = None
+
+    def trace_async(self, stream=None):
+        N.check(self.lib.emrt_batch_trace(self.h, _stream(stream)), "emrt_batch_trace")
+
+    def sync(self, stream=None) -> dict:
+        st = N.Stats()
+        code = self.lib.emrt_batch_sync(self.h, _stream(stream), C.byref(st))
+        out = {f: getattr(st, f) for f, _ in N.Stats._fields_}
+        out["segments"] = list(st.segments)
+        N.check(code, "emrt_batch_sync")
+        return out
+
+    def config(self) -> str:
+        buf = C.create_string_buffer(128)
+        N.check(self.lib.emrt_batch_config(self.h, buf, 128), "emrt_batch_config")
+        return buf.value.decode()
