@@ -82,6 +82,8 @@ def lib():
         L.orc_trace.restype = i64
         L.orc_trace.argtypes = [vp, u64, C.c_int, u64, u64, u64, d, d, C.c_int,
                                 vp, i64, vp, vp]
+        L.orc_trace_list.restype = i64
+        L.orc_trace_list.argtypes = [vp, u64, C.c_int, vp, u64, d, d, C.c_int, vp, i64, vp, vp]
         L.orc_validate.argtypes = [vp, i64, vp, d, d, C.c_int, vp, vp, vp]
         L.orc_field.argtypes = [vp, i64, vp, d, C.c_int, vp, vp, vp]
         L.orc_fresnel.argtypes = [d, d, d, vp]
@@ -169,6 +171,24 @@ def trace(os_: OracleScene, n_rays, max_depth, offset=0, stride=1, count=None,
         n = lib().orc_trace(os_.h, n_rays, max_depth, offset, stride, count,
                             eps_abs, eps_rel, threads, _ptr(out), cap,
                             _ptr(marg), _ptr(segs))
+        if n <= cap:
+            return out[:n], marg, segs
+        cap = int(n)
+
+
+def trace_list(os_, n_rays, max_depth, ray_idx, eps_abs=1e-4, eps_rel=0.0, threads=None):
+    """SBR discovery for an explicit list of ray indices (same outputs as
+    trace; candidate and ray_marg indices refer to positions in the list)."""
+    idx = np.ascontiguousarray(ray_idx, np.uint64)
+    count = len(idx)
+    threads = threads or n_threads()
+    cap = max(1024, 4 * count * os_.n_tx)
+    marg = np.zeros((os_.n_tx, count), np.uint8)
+    segs = np.zeros((os_.n_tx, count), np.uint8)
+    while True:
+        out = np.zeros(cap, PATH_DTYPE)
+        n = lib().orc_trace_list(os_.h, n_rays, max_depth, _ptr(idx), count, eps_abs, eps_rel,
+                                 threads, _ptr(out), cap, _ptr(marg), _ptr(segs))
         if n <= cap:
             return out[:n], marg, segs
         cap = int(n)

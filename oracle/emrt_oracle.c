@@ -244,6 +244,7 @@ static void pb_push(pbuf *b, const orc_path *r) {
 typedef struct {
   orc_scene s;
   uint64_t n_rays, offset, stride, count;
+  const uint64_t *idx;  /* explicit ray list, or NULL */
   int K;
   double eps_abs, eps_rel, kappa;
   pbuf *bufs;  /* per chunk */
@@ -253,7 +254,7 @@ typedef struct {
 static void trace_one(trace_ctx *C, int tx, uint64_t j, pbuf *out, uint8_t *marg_out,
                       uint8_t *segs_out) {
   orc_scene s = C->s;
-  uint64_t idx = C->offset + C->stride * j;
+  uint64_t idx = C->idx ? C->idx[j] : C->offset + C->stride * j;
   float df[3];
   orc_ray_dir(C->n_rays, idx, df);
   v3 d = unit(ld3(df));
@@ -350,12 +351,12 @@ static void trace_chunk(void *ctx, int64_t c) {
               &C->segs[tx * C->count + j]);
 }
 
-int64_t orc_trace(orc_scene s, uint64_t n_rays, int max_depth, uint64_t offset,
-                  uint64_t stride, uint64_t count, double eps_abs, double eps_rel,
-                  int n_threads, orc_path *out, int64_t cap, uint8_t *ray_marg,
-                  uint8_t *ray_segs) {
+static int64_t trace_impl(orc_scene s, uint64_t n_rays, int max_depth, uint64_t offset,
+                          uint64_t stride, const uint64_t *idx, uint64_t count, double eps_abs,
+                          double eps_rel, int n_threads, orc_path *out, int64_t cap,
+                          uint8_t *ray_marg, uint8_t *ray_segs) {
   trace_ctx C;
-  C.s = s; C.n_rays = n_rays; C.offset = offset; C.stride = stride;
+  C.s = s; C.n_rays = n_rays; C.offset = offset; C.stride = stride; C.idx = idx;
   C.count = count; C.K = max_depth; C.eps_abs = eps_abs; C.eps_rel = eps_rel;
   C.kappa = orc_radius_factor(n_rays);
   C.marg = ray_marg; C.segs = ray_segs;
@@ -373,6 +374,21 @@ int64_t orc_trace(orc_scene s, uint64_t n_rays, int max_depth, uint64_t offset,
   }
   free(C.bufs);
   return total;
+}
+
+int64_t orc_trace(orc_scene s, uint64_t n_rays, int max_depth, uint64_t offset,
+                  uint64_t stride, uint64_t count, double eps_abs, double eps_rel,
+                  int n_threads, orc_path *out, int64_t cap, uint8_t *ray_marg,
+                  uint8_t *ray_segs) {
+  return trace_impl(s, n_rays, max_depth, offset, stride, NULL, count, eps_abs, eps_rel,
+                    n_threads, out, cap, ray_marg, ray_segs);
+}
+
+int64_t orc_trace_list(orc_scene s, uint64_t n_rays, int max_depth, const uint64_t *ray_idx,
+                       uint64_t count, double eps_abs, double eps_rel, int n_threads,
+                       orc_path *out, int64_t cap, uint8_t *ray_marg, uint8_t *ray_segs) {
+  return trace_impl(s, n_rays, max_depth, 0, 1, ray_idx, count, eps_abs, eps_rel, n_threads,
+                    out, cap, ray_marg, ray_segs);
 }
 
 /* ------------------------------------------------------------------ */

@@ -83,6 +83,12 @@ int64_t orc_trace(orc_scene s, uint64_t n_rays, int max_depth,
                   double eps_abs, double eps_rel, int n_threads,
                   orc_path *out, int64_t cap, uint8_t *ray_marg,
                   uint8_t *ray_segs);
+/* Same, for an explicit list of ray indices (ray j of the traced set is
+ * ray_idx[j]; candidates report j). */
+int64_t orc_trace_list(orc_scene s, uint64_t n_rays, int max_depth,
+                       const uint64_t *ray_idx, uint64_t count, double eps_abs,
+                       double eps_rel, int n_threads, orc_path *out, int64_t cap,
+                       uint8_t *ray_marg, uint8_t *ray_segs);
 
 /* Image-method acceptance of n paths.  accepted[i] = 1 if valid; marginal[i]
  * bit0 = a reflection point or side test within the margin, bit1 = an

@@ -50,9 +50,9 @@ def compare_candidates(gpu_unique, orc_cands, ray_marg):
                 oracle_marginal=sum(1 for f in oflag.values() if f != 0))
 
 
-def compare_acceptance(os_, gpu_paths, eps_abs=1e-4):
+def compare_acceptance(os_, gpu_paths, eps_abs=1e-4, eps_rel=0.0):
     """Acceptance parity on the GPU's own candidate list."""
-    acc_o, marg_o = oracle.validate(os_, gpu_paths, eps_abs=eps_abs)
+    acc_o, marg_o = oracle.validate(os_, gpu_paths, eps_abs=eps_abs, eps_rel=eps_rel)
     acc_g = (gpu_paths["flag"] & 1).astype(bool)
     diff = acc_o != acc_g
     bad = np.nonzero(diff & (marg_o == 0))[0]
