@@ -31,8 +31,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s traversal and receiver-frames/s channel update (2x2km,10k Rx), cached vs plain"
 UNIT = "receiver-frames/s"
-REFRESH = 10          # cached method: full-density rediscovery every REFRESH frames
-R_LOW = 10            # cached method: per-frame rediscovery with N / R_LOW rays
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bounce_city_traffic.txt")
 KERNEL_SOURCES = ["paper_2303_10521_gb300/csrc/trace.cu",
                   "paper_2303_10521_gb300/csrc/traverse.cuh"]
@@ -46,6 +44,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cached-frames", type=int, default=30)
+    ap.add_argument("--refresh", type=int, default=10,
+                    help="cached method: full-density rediscovery every N frames")
+    ap.add_argument("--rediscovery-fraction", type=int, default=10,
+                    help="cached method: per-frame rediscovery with N_rays / this (0: none)")
     ap.add_argument("--ray-stride", type=int, default=1,
                     help="trace rays offset + stride*j only (profiling captures)")
     ap.add_argument("--no-sort-rays", action="store_true",
@@ -351,31 +353,44 @@ def main():
     # for that density) merged into the cache, and a full-density
     # rediscovery replaces it every REFRESH frames.
     nc = args.cached_frames
+    REFRESH, R_LOW = args.refresh, args.rediscovery_fraction
     cframes = [F(frame_dev(total + 1 + k)) for k in range(nc)]
     cache = engine.Paths(cap * 4, dev)
     fresh = engine.Paths(cap * 2, dev)
+    for k in (nc - 2, nc - 1):  # untimed warm-up of the cached pipeline (sizes scratch)
+        g.update(cframes[k])
+        g.trace_async(cache, sort_rays=sort_rays)
+        g.revalidate(cache)
+        g.trace_async(fresh, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays)
+        g.merge(cache, fresh)
+        g.sync()
     g.update(cframes[0])
     g.trace_async(cache, sort_rays=sort_rays)
     g.sync()
     cached_rx = []
     torch.cuda.synchronize()
     e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fev = [torch.cuda.Event(enable_timing=True) for _ in range(nc)]
     e4.record(stream)
     for k in range(1, nc):
+        fev[k - 1].record(stream)
         g.update(cframes[k])
         g.revalidate(cache)
-        if k % REFRESH == 0:
+        if REFRESH and k % REFRESH == 0:
             g.trace_async(fresh, sort_rays=sort_rays)
-        else:
+            g.merge(cache, fresh)
+        elif R_LOW:
             g.trace_async(fresh, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays)
-        g.merge(cache, fresh)
+            g.merge(cache, fresh)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
         cached_rx.append(chs[0].rx[:, 0].clone())
         g.sync()
     e5.record(stream)
+    fev[nc - 1].record(stream)
     torch.cuda.synchronize()
     cached_ms = e4.elapsed_time(e5)
+    cached_frame_ms = [fev[k].elapsed_time(fev[k + 1]) for k in range(nc - 1)]
     cached_val = n_rx * (nc - 1) * ws / (cached_ms / 1e3)
 
     def agree(pa, pb):
@@ -398,7 +413,9 @@ def main():
         acc_p.append(agree(pq, pp))
     acc_c, acc_p = np.array(acc_c), np.array(acc_p)
     accuracy = {
-        "frames": nc, "refresh_every": REFRESH, "rediscovery_rays_per_tx": sc.n_rays // R_LOW,
+        "frames": nc, "refresh_every": REFRESH, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
+        "frame_ms_median": float(np.median(cached_frame_ms)),
+        "frame_ms_max": float(np.max(cached_frame_ms)),
         "reference": "plain retrace of the same frame with N = 1e7 rays per Tx",
         "cached": {"power_recall_mean": float(acc_c[:, 0].mean()),
                    "power_recall_min": float(acc_c[:, 0].min()),

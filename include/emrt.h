@@ -57,6 +57,10 @@ extern "C" {
                                           EMRT_PATH_VALID set on accepted ones */
 #define EMRT_TRACE_SORT_RAYS 0x2u      /* reorder rays between bounces by
                                           origin cell and direction bin       */
+#define EMRT_TRACE_WIDE_BVH 0x4u       /* traverse the static geometry through
+                                          its 4-wide BVH (same results; on
+                                          GB300 the binary LBVH is faster for
+                                          the city scenes measured)           */
 /* emrt_revalidate flags */
 #define EMRT_REVALIDATE_KEEP 0x1u      /* do not compact: flag only          */
 

@@ -18,6 +18,7 @@ PATH_VALID = 0x100
 PATH_MARGINAL = 0x200
 TRACE_KEEP_REJECTED = 0x1
 TRACE_SORT_RAYS = 0x2
+TRACE_WIDE_BVH = 0x4
 REVALIDATE_KEEP = 0x1
 NOALLOC_MAX_PATHS = 65536
 BATCH_AUTOTUNE = 0x1

@@ -206,6 +206,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = bvh_alloc(s->stat, PRIM_TRI, std::max(s->T, 2u)))) return fail(e);
   if ((e = bvh_build_tris(s->stat, d->tri_xyz, d->tri_face, s->T, s->bbox, s->hist, st)))
     return fail(e);
+  if ((e = bvh4_collapse(s->stat, st))) return fail(e);
   if ((e = bvh_alloc(s->dyn, PRIM_BOX, std::max(s->V, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->rxb, PRIM_POINT, std::max(s->max_rx, 2u)))) return fail(e);
   uint32_t V1 = std::max(s->V, 1u);
@@ -381,7 +382,7 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     L.b = (int)b;
     L.K = (int)p->max_depth;
     cudaEventRecord(s->evb[2 * b], st);
-    launch_bounce(L, grid, st);
+    launch_bounce(L, grid, st, (p->flags & EMRT_TRACE_WIDE_BVH) != 0);
     cudaEventRecord(s->evb[2 * b + 1], st);
   }
   s->ev_bounces = p->max_depth + 1;

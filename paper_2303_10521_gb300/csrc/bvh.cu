@@ -20,10 +20,13 @@ __device__ inline uint64_t spread3(uint32_t v) {
   return x;
 }
 
+// 63-bit Morton code of p quantised in the cube spanned by the largest extent
+// of the box (all axes share one scale), so that a flat scene is split along
+// its long axes first instead of slicing it into thin horizontal slabs.
 __device__ inline uint64_t morton63(float3 p, const float4 *bb) {
   float4 lo = bb[0], hi = bb[1];
-  float q[3] = {(p.x - lo.x) / fmaxf(hi.x - lo.x, 1e-6f), (p.y - lo.y) / fmaxf(hi.y - lo.y, 1e-6f),
-                (p.z - lo.z) / fmaxf(hi.z - lo.z, 1e-6f)};
+  float ext = fmaxf(fmaxf(hi.x - lo.x, hi.y - lo.y), fmaxf(hi.z - lo.z, 1e-6f));
+  float q[3] = {(p.x - lo.x) / ext, (p.y - lo.y) / ext, (p.z - lo.z) / ext};
   uint32_t c[3];
   for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 2097151.f);
   return spread3(c[0]) << 2 | spread3(c[1]) << 1 | spread3(c[2]);
@@ -185,6 +188,78 @@ __global__ void k_refit(const float4 *prims, uint32_t n, float4 *nodes, const ui
   }
 }
 
+struct Child {
+  int code;
+  float lo[3], hi[3];
+};
+
+__device__ inline Child child_of(const float4 *nodes, int p, int side) {
+  const float4 *np = nodes + 4ll * p;
+  float4 a = np[side], z = np[2];
+  Child c;
+  c.code = reinterpret_cast<const int *>(np + 3)[side];
+  c.lo[0] = a.x; c.hi[0] = a.y; c.lo[1] = a.z; c.hi[1] = a.w;
+  c.lo[2] = side ? z.z : z.x;
+  c.hi[2] = side ? z.w : z.y;
+  return c;
+}
+
+__device__ inline float half_area(const Child &c) {
+  float dx = c.hi[0] - c.lo[0], dy = c.hi[1] - c.lo[1], dz = c.hi[2] - c.lo[2];
+  return dx * dy + dy * dz + dz * dx;
+}
+
+// one thread per 4-wide node of the current level
+__global__ void k_collapse(const float4 *bn, const uint32_t *in_bin, const uint32_t *in_dst,
+                           const uint32_t *n_in, float4 *out4, uint32_t *out_bin,
+                           uint32_t *out_dst, uint32_t *n_out, uint32_t *n_alloc) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n_in) return;
+  int b = (int)in_bin[i];
+  uint32_t dst = in_dst[i];
+  Child c[4];
+  int cnt = 2;
+  c[0] = child_of(bn, b, 0);
+  c[1] = child_of(bn, b, 1);
+  while (cnt < 4) {
+    int best = -1;
+    float ba = -1.f;
+    for (int k = 0; k < cnt; k++)
+      if (c[k].code >= 0 && half_area(c[k]) > ba) {
+        ba = half_area(c[k]);
+        best = k;
+      }
+    if (best < 0) break;
+    int nb = c[best].code;
+    c[best] = child_of(bn, nb, 0);
+    c[cnt++] = child_of(bn, nb, 1);
+  }
+  float4 *o = out4 + 8ull * dst;
+  float v[6][4];
+  int codes[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 4; k++) {
+    bool ok = k < cnt;
+    for (int a = 0; a < 3; a++) {
+      v[2 * a][k] = ok ? c[k].lo[a] : 0.f;
+      v[2 * a + 1][k] = ok ? c[k].hi[a] : 0.f;
+    }
+    if (!ok) continue;
+    if (c[k].code < 0) {
+      codes[k] = c[k].code;
+    } else {
+      uint32_t ni = atomicAdd(n_alloc, 1u);
+      uint32_t slot = atomicAdd(n_out, 1u);
+      out_bin[slot] = (uint32_t)c[k].code;
+      out_dst[slot] = ni;
+      codes[k] = (int)ni;
+    }
+  }
+  for (int r = 0; r < 6; r++) o[r] = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
+  o[6] = make_float4(__int_as_float(codes[0]), __int_as_float(codes[1]), __int_as_float(codes[2]),
+                     __int_as_float(codes[3]));
+  o[7] = make_float4(__int_as_float(cnt), 0.f, 0.f, 0.f);
+}
+
 __device__ inline uint32_t f2o(float f) {
   uint32_t u = __float_as_uint(f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -262,6 +337,7 @@ cudaError_t sort_codes(BVHBuf &b, uint32_t *hist, cudaStream_t s) {
 
 BVHView BVHBuf::view() const {
   BVHView v;
+  v.nodes4 = nodes4;
   v.nodes = nodes;
   v.prims = prims;
   v.root = n >= 2 ? 0 : ~0;
@@ -291,6 +367,9 @@ cudaError_t bvh_alloc(BVHBuf &b, PrimKind kind, uint32_t cap) {
 void bvh_free(BVHBuf &b) {
   cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.leaf_parent); cudaFree(b.flags);
   cudaFree(b.keys); cudaFree(b.keys2); cudaFree(b.idx); cudaFree(b.idx2); cudaFree(b.d_n);
+  cudaFree(b.nodes4);
+  b.nodes4 = nullptr;
+  b.n4 = 0;
   b.nodes = b.prims = nullptr;
   b.leaf_parent = b.flags = b.idx = b.idx2 = b.d_n = nullptr;
   b.keys = b.keys2 = nullptr;
@@ -336,6 +415,39 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
   sort_codes<PRIM_POINT>(b, hist, s);
   emrt::note_launch(), k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, b.idx, n, b.prims);
   return finish_build<PRIM_POINT>(b, s);
+}
+
+cudaError_t bvh4_collapse(BVHBuf &b, cudaStream_t s) {
+  if (b.n < 2) return cudaSuccess;
+  cudaError_t e;
+  cudaFree(b.nodes4);
+  b.nodes4 = nullptr;
+  if ((e = cudaMalloc(&b.nodes4, sizeof(float4) * 8 * (size_t)b.n))) return e;
+  uint32_t *buf = nullptr;  // two level lists (binary index, 4-wide index) + counters
+  if ((e = cudaMalloc(&buf, sizeof(uint32_t) * (4 * (size_t)b.n + 4)))) return e;
+  uint32_t *lb[2] = {buf, buf + b.n}, *ld[2] = {buf + 2 * b.n, buf + 3 * b.n};
+  uint32_t *ctr = buf + 4 * b.n;  // [0],[1]: level sizes, [2]: nodes allocated
+  uint32_t init[4] = {1, 0, 1, 0};
+  uint32_t zero = 0;
+  cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(lb[0], 0, sizeof(uint32_t), s);
+  cudaMemsetAsync(ld[0], 0, sizeof(uint32_t), s);
+  uint32_t n_level = 1;
+  int cur = 0;
+  for (int guard = 0; n_level && guard < 4096; guard++) {
+    cudaMemcpyAsync(ctr + (cur ^ 1), &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    emrt::note_launch(), k_collapse<<<ceil_div(n_level, 128), 128, 0, s>>>(
+        b.nodes, lb[cur], ld[cur], ctr + cur, b.nodes4, lb[cur ^ 1], ld[cur ^ 1], ctr + (cur ^ 1),
+        ctr + 2);
+    cudaMemcpyAsync(&n_level, ctr + (cur ^ 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) break;
+    cur ^= 1;
+  }
+  cudaMemcpyAsync(&b.n4, ctr + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e) return e;
+  return cudaGetLastError();
 }
 
 void bbox_of_tris(const float *tri_xyz, uint32_t n, float4 *bbox, cudaStream_t s) {

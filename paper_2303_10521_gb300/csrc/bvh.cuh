@@ -19,6 +19,8 @@ struct BVHBuf {
   KeyW<2> *keys = nullptr, *keys2 = nullptr;  // [cap]
   uint32_t *idx = nullptr, *idx2 = nullptr;   // [cap]
   uint32_t *d_n = nullptr;       // device copy of n
+  float4 *nodes4 = nullptr;      // 4-wide collapse (static BVH), or null
+  uint32_t n4 = 0;
   BVHView view() const;
 };
 
@@ -39,6 +41,12 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
                              uint32_t *hist, cudaStream_t s);
 // Moves box primitives to new corners (vehicle id kept in lo.w) and refits.
 cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaStream_t s);
+
+// Collapses the binary tree of b (built, refitted) into 4-wide nodes
+// (b.nodes4): every 4-wide node takes its binary node's two children and
+// repeatedly opens the inner child of largest surface area until it holds 4
+// children.  Synchronises the stream (build time only).
+cudaError_t bvh4_collapse(BVHBuf &b, cudaStream_t s);
 
 // Axis-aligned bounds of n float[9] triangles, written to bbox[2].
 void bbox_of_tris(const float *tri_xyz, uint32_t n, float4 *bbox, cudaStream_t s);

@@ -44,6 +44,9 @@ struct Counters {
 //   [2] c0.lo.z c0.hi.z c1.lo.z c1.hi.z
 //   [3] (int) c0, c1, parent, 0     child >= 0: inner node, < 0: leaf ~prim
 struct BVHView {
+  const float4 *nodes4;  // optional 4-wide collapse of `nodes` (8 float4 per
+                         // node: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the 4
+                         // children, int4 child codes, int child count)
   const float4 *nodes;
   const float4 *prims;  // triangles: 3 float4 (v0 with face id bits in .w,
                         // v1, v2); boxes: 2 float4 (lo with vehicle id bits in

@@ -101,8 +101,8 @@ __device__ inline void add_u64(unsigned long long *p, unsigned long long v) {
 // L.g.  Per ray: nearest hit over the static triangles and the vehicle
 // boxes, reception-sphere detections on the traced segment (appended as
 // candidates), and the specular continuation (appended to the next buffer).
-template <bool BATCH, int BLOCK, int FETCH>
-__global__ void __launch_bounds__(BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
+template <bool BATCH, int BLOCK, int FETCH, bool WIDE>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
                                                   uint32_t n_scenes) {
   int stk[kStack];
   float stt[kStack];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(BLOCK) k_bounce(BounceLaunch L, const BatchSce
       ray_setup(q, o, d);
       float tbest = FLT_MAX;
       uint32_t face = NO;
-      trace_tris<false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+      trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
       uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
       trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
       bool hit = face != NO;
@@ -561,7 +561,7 @@ int bounce_grid() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bounce<false, kBounceBlock, 32>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bounce<false, kBounceBlock, 32, false>,
                                                   kBounceBlock, 0);
     g_bounce_grid = sms * (per > 0 ? per : 1);
   }
@@ -576,12 +576,14 @@ struct Variant {
   int grid;
 };
 Variant g_variants[] = {
-    {"block64_fetch32", 64, k_bounce<true, 64, 32>, 0},
-    {"block128_fetch32", 128, k_bounce<true, 128, 32>, 0},
-    {"block256_fetch32", 256, k_bounce<true, 256, 32>, 0},
-    {"block128_fetch128", 128, k_bounce<true, 128, 128>, 0},
-    {"block256_fetch64", 256, k_bounce<true, 256, 64>, 0},
-    {"block64_fetch128", 64, k_bounce<true, 64, 128>, 0},
+    {"block64_fetch32", 64, k_bounce<true, 64, 32, false>, 0},
+    {"block128_fetch32", 128, k_bounce<true, 128, 32, false>, 0},
+    {"block256_fetch32", 256, k_bounce<true, 256, 32, false>, 0},
+    {"block128_fetch128", 128, k_bounce<true, 128, 128, false>, 0},
+    {"block256_fetch64", 256, k_bounce<true, 256, 64, false>, 0},
+    {"block64_fetch128", 64, k_bounce<true, 64, 128, false>, 0},
+    {"block128_fetch32_bvh4", 128, k_bounce<true, 128, 32, true>, 0},
+    {"block64_fetch32_bvh4", 64, k_bounce<true, 64, 32, true>, 0},
 };
 constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 }  // namespace
@@ -637,8 +639,11 @@ void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1
   emrt::note_launch(), k_ray_keys<<<kPrimGrid * 8, 256, 0, s>>>(r, n, bbox, keys, vals, batched);
 }
 
-void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s) {
-  emrt::note_launch(), k_bounce<false, kBounceBlock, 32><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);
+void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s, bool wide) {
+  if (wide)
+    emrt::note_launch(), k_bounce<false, kBounceBlock, 32, true><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);
+  else
+    emrt::note_launch(), k_bounce<false, kBounceBlock, 32, false><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);
 }
 
 void launch_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,

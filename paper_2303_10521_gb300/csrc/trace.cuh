@@ -36,7 +36,8 @@ struct BounceLaunch {
   float kappa;
   int b, K;
 };
-void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s);
+// wide: traverse the static BVH's 4-wide collapse
+void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s, bool wide = false);
 int bounce_grid();  // persistent grid size (SMs x resident blocks)
 
 // One scene of a batch (device table entry).  Batched rays pack

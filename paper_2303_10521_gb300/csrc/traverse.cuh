@@ -101,14 +101,111 @@ struct TravStats {
     return hit;                        \
   }
 
+// One triangle leaf: watertight test, exclusion of faces ex0/ex1, closest-hit
+// tie to the lower face ID.  Returns true when tmax/face changed.
+template <bool ANY>
+__device__ inline bool leaf_tri(const BVHView &b, uint32_t g, const RayQ &r, float tmin,
+                                float &tmax, uint32_t &face, uint32_t ex0, uint32_t ex1,
+                                TravStats &st) {
+  const float4 *tp = b.prims + 3ull * g;
+  float4 a = ldg4(tp), bb = ldg4(tp + 1), c = ldg4(tp + 2);
+  st.tris++;
+  uint32_t f = __float_as_uint(a.w);
+  float t;
+  // closest hit: widen the bound slightly so that an exact tie can go to
+  // the lower face ID; any hit: strictly inside (tmin, tmax)
+  if (f != ex0 && f != ex1 &&
+      tri_hit(r, f3(a), f3(bb), f3(c), tmin, ANY ? tmax : tmax * 1.0000001f, t)) {
+    if (t < tmax || (!ANY && t == tmax && f < face)) {
+      tmax = t;
+      face = f;
+      return true;
+    }
+  }
+  return false;
+}
+
+// 4-wide traversal: each node fetch (8 x 16 B) tests four child boxes; the
+// nearest hit child is entered, the others are pushed far-to-near.
+template <bool ANY>
+__device__ inline bool trace_tris4(const BVHView &b, const RayQ &r, float tmin, float &tmax,
+                                   uint32_t &face, uint32_t ex0, uint32_t ex1, int *stk, float *stt,
+                                   TravStats &st) {
+  bool hit = false;
+  int sp = 0;
+  int node = 0;
+  uint32_t iter = 0;
+  for (;;) {
+    EMRT_ITER_GUARD(st)
+    if (node >= 0) {
+      const float4 *np = b.nodes4 + 8ll * node;
+      float4 lx = ldg4(np), hx = ldg4(np + 1), ly = ldg4(np + 2), hy = ldg4(np + 3);
+      float4 lz = ldg4(np + 4), hz = ldg4(np + 5), cc = ldg4(np + 6), nn = ldg4(np + 7);
+      st.nodes++;
+      int cnt = __float_as_int(nn.x);
+      float tn[4];
+      bool h[4];
+      h[0] = slab(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tmin, tmax, tn[0]);
+      h[1] = slab(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tmin, tmax, tn[1]);
+      h[2] = cnt > 2 && slab(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tmin, tmax, tn[2]);
+      h[3] = cnt > 3 && slab(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tmin, tmax, tn[3]);
+      int code[4] = {__float_as_int(cc.x), __float_as_int(cc.y), __float_as_int(cc.z),
+                     __float_as_int(cc.w)};
+      int best = -1;
+      float bt = 3.4e38f;
+      for (int k = 0; k < 4; k++)
+        if (h[k] && tn[k] < bt) {
+          bt = tn[k];
+          best = k;
+        }
+      if (best >= 0) {
+        // push the other hits far-to-near (insertion sort within this
+        // node's group, so the nearest remaining child is popped first)
+        const int g0 = sp;
+        for (int k = 0; k < 4; k++) {
+          if (!h[k] || k == best) continue;
+          if (sp >= kStack) {
+            st.overflow = true;
+            continue;
+          }
+          int q = sp++;
+          while (q > g0 && stt[q - 1] < tn[k]) {
+            stk[q] = stk[q - 1];
+            stt[q] = stt[q - 1];
+            q--;
+          }
+          stk[q] = code[k];
+          stt[q] = tn[k];
+        }
+        node = code[best];
+        continue;
+      }
+    } else {
+      if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
+        hit = true;
+        if (ANY) return true;
+      }
+    }
+    for (;;) {
+      if (sp == 0) return hit;
+      sp--;
+      if (stt[sp] <= tmax) break;
+    }
+    node = stk[sp];
+  }
+}
+
 // Closest hit (ANY = false) or any hit (ANY = true) over the triangle BVH with
 // t in (tmin, tmax).  Triangles of faces ex0/ex1 are skipped.  On a hit
 // tmax and face are updated.  Ties in t go to the lower face ID.
-template <bool ANY>
+// WIDE: use the 4-wide collapse when the BVH has one.
+template <bool ANY, bool WIDE = false>
 __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, float &tmax,
                                   uint32_t &face, uint32_t ex0, uint32_t ex1, int *stk, float *stt,
                                   TravStats &st) {
   if (b.n_prims == 0) return false;
+  if (WIDE && b.nodes4 && b.n_prims >= 2)
+    return trace_tris4<ANY>(b, r, tmin, tmax, face, ex0, ex1, stk, stt, st);
   bool hit = false;
   int sp = 0;
   int node = b.root;
@@ -135,22 +232,9 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
       if (h0) { node = c0; continue; }
       if (h1) { node = c1; continue; }
     } else {
-      uint32_t g = (uint32_t)(~node);
-      const float4 *tp = b.prims + 3ull * g;
-      float4 a = ldg4(tp), bb = ldg4(tp + 1), c = ldg4(tp + 2);
-      st.tris++;
-      uint32_t f = __float_as_uint(a.w);
-      float t;
-      // closest hit: widen the bound slightly so that an exact tie can go to
-      // the lower face ID; any hit: strictly inside (tmin, tmax)
-      if (f != ex0 && f != ex1 &&
-          tri_hit(r, f3(a), f3(bb), f3(c), tmin, ANY ? tmax : tmax * 1.0000001f, t)) {
-        if (t < tmax || (!ANY && t == tmax && f < face)) {
-          tmax = t;
-          face = f;
-          hit = true;
-          if (ANY) return true;
-        }
+      if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
+        hit = true;
+        if (ANY) return true;
       }
     }
     // pop the next subtree that can still hold a closer hit

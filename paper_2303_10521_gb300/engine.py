@@ -135,25 +135,26 @@ class Scene:
             "emrt_scene_update_dynamic")
 
     def trace_async(self, out: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
-                    keep_rejected=False, sort_rays=True, stream=None):
+                    keep_rejected=False, sort_rays=True, stream=None, wide_bvh=False):
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
                           (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
-                          (N.TRACE_SORT_RAYS if sort_rays else 0))
+                          (N.TRACE_SORT_RAYS if sort_rays else 0) |
+                          (N.TRACE_WIDE_BVH if wide_bvh else 0))
         pc = out.c()
         N.check(self.lib.emrt_trace(self.h, C.byref(p), C.byref(pc), _stream(stream)),
                 "emrt_trace")
 
     def trace(self, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
               keep_rejected=False, capacity=None, stream=None, retries=3,
-              sort_rays=True) -> Paths:
+              sort_rays=True, wide_bvh=False) -> Paths:
         """Plain discovery; grows scratch and output on capacity errors."""
         cap = capacity or max(4096, 8 * self.n_tx * self.n_rx)
         for _ in range(retries + 1):
             out = Paths(cap, self.device)
             self.trace_async(out, n_rays, max_depth, offset, stride, count, keep_rejected,
-                             sort_rays=sort_rays, stream=stream)
+                             sort_rays=sort_rays, stream=stream, wide_bvh=wide_bvh)
             try:
                 self.last_stats = self.sync(stream)
                 return out
