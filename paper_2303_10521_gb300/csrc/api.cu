@@ -204,8 +204,13 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   cudaMemsetAsync(s->ctr, 0, sizeof(Counters), st);
   bbox_of_tris(d->tri_xyz, s->T, s->bbox, st);
   if ((e = bvh_alloc(s->stat, PRIM_TRI, std::max(s->T, 2u)))) return fail(e);
-  if ((e = bvh_build_tris(s->stat, d->tri_xyz, d->tri_face, s->T, s->bbox, s->hist, st)))
-    return fail(e);
+  // static geometry: binned-SAH tree (built once); the LBVH if the SAH tree
+  // would be deeper than the traversal stack
+  if (bvh_build_tris_sah(s->stat, d->tri_xyz, d->tri_face, s->T, st) != cudaSuccess) {
+    cudaGetLastError();
+    if ((e = bvh_build_tris(s->stat, d->tri_xyz, d->tri_face, s->T, s->bbox, s->hist, st)))
+      return fail(e);
+  }
   if ((e = bvh4_collapse(s->stat, st))) return fail(e);
   if ((e = bvh_alloc(s->dyn, PRIM_BOX, std::max(s->V, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->rxb, PRIM_POINT, std::max(s->max_rx, 2u)))) return fail(e);

@@ -417,6 +417,305 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
   return finish_build<PRIM_POINT>(b, s);
 }
 
+// ---------------------------------------------------------------------------
+// Binned SAH top-down build (static triangles; built once).  Level by level,
+// one block per node range: centroid bounds, 32 bins along the longest axis,
+// surface-area-heuristic sweep, stable partition of the range.  Ranges of one
+// triangle become leaves.  Writes the same node format as the LBVH (child
+// codes and parent links); boxes are filled by the bottom-up refit.
+namespace {
+
+constexpr int kSahBins = 32;
+constexpr int kSahBlock = 256;
+constexpr int kSahMaxDepth = 60;  // levels; the traversal stack holds 64 entries
+
+struct SahTask {
+  uint32_t b, e, node, pad;
+};
+
+__global__ void k_tri_bounds(const float *t, uint32_t n, float4 *cen, float4 *lo, float4 *hi,
+                             uint32_t *perm) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float *v = t + 9ull * i;
+  float3 a = make_float3(fminf(v[0], fminf(v[3], v[6])), fminf(v[1], fminf(v[4], v[7])),
+                         fminf(v[2], fminf(v[5], v[8])));
+  float3 b = make_float3(fmaxf(v[0], fmaxf(v[3], v[6])), fmaxf(v[1], fmaxf(v[4], v[7])),
+                         fmaxf(v[2], fmaxf(v[5], v[8])));
+  lo[i] = make_float4(a.x, a.y, a.z, 0.f);
+  hi[i] = make_float4(b.x, b.y, b.z, 0.f);
+  cen[i] = make_float4((v[0] + v[3] + v[6]) * (1.f / 3.f), (v[1] + v[4] + v[7]) * (1.f / 3.f),
+                       (v[2] + v[5] + v[8]) * (1.f / 3.f), 0.f);
+  perm[i] = i;
+}
+
+__device__ inline float sel(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ inline void block_minmax(float &mn, float &mx, float *sh) {
+  for (int o = 16; o; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sh[w] = mn; sh[32 + w] = mx; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int nw = blockDim.x >> 5;
+    mn = threadIdx.x < nw ? sh[threadIdx.x] : 3.4e38f;
+    mx = threadIdx.x < nw ? sh[32 + threadIdx.x] : -3.4e38f;
+    for (int o = 16; o; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (threadIdx.x == 0) { sh[0] = mn; sh[32] = mx; }
+  }
+  __syncthreads();
+  mn = sh[0];
+  mx = sh[32];
+  __syncthreads();
+}
+
+__device__ inline uint32_t f2o_d(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline float o2f_d(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void __launch_bounds__(kSahBlock) k_sah_level(
+    const SahTask *tasks, const uint32_t *n_tasks, const float4 *cen, const float4 *blo,
+    const float4 *bhi, uint32_t *perm, uint32_t *tmp, float4 *nodes, uint32_t *leaf_parent,
+    SahTask *out, uint32_t *n_out, uint32_t *n_alloc) {
+  __shared__ float sh[64];
+  __shared__ uint32_t bcnt[kSahBins];
+  __shared__ uint32_t blo_s[kSahBins][3], bhi_s[kSahBins][3];
+  __shared__ int s_axis, s_split;
+  __shared__ float s_lo, s_ext;
+  __shared__ uint32_t s_carry, s_wsum[kSahBlock / 32];
+  if (blockIdx.x >= *n_tasks) return;
+  SahTask T = tasks[blockIdx.x];
+  const uint32_t b = T.b, e = T.e, cnt = e - b;
+  // centroid bounds
+  float lo3[3], hi3[3];
+  for (int k = 0; k < 3; k++) {
+    float mn = 3.4e38f, mx = -3.4e38f;
+    for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+      float c = sel(cen[perm[i]], k);
+      mn = fminf(mn, c);
+      mx = fmaxf(mx, c);
+    }
+    block_minmax(mn, mx, sh);
+    lo3[k] = mn;
+    hi3[k] = mx;
+  }
+  if (threadIdx.x == 0) {
+    int ax = 0;
+    float ext = hi3[0] - lo3[0];
+    for (int k = 1; k < 3; k++)
+      if (hi3[k] - lo3[k] > ext) { ext = hi3[k] - lo3[k]; ax = k; }
+    s_axis = ax;
+    s_lo = lo3[ax];
+    s_ext = ext;
+    s_split = -1;
+  }
+  if (threadIdx.x < kSahBins) {
+    bcnt[threadIdx.x] = 0;
+    for (int k = 0; k < 3; k++) {
+      blo_s[threadIdx.x][k] = 0xffffffffu;
+      bhi_s[threadIdx.x][k] = 0u;
+    }
+  }
+  __syncthreads();
+  const int ax = s_axis;
+  const float lo = s_lo, ext = s_ext;
+  if (ext > 0.f) {
+    for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+      uint32_t p = perm[i];
+      int bin = min(kSahBins - 1, (int)((sel(cen[p], ax) - lo) / ext * kSahBins));
+      atomicAdd(&bcnt[bin], 1u);
+      float4 a = blo[p], z = bhi[p];
+      for (int k = 0; k < 3; k++) {
+        atomicMin(&blo_s[bin][k], f2o_d(sel(a, k)));
+        atomicMax(&bhi_s[bin][k], f2o_d(sel(z, k)));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // SAH sweep over the 31 bin boundaries
+      float rl[kSahBins][3], rh[kSahBins][3];
+      uint32_t rc[kSahBins];
+      float l3[3] = {3.4e38f, 3.4e38f, 3.4e38f}, h3[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+      uint32_t c = 0;
+      for (int q = kSahBins - 1; q >= 0; q--) {
+        if (bcnt[q]) {
+          for (int k = 0; k < 3; k++) {
+            l3[k] = fminf(l3[k], o2f_d(blo_s[q][k]));
+            h3[k] = fmaxf(h3[k], o2f_d(bhi_s[q][k]));
+          }
+        }
+        c += bcnt[q];
+        rc[q] = c;
+        for (int k = 0; k < 3; k++) { rl[q][k] = l3[k]; rh[q][k] = h3[k]; }
+      }
+      float best = 3.4e38f;
+      int bs = -1;
+      float a3[3] = {3.4e38f, 3.4e38f, 3.4e38f}, z3[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+      uint32_t lc = 0;
+      for (int q = 0; q < kSahBins - 1; q++) {
+        if (bcnt[q]) {
+          for (int k = 0; k < 3; k++) {
+            a3[k] = fminf(a3[k], o2f_d(blo_s[q][k]));
+            z3[k] = fmaxf(z3[k], o2f_d(bhi_s[q][k]));
+          }
+        }
+        lc += bcnt[q];
+        uint32_t rcnt = rc[q + 1];
+        if (lc == 0 || rcnt == 0) continue;
+        float dl[3] = {z3[0] - a3[0], z3[1] - a3[1], z3[2] - a3[2]};
+        float dr[3] = {rh[q + 1][0] - rl[q + 1][0], rh[q + 1][1] - rl[q + 1][1],
+                       rh[q + 1][2] - rl[q + 1][2]};
+        float al = dl[0] * dl[1] + dl[1] * dl[2] + dl[2] * dl[0];
+        float ar = dr[0] * dr[1] + dr[1] * dr[2] + dr[2] * dr[0];
+        float cost = al * lc + ar * rcnt;
+        if (cost < best) { best = cost; bs = q + 1; }
+      }
+      s_split = bs;
+    }
+    __syncthreads();
+  }
+  const int split = s_split;
+  // stable partition of the range into tmp, then back into perm
+  uint32_t nl;
+  if (split < 0) {
+    nl = cnt / 2;  // degenerate: all centroids in one bin; any split is valid
+  } else {
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t r0 = b; r0 < e; r0 += blockDim.x) {
+      uint32_t i = r0 + threadIdx.x;
+      uint32_t p = 0;
+      bool left = false;
+      if (i < e) {
+        p = perm[i];
+        left = min(kSahBins - 1, (int)((sel(cen[p], ax) - lo) / ext * kSahBins)) < split;
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, left);
+      int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+      if (l == 0) s_wsum[w] = __popc(m);
+      __syncthreads();
+      uint32_t before = s_carry;
+      for (int q = 0; q < w; q++) before += s_wsum[q];
+      before += __popc(m & ((1u << l) - 1u));
+      if (i < e && left) tmp[b + before] = p;
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) s_carry += s_wsum[q];
+      __syncthreads();
+    }
+    nl = s_carry;
+    __syncthreads();  // every thread has read the left count before the reset
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t r0 = b; r0 < e; r0 += blockDim.x) {
+      uint32_t i = r0 + threadIdx.x;
+      uint32_t p = 0;
+      bool right = false;
+      if (i < e) {
+        p = perm[i];
+        right = min(kSahBins - 1, (int)((sel(cen[p], ax) - lo) / ext * kSahBins)) >= split;
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, right);
+      int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+      if (l == 0) s_wsum[w] = __popc(m);
+      __syncthreads();
+      uint32_t before = s_carry;
+      for (int q = 0; q < w; q++) before += s_wsum[q];
+      before += __popc(m & ((1u << l) - 1u));
+      if (i < e && right) tmp[b + nl + before] = p;
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) s_carry += s_wsum[q];
+      __syncthreads();
+    }
+    for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) perm[i] = tmp[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t rb[2] = {b, b + nl}, re[2] = {b + nl, e};
+    int code[2];
+    for (int side = 0; side < 2; side++) {
+      if (re[side] - rb[side] == 1) {
+        code[side] = ~(int)rb[side];
+        leaf_parent[rb[side]] = 2 * T.node + side;
+      } else {
+        uint32_t ni = atomicAdd(n_alloc, 1u);
+        code[side] = (int)ni;
+        reinterpret_cast<int *>(nodes + 4ll * ni + 3)[2] = (int)(2 * T.node + side);
+        uint32_t slot = atomicAdd(n_out, 1u);
+        out[slot] = SahTask{rb[side], re[side], ni, 0u};
+      }
+    }
+    int *n3 = reinterpret_cast<int *>(nodes + 4ll * T.node + 3);
+    n3[0] = code[0];
+    n3[1] = code[1];
+    n3[3] = 0;
+    if (T.node == 0) n3[2] = -1;
+  }
+}
+
+}  // namespace
+
+cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_face, uint32_t n,
+                               cudaStream_t s) {
+  b.n = n;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e;
+  float4 *cen = nullptr, *lo = nullptr, *hi = nullptr;
+  uint32_t *tmp = nullptr, *ctr = nullptr;
+  SahTask *tasks[2] = {nullptr, nullptr};
+  if ((e = cudaMalloc(&cen, sizeof(float4) * n))) return e;
+  if ((e = cudaMalloc(&lo, sizeof(float4) * n))) return e;
+  if ((e = cudaMalloc(&hi, sizeof(float4) * n))) return e;
+  if ((e = cudaMalloc(&tmp, sizeof(uint32_t) * n))) return e;
+  if ((e = cudaMalloc(&tasks[0], sizeof(SahTask) * (n / 2 + 2)))) return e;
+  if ((e = cudaMalloc(&tasks[1], sizeof(SahTask) * (n / 2 + 2)))) return e;
+  if ((e = cudaMalloc(&ctr, sizeof(uint32_t) * 4))) return e;
+  emrt::note_launch(), k_tri_bounds<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, n, cen, lo, hi, b.idx);
+  if (n >= 2) {
+    SahTask root{0u, n, 0u, 0u};
+    uint32_t init[4] = {1, 0, 1, 0};  // level sizes [0],[1]; nodes allocated [2]
+    cudaMemcpyAsync(tasks[0], &root, sizeof(root), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    uint32_t n_level = 1, zero = 0;
+    int cur = 0, levels = 0;
+    for (; n_level && levels < kSahMaxDepth; levels++) {
+      cudaMemcpyAsync(ctr + (cur ^ 1), &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+      emrt::note_launch(), k_sah_level<<<n_level, kSahBlock, 0, s>>>(
+          tasks[cur], ctr + cur, cen, lo, hi, b.idx, tmp, b.nodes, b.leaf_parent, tasks[cur ^ 1],
+          ctr + (cur ^ 1), ctr + 2);
+      cudaMemcpyAsync(&n_level, ctr + (cur ^ 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+      if ((e = cudaStreamSynchronize(s))) break;
+      cur ^= 1;
+    }
+    // a tree deeper than the traversal stack can serve is not used: the
+    // caller falls back to the LBVH
+    if (!e && n_level) e = cudaErrorNotSupported;
+  }
+  if (!e) {
+    emrt::note_launch(), k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
+    if (n >= 2) {
+      cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
+      emrt::note_launch(), k_refit<PRIM_TRI><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+    }
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFree(cen); cudaFree(lo); cudaFree(hi); cudaFree(tmp);
+  cudaFree(tasks[0]); cudaFree(tasks[1]); cudaFree(ctr);
+  if (e) return e;
+  return cudaGetLastError();
+}
+
 cudaError_t bvh4_collapse(BVHBuf &b, cudaStream_t s) {
   if (b.n < 2) return cudaSuccess;
   cudaError_t e;
