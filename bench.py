@@ -64,6 +64,31 @@ def dist_env():
     return ws, rank, local
 
 
+# ---------------------------------------------------------------------------
+# replicas (N > 1 under torchrun): independent frames per rank, the timed
+# region ends with a barrier and the max of the per-rank times
+def replica_frame_base(rank: int) -> int:
+    """First frame index traced by a rank (ranks trace disjoint frames)."""
+    return rank * 1000
+
+
+def max_over_ranks(t_ms: float, device=None) -> float:
+    """Max of a per-rank duration over all ranks (identity without a
+    process group); every rank gets the result."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(t_ms)
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -218,7 +243,7 @@ def main():
     sc = scenes.city_scene(seed=0)
     n_rx = len(sc.frame(0).rx_pos)
     stream = torch.cuda.current_stream()
-    base = rank * 1000  # each replica traces its own frames
+    base = replica_frame_base(rank)  # each replica traces its own frames
     total = args.warmup + args.steps
 
     def frame_dev(k):
@@ -267,13 +292,10 @@ def main():
     torch.cuda.synchronize()
     launches = lib.emrt_kernel_launches() - l0
     clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dev)
     if ws > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-        t_ms = float(t.item())
-    value = n_rx * args.steps * ws / (t_ms / 1e3)
+    value = job_throughput(n_rx * args.steps, ws, t_ms)
 
     # traversal kernel: algorithmic bytes per launch / launch time
     K = sc.max_depth
@@ -339,12 +361,8 @@ def main():
         g.sync()
     e3.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e2.elapsed_time(e3)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": n_rx * args.steps * ws / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms = max_over_ranks(e2.elapsed_time(e3), dev)
+    e2e = {"value": job_throughput(n_rx * args.steps, ws, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---------------- cached frames: the path cache is revalidated every frame
@@ -392,9 +410,9 @@ def main():
     e5.record(stream)
     fev[nc - 1].record(stream)
     torch.cuda.synchronize()
-    cached_ms = e4.elapsed_time(e5)
+    cached_ms = max_over_ranks(e4.elapsed_time(e5), dev)
     cached_frame_ms = [fev[k].elapsed_time(fev[k + 1]) for k in range(nc - 1)]
-    cached_val = n_rx * (nc - 1) * ws / (cached_ms / 1e3)
+    cached_val = job_throughput(n_rx * (nc - 1), ws, cached_ms)
 
     def agree(pa, pb):
         """Agreement of per-receiver powers pa against pb (W)."""
