@@ -218,6 +218,25 @@ emrt_status emrt_channel_backward_noalloc(emrt_scene sc, const emrt_paths *paths
                                           double *grad_sigma, double *grad_tx,
                                           emrt_stream s);
 
+/* Channel correlation over a series of frames, Eq. 1 (Sec. III-B), read as
+ * the normalised autocovariance of g(t) = |h(t)| (the printed denominator
+ * E[g^2] E[g]^2 is dimensionally inconsistent):
+ *   R(tau) = (mean_{t < F - tau} g(t) g(t + tau) - mu^2) / (mean_t g^2 - mu^2),
+ * mu = mean_t g.  h: [n_frames][n_pairs][2] complex coherent sums (e.g. the
+ * Re h, Im h of emrt_channel's pair_out gathered frame by frame); R:
+ * [n_pairs][max_lag + 1].  Pairs whose |h| is constant get R = 0. */
+emrt_status emrt_channel_correlation(const double *h, uint32_t n_frames, uint32_t n_pairs,
+                                     uint32_t max_lag, double *R, emrt_stream s);
+
+/* Coherence time per (tx, rx) from Eq. 2 (Sec. III-B) as printed:
+ *   T_c = sqrt(1 / R^4 - 1) / (2 pi f_D theta^2)  [seconds],
+ * R = r_threshold in (0, 1], f_D = freq |v_rx| / c the receiver's maximum
+ * Doppler shift, theta the angle (radians) between the receiver's motion and
+ * the direction from transmitter to receiver.  Infinite for a receiver at
+ * rest or moving along that direction.  tc: [n_tx][n_rx]. */
+emrt_status emrt_coherence_time(emrt_scene sc, double freq_hz, double r_threshold, double *tc,
+                                emrt_stream s);
+
 typedef struct {
   uint64_t segments[EMRT_MAX_DEPTH + 1]; /* closest-hit segments per bounce */
   uint64_t candidates;        /* reception-sphere detections                 */

@@ -348,3 +348,48 @@ def fd_gradient(scene, frame, paths, freq, tx_power_w, target_dbm, mask,
             fdn = dataclasses.replace(frame, tx_pos=dn)
             g_tx[t, c] = (loss(eps0, sig0, fu) - loss(eps0, sig0, fdn)) / (2 * h)
     return g_eps, g_sig, g_tx
+
+
+# ---------------------------------------------------------------------------
+# channel statistics over time (Sec. III-B)
+def channel_correlation(h, max_lag):
+    """Eq. 1 read as the normalised autocovariance of g(t) = |h(t)| over the
+    frames t (the printed denominator E[g^2] E[g]^2 is dimensionally
+    inconsistent): R(tau) = (mean_{t<F-tau} g(t) g(t+tau) - mu^2) /
+    (mean_t g^2 - mu^2).  h: complex [F, P]; returns [P, max_lag + 1]; a
+    constant |h| gives 0."""
+    g = np.abs(np.asarray(h))
+    F, P = g.shape
+    R = np.zeros((P, max_lag + 1))
+    for p in range(P):
+        mu = g[:, p].mean()
+        var = (g[:, p] ** 2).mean() - mu ** 2
+        for tau in range(max_lag + 1):
+            n = F - tau
+            if n <= 0 or var <= 0:
+                continue
+            R[p, tau] = (np.dot(g[:n, p], g[tau:, p]) / n - mu ** 2) / var
+    return R
+
+
+def coherence_time(tx_pos, rx_pos, rx_vel, freq, r_threshold):
+    """Eq. 2 as printed: T_c = sqrt(1/R^4 - 1) / (2 pi f_D theta^2) per
+    (tx, rx), f_D = f |v| / c, theta the angle between the receiver's motion
+    and the direction from transmitter to receiver; infinite when f_D theta^2
+    is zero."""
+    tx = np.asarray(tx_pos, np.float64)
+    rx = np.asarray(rx_pos, np.float64)
+    v = np.asarray(rx_vel, np.float64)
+    out = np.full((len(tx), len(rx)), np.inf)
+    num = np.sqrt(max(0.0, 1.0 / r_threshold ** 4 - 1.0))
+    for t in range(len(tx)):
+        for r in range(len(rx)):
+            k = rx[r] - tx[t]
+            kn, vn = np.linalg.norm(k), np.linalg.norm(v[r])
+            if kn == 0 or vn == 0:
+                continue
+            th = np.arccos(np.clip(np.dot(k, v[r]) / (kn * vn), -1.0, 1.0))
+            den = 2 * np.pi * (freq * vn / C_LIGHT) * th * th
+            if den > 0:
+                out[t, r] = num / den
+    return out

@@ -558,6 +558,24 @@ emrt_status emrt_channel_backward_noalloc(emrt_scene s, const emrt_paths *paths,
   return EMRT_OK;
 }
 
+emrt_status emrt_channel_correlation(const double *h, uint32_t n_frames, uint32_t n_pairs,
+                                     uint32_t max_lag, double *R, emrt_stream stream) {
+  if (!h || !R || n_frames == 0 || n_pairs == 0) return EMRT_ERR_INVALID_ARG;
+  launch_correlation(h, n_frames, n_pairs, max_lag, R, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_coherence_time(emrt_scene s, double freq_hz, double r_threshold, double *tc,
+                                emrt_stream stream) {
+  if (!s || !tc || !(freq_hz > 0) || !(r_threshold > 0) || !(r_threshold <= 1))
+    return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  launch_coherence(emrt::geom(s), freq_hz, r_threshold, tc, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
 emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
   if (!s) return EMRT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;

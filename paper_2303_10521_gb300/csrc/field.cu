@@ -443,7 +443,68 @@ __global__ void k_grad_reduce(GeomView g, MatView m, const uint32_t *rec, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Channel statistics over time (Sec. III-B)
+// Eq. 1 read as the normalised autocovariance of g = |h| over the frames:
+// R(tau) = (mean_{t < F - tau} g(t) g(t + tau) - mu^2) / (mean g^2 - mu^2)
+__global__ void k_correlation(const double *h, uint32_t F, uint32_t P, uint32_t L, double *R) {
+  uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (uint64_t)P * (L + 1)) return;
+  uint32_t p = (uint32_t)(id / (L + 1)), tau = (uint32_t)(id % (L + 1));
+  double s1 = 0.0, s2 = 0.0;
+  for (uint32_t t = 0; t < F; t++) {
+    const double *z = h + 2ull * ((uint64_t)t * P + p);
+    double g = sqrt(z[0] * z[0] + z[1] * z[1]);
+    s1 += g;
+    s2 += g * g;
+  }
+  double mu = s1 / F, var = s2 / F - mu * mu;
+  double c = 0.0;
+  uint32_t n = tau < F ? F - tau : 0;
+  for (uint32_t t = 0; t < n; t++) {
+    const double *a = h + 2ull * ((uint64_t)t * P + p);
+    const double *b = h + 2ull * ((uint64_t)(t + tau) * P + p);
+    c += sqrt(a[0] * a[0] + a[1] * a[1]) * sqrt(b[0] * b[0] + b[1] * b[1]);
+  }
+  double r = 0.0;
+  if (n > 0 && var > 0.0) r = (c / n - mu * mu) / var;
+  R[id] = r;
+}
+
+// Eq. 2 as printed: T_c = sqrt(1/R^4 - 1) / (2 pi f_D theta^2), f_D = f |v| / c
+// the maximum Doppler shift of the receiver, theta the angle between its
+// motion and the direction from the transmitter to the receiver
+__global__ void k_coherence(GeomView g, double freq, double r_thr, double *tc) {
+  uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= g.n_tx * g.n_rx) return;
+  uint32_t t = id / g.n_rx, r = id % g.n_rx;
+  float3 a = f3(g.tx_pos[t]), b = f3(g.rx_pos[r]), v = f3(g.rx_vel[r]);
+  double kx = (double)b.x - a.x, ky = (double)b.y - a.y, kz = (double)b.z - a.z;
+  double kn = sqrt(kx * kx + ky * ky + kz * kz);
+  double vn = sqrt((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+  double out = INFINITY;
+  if (kn > 0.0 && vn > 0.0) {
+    double c = ((double)v.x * kx + (double)v.y * ky + (double)v.z * kz) / (kn * vn);
+    double th = acos(fmin(1.0, fmax(-1.0, c)));
+    double fd = freq * vn / kC;
+    double den = 2.0 * kPi * fd * th * th;
+    double num = sqrt(fmax(0.0, 1.0 / (r_thr * r_thr * r_thr * r_thr) - 1.0));
+    if (den > 0.0) out = num / den;
+  }
+  tc[id] = out;
+}
+
 }  // namespace
+
+void launch_correlation(const double *h, uint32_t n_frames, uint32_t n_pairs, uint32_t max_lag,
+                        double *R, cudaStream_t s) {
+  uint64_t n = (uint64_t)n_pairs * (max_lag + 1);
+  emrt::note_launch(), k_correlation<<<ceil_div(n, 256), 256, 0, s>>>(h, n_frames, n_pairs, max_lag, R);
+}
+
+void launch_coherence(const GeomView &g, double freq, double r_thr, double *tc, cudaStream_t s) {
+  emrt::note_launch(), k_coherence<<<ceil_div((uint64_t)g.n_tx * g.n_rx, 256), 256, 0, s>>>(g, freq, r_thr, tc);
+}
 
 void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                   uint32_t cap, double freq, double *path_out, cudaStream_t s) {

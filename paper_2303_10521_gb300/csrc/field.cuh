@@ -25,5 +25,10 @@ void launch_field_adjoint(const GeomView &g, MatView m, const uint32_t *rec, con
                           double *partial, double *grad_eps, double *grad_sigma, double *grad_tx,
                           cudaStream_t s);
 int adjoint_grid();
+// Eq. 1 (normalised autocovariance of |h| over frames) and Eq. 2 (coherence
+// time) of Sec. III-B
+void launch_correlation(const double *h, uint32_t n_frames, uint32_t n_pairs, uint32_t max_lag,
+                        double *R, cudaStream_t s);
+void launch_coherence(const GeomView &g, double freq, double r_thr, double *tc, cudaStream_t s);
 
 }  // namespace emrt

@@ -206,6 +206,22 @@ class Scene:
                                                _stream(stream)), "emrt_channel_backward")
         return ge, gs, gt
 
+    def coherence_time(self, freq: float, r_threshold: float = 0.5, stream=None) -> torch.Tensor:
+        """Eq. 2 coherence time (s) per (tx, rx) for the current frame."""
+        tc = torch.empty((self.n_tx, self.n_rx), dtype=torch.float64, device=self.device)
+        N.check(self.lib.emrt_coherence_time(self.h, float(freq), float(r_threshold),
+                                             _ptr(tc), _stream(stream)), "emrt_coherence_time")
+        return tc
+
+    def refresh_interval(self, freq: float, dt: float, r_threshold: float = 0.5,
+                         quantile: float = 0.5) -> int:
+        """Frames a cached path set stays within the coherence time:
+        max(1, floor(T_c / dt)) with T_c the given quantile over the pairs."""
+        tc = self.coherence_time(freq, r_threshold).flatten()
+        q = float(torch.quantile(tc[torch.isfinite(tc)], quantile)) if torch.isfinite(tc).any() \
+            else float("inf")
+        return max(1, int(q // dt)) if q != float("inf") else 1 << 30
+
     def sync(self, stream=None) -> dict:
         st = N.Stats()
         code = self.lib.emrt_sync(self.h, _stream(stream), C.byref(st))
@@ -271,3 +287,15 @@ class Batch:
         buf = C.create_string_buffer(128)
         N.check(self.lib.emrt_batch_config(self.h, buf, 128), "emrt_batch_config")
         return buf.value.decode()
+
+
+def channel_correlation(h_series: torch.Tensor, max_lag: int, stream=None) -> torch.Tensor:
+    """Eq. 1 over frames: h_series [n_frames, n_pairs, 2] float64 (device) ->
+    R [n_pairs, max_lag + 1]."""
+    lib = N.load()
+    h = h_series.to(torch.float64).contiguous()
+    F, P = int(h.shape[0]), int(h.shape[1])
+    R = torch.empty((P, max_lag + 1), dtype=torch.float64, device=h.device)
+    N.check(lib.emrt_channel_correlation(_ptr(h), F, P, int(max_lag), _ptr(R), _stream(stream)),
+            "emrt_channel_correlation")
+    return R
