@@ -142,6 +142,23 @@ typedef struct {
 emrt_status emrt_trace(emrt_scene sc, const emrt_trace_params *p,
                        emrt_paths *out, emrt_stream s);
 
+/* Backward discovery (Sec. II-A: ray tracing from the receiver in the
+ * visibility step): shoot-and-bounce from receivers, with the same Fibonacci
+ * ray set p (per receiver instead of per Tx) and reception spheres of the
+ * same radius r(L) around every transmitter.  Paths are reciprocal, so each
+ * candidate is turned round -- transmitter first, face IDs in the order met
+ * from the transmitter -- and then deduplicated, accepted and written exactly
+ * as by emrt_trace (same record layout and canonical order; word 7 holds
+ * the smallest backward ray index that found the path).
+ * rx_ids: device uint32[n_ids] receiver indices to shoot from (distinct, each
+ * < n_rx), or NULL for every receiver (n_ids ignored).  The ray ids pack
+ * source << (32 - b) | ray index with b = bits(n_sources - 1), so the ray
+ * count per receiver must be <= 2^(32 - b), and n_sources x count < 2^32;
+ * otherwise EMRT_ERR_INVALID_ARG.  Capacity handling as emrt_trace. */
+emrt_status emrt_trace_backward(emrt_scene sc, const emrt_trace_params *p,
+                                const uint32_t *rx_ids, uint32_t n_ids,
+                                emrt_paths *out, emrt_stream s);
+
 /* Cached frame (Sec. II-A path caching, Sec. III-B): re-runs image-method
  * acceptance and occlusion on every record of `cache` with the current
  * poses; removes the paths that failed (keeps order) unless

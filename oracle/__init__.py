@@ -18,6 +18,7 @@ Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import os
 import subprocess
 import sys
@@ -192,6 +193,47 @@ def trace_list(os_, n_rays, max_depth, ray_idx, eps_abs=1e-4, eps_rel=0.0, threa
         if n <= cap:
             return out[:n], marg, segs
         cap = int(n)
+
+
+# ---------------------------------------------------------------------------
+# Backward tracing (Sec. II-A: rays shot from the receiver side).  A path is
+# reciprocal -- the same face sequence joins Tx and Rx in either direction --
+# so backward discovery is forward discovery in the frame with the roles
+# exchanged, followed by turning each record round.
+def backward_scene(scene, frame, rx_ids=None, **kw) -> OracleScene:
+    """The frame with the roles exchanged: the receivers rx_ids (all when
+    None) shoot as transmitters, the transmitters receive."""
+    ids = np.arange(len(frame.rx_pos)) if rx_ids is None else np.asarray(rx_ids, np.int64)
+    fr = dataclasses.replace(frame, tx_pos=np.asarray(frame.rx_pos)[ids],
+                             tx_vel=np.asarray(frame.rx_vel)[ids],
+                             rx_pos=frame.tx_pos, rx_vel=frame.tx_vel)
+    return OracleScene(scene, fr, **kw)
+
+
+def reverse_paths(p, rx_ids=None):
+    """Records of the role-exchanged frame (tx = shooting receiver's position
+    in rx_ids, rx = transmitter, faces in the order met from the receiver)
+    in forward orientation: tx first, rx = rx_ids[source], faces reversed."""
+    out = np.array(p, PATH_DTYPE, copy=True)
+    src = p["tx"].astype(np.int64)
+    out["tx"] = p["rx"]
+    out["rx"] = src if rx_ids is None else np.asarray(rx_ids, np.int64)[src]
+    for d in range(1, MAX_DEPTH + 1):
+        sel = p["depth"] == d
+        for k in range(d):
+            out["face"][sel, k] = p["face"][sel, d - 1 - k]
+    return out
+
+
+def trace_backward(scene, frame, n_rays, max_depth, rx_ids=None, offset=0, stride=1,
+                   count=None, eps_abs=1e-4, eps_rel=0.0, threads=None):
+    """Backward SBR discovery from the receivers rx_ids with reception spheres
+    at the transmitters.  Returns (candidates in forward orientation,
+    ray_marg, ray_segs); ray_marg rows are positions in rx_ids."""
+    ob = backward_scene(scene, frame, rx_ids)
+    c, marg, segs = trace(ob, n_rays, max_depth, offset=offset, stride=stride, count=count,
+                          eps_abs=eps_abs, eps_rel=eps_rel, threads=threads)
+    return reverse_paths(c, rx_ids), marg, segs
 
 
 def key_fields(p):

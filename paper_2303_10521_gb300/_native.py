@@ -72,6 +72,8 @@ SIGNATURES = {
     "emrt_scene_destroy": (None, [vp]),
     "emrt_scene_update_dynamic": (C.c_int, [vp, vp, vp, vp, vp, u32, vp, vp, u32, vp]),
     "emrt_trace": (C.c_int, [vp, C.POINTER(TraceParams), C.POINTER(PathsC), vp]),
+    "emrt_trace_backward": (C.c_int, [vp, C.POINTER(TraceParams), vp, C.c_uint32,
+                                      C.POINTER(PathsC), vp]),
     "emrt_revalidate": (C.c_int, [vp, C.POINTER(PathsC), u32, vp]),
     "emrt_cache_merge": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(PathsC), vp]),
     "emrt_channel": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, dbl,

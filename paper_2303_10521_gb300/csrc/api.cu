@@ -214,6 +214,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = bvh4_collapse(s->stat, st))) return fail(e);
   if ((e = bvh_alloc(s->dyn, PRIM_BOX, std::max(s->V, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->rxb, PRIM_POINT, std::max(s->max_rx, 2u)))) return fail(e);
+  if ((e = bvh_alloc(s->txb, PRIM_POINT, std::max(s->max_tx, 2u)))) return fail(e);
   uint32_t V1 = std::max(s->V, 1u);
   if ((e = grow(&s->veh_half, c, V1))) return fail(e); c = 0;
   if ((e = grow(&s->veh_lo, c, V1))) return fail(e); c = 0;
@@ -238,7 +239,8 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
 void emrt_scene_destroy(emrt_scene s) {
   if (!s) return;
   cudaFree(s->face_plane); cudaFree(s->face_info); cudaFree(s->face_vert); cudaFree(s->bbox);
-  bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb);
+  bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb); bvh_free(s->txb);
+  cudaFree(s->src_pos);
   cudaFree(s->veh_half); cudaFree(s->veh_lo); cudaFree(s->veh_hi); cudaFree(s->veh_vel);
   cudaFree(s->rx_pos); cudaFree(s->rx_vel); cudaFree(s->tx_pos); cudaFree(s->tx_vel);
   cudaFree(s->ctr); cudaFree(s->hist); cudaFree(s->partial);
@@ -285,22 +287,30 @@ emrt_status emrt_scene_update_dynamic(emrt_scene s, const float *veh_pos, const 
   return EMRT_OK;
 }
 
-emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out,
-                       emrt_stream stream) {
-  if (!s || !p || check_paths(out) != EMRT_OK) return EMRT_ERR_INVALID_ARG;
-  if (!s->updated) return EMRT_ERR_STATE;
-  if (p->max_depth > EMRT_MAX_DEPTH || p->n_rays == 0 || p->ray_stride == 0 ||
-      p->ray_offset >= p->n_rays)
-    return EMRT_ERR_INVALID_ARG;
-  uint64_t count = p->ray_count ? p->ray_count
-                                : (p->n_rays - p->ray_offset + p->ray_stride - 1) / p->ray_stride;
-  if (count == 0 || p->ray_offset + (count - 1) * p->ray_stride >= p->n_rays ||
-      count > (1u << 24) || count * s->n_tx >= (1ull << 32))
-    return EMRT_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Bits needed to hold 0 .. v-1 (at least 1).
+int id_bits(uint64_t v) {
+  int b = 1;
+  while (b < 32 && (1ull << b) < v) b++;
+  return b;
+}
+
+// Discovery from the n_src source points gt.tx_pos with reception spheres at
+// the points of gt.rxb (forward: transmitters -> receivers; backward:
+// receivers -> transmitters), then, when backward, the candidates' reversal
+// to forward orientation (receiver ids from rx_ids), and the common tail:
+// canonical dedup, image-method acceptance in the scene's forward geometry
+// and compaction into out.  count: rays per source; jbits: ray-index bits of
+// the ray ids.
+emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t count,
+                      const GeomView &gt, uint32_t n_src, int jbits, bool backward,
+                      const uint32_t *rx_ids, emrt_paths *out, cudaStream_t st) {
   uint32_t nf = s->Fs + 6 * s->V;
   KeyLayout kl = key_layout(s->n_tx, s->n_rx, nf + 1, (int)p->max_depth);
   if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
   Counters *c = s->ctr;
   // primary direction table of this ray set (built once, kept in an LRU of 4)
   emrt_scene_s::DirTable *tab = nullptr;
@@ -324,7 +334,7 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     tab->count = (uint32_t)count;
   }
   tab->last_use = ++s->dt_clock;
-  uint64_t nrays = count * s->n_tx;
+  uint64_t nrays = count * n_src;
   if (p->max_depth > 0 && nrays > s->ray_cap) {
     cudaFree(s->rays[0]);
     cudaFree(s->rays[1]);
@@ -363,7 +373,7 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
   cudaEventRecord(s->ev[0], st);
   for (uint32_t b = 0; b <= p->max_depth; b++) {
     BounceLaunch L;
-    L.g = g;
+    L.g = gt;
     L.rin = b ? s->rays[(b - 1) & 1] : nullptr;
     L.order = nullptr;
     if (b > 0 && sort_rays) {  // reorder reflected rays for coherent traversal
@@ -386,6 +396,7 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     L.kappa = kappa;
     L.b = (int)b;
     L.K = (int)p->max_depth;
+    L.jbits = jbits;
     cudaEventRecord(s->evb[2 * b], st);
     launch_bounce(L, grid, st, (p->flags & EMRT_TRACE_WIDE_BVH) != 0);
     cudaEventRecord(s->evb[2 * b + 1], st);
@@ -393,6 +404,7 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
   s->ev_bounces = p->max_depth + 1;
   cudaEventRecord(s->ev[1], st);
   emrt::note_launch(), k_check_cand<<<1, 1, 0, st>>>(c, s->cand_cap);
+  if (backward) launch_reverse_candidates(s->cand, &c->n_cand, s->cand_cap, rx_ids, st);
   dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
   cudaEventRecord(s->ev[2], st);
   launch_accept(g, s->uniq, &c->n_unique, c, st);
@@ -406,6 +418,58 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
   s->ev_recorded = true;
   CK(cudaGetLastError());
   return EMRT_OK;
+}
+
+// Rays per source of a trace call (0 when the parameters are invalid).
+uint64_t ray_count(const emrt_trace_params *p) {
+  if (p->max_depth > EMRT_MAX_DEPTH || p->n_rays == 0 || p->ray_stride == 0 ||
+      p->ray_offset >= p->n_rays)
+    return 0;
+  uint64_t count = p->ray_count ? p->ray_count
+                                : (p->n_rays - p->ray_offset + p->ray_stride - 1) / p->ray_stride;
+  if (count == 0 || p->ray_offset + (count - 1) * p->ray_stride >= p->n_rays) return 0;
+  return count;
+}
+
+}  // namespace
+
+extern "C" {
+
+emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out,
+                       emrt_stream stream) {
+  if (!s || !p || check_paths(out) != EMRT_OK) return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  uint64_t count = ray_count(p);
+  if (count == 0 || count > (1u << 24) || count * s->n_tx >= (1ull << 32))
+    return EMRT_ERR_INVALID_ARG;
+  return run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, out,
+                   (cudaStream_t)stream);
+}
+
+emrt_status emrt_trace_backward(emrt_scene s, const emrt_trace_params *p, const uint32_t *rx_ids,
+                                uint32_t n_ids, emrt_paths *out, emrt_stream stream) {
+  if (!s || !p || check_paths(out) != EMRT_OK) return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  const uint32_t n_src = rx_ids ? n_ids : s->n_rx;
+  if (n_src == 0 || n_src > s->n_rx) return EMRT_ERR_INVALID_ARG;
+  uint64_t count = ray_count(p);
+  const int jbits = 32 - id_bits(n_src);
+  if (count == 0 || count > (1ull << jbits) || count * n_src >= (1ull << 32))
+    return EMRT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  GeomView gb = geom(s);
+  if (rx_ids) {
+    CK(grow(&s->src_pos, s->src_cap, n_src));
+    launch_gather_points(s->rx_pos, rx_ids, n_src, s->src_pos, st);
+    gb.tx_pos = s->src_pos;
+  } else {
+    gb.tx_pos = s->rx_pos;
+  }
+  CK(bvh_build_points(s->txb, s->tx_pos, s->n_tx, s->bbox, s->hist, st));
+  gb.rxb = s->txb.view();
+  gb.n_tx = n_src;
+  gb.n_rx = s->n_tx;
+  return run_trace(s, p, count, gb, n_src, jbits, true, rx_ids, out, st);
 }
 
 emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emrt_stream stream) {

@@ -15,6 +15,9 @@ struct emrt_scene_s {
   float4 *face_vert = nullptr;
   float4 *bbox = nullptr;  // [4]: lo, hi, scratch
   BVHBuf stat, dyn, rxb;
+  BVHBuf txb;                     // transmitter points (backward tracing)
+  float4 *src_pos = nullptr;      // receiver points shot from (backward tracing)
+  uint64_t src_cap = 0;
   float4 *veh_half = nullptr, *veh_lo = nullptr, *veh_hi = nullptr, *veh_vel = nullptr;
   float4 *rx_pos = nullptr, *rx_vel = nullptr, *tx_pos = nullptr, *tx_vel = nullptr;
   uint32_t n_rx = 0, n_tx = 0;

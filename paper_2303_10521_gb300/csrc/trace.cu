@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bounce(BounceLaunch L, 
           tx = (id >> 22) & 15u;
           j = id & 0x3fffffu;
         } else {
-          tx = id >> 24;
-          j = id & 0xffffffu;
+          tx = id >> L.jbits;
+          j = id & ((1u << L.jbits) - 1u);
         }
         fc[0] = R.faces.x; fc[1] = R.faces.y; fc[2] = R.faces.z; fc[3] = R.faces.w;
       }
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bounce(BounceLaunch L, 
         uint32_t slot = warp_append(L.n_out);
         Ray R;
         R.o_L = make_float4(p.x, p.y, p.z, Lacc + tbest);
-        uint32_t id = BATCH ? (sc << 26 | tx << 22 | j) : (tx << 24 | j);
+        uint32_t id = BATCH ? (sc << 26 | tx << 22 | j) : (tx << L.jbits | j);
         R.d_id = make_float4(r.x, r.y, r.z, __uint_as_float(id));
         R.faces = make_uint4(fc[0], fc[1], fc[2], fc[3]);
         L.rout[slot] = R;
@@ -467,6 +467,28 @@ __global__ void k_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, 
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 
+__global__ void k_gather_points(const float4 *pos, const uint32_t *ids, uint32_t n, float4 *out) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = pos[ids[i]];
+}
+
+__global__ void k_reverse_cand(uint32_t *cand, const uint32_t *n, uint32_t cap,
+                               const uint32_t *ids) {
+  const uint32_t cnt = min(*n, cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    uint4 *c = reinterpret_cast<uint4 *>(cand + 8ull * i);
+    uint4 a = c[0], b = c[1];
+    const uint32_t depth = a.z & 15u;
+    const uint32_t f[EMRT_MAX_DEPTH] = {a.w, b.x, b.y, b.z};
+    uint32_t r[EMRT_MAX_DEPTH];
+#pragma unroll
+    for (int k = 0; k < EMRT_MAX_DEPTH; k++)
+      r[k] = (uint32_t)k < depth ? f[depth - 1 - k] : EMRT_NO_FACE;
+    c[0] = make_uint4(a.y, ids ? ids[a.x] : a.x, a.z, r[0]);
+    c[1] = make_uint4(r[1], r[2], r[3], b.w);
+  }
+}
+
 __global__ void k_batch_first(const uint32_t *rec, const uint32_t *n, const uint32_t *flag,
                               const uint32_t *pos, uint32_t *first, uint32_t *cnt) {
   uint32_t c = *n;
@@ -681,5 +703,14 @@ void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const 
   emrt::note_launch(), k_concat<<<kPrimGrid * 4, 256, 0, s>>>(a, na, cap_a, b, nb, cap_b, dst, dst_cap, n_dst, ctr);
 }
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s) { emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(p, v); }
+
+void launch_gather_points(const float4 *pos, const uint32_t *ids, uint32_t n, float4 *out,
+                          cudaStream_t s) {
+  if (n) emrt::note_launch(), k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pos, ids, n, out);
+}
+void launch_reverse_candidates(uint32_t *cand, const uint32_t *n, uint32_t cap,
+                               const uint32_t *ids, cudaStream_t s) {
+  emrt::note_launch(), k_reverse_cand<<<kPrimGrid * 4, 256, 0, s>>>(cand, n, cap, ids);
+}
 
 }  // namespace emrt

@@ -35,6 +35,7 @@ struct BounceLaunch {
   Counters *ctr;
   float kappa;
   int b, K;
+  int jbits;             // single-scene ray ids: source << jbits | ray index j
 };
 // wide: traverse the static BVH's 4-wide collapse
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s, bool wide = false);
@@ -108,5 +109,17 @@ void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const 
                    const uint32_t *nb, uint32_t cap_b, uint32_t *dst, uint32_t dst_cap,
                    uint32_t *n_dst, Counters *ctr, cudaStream_t s);
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
+
+// Backward tracing.  out[i] = pos[ids[i]] for i < n (source points of the
+// selected receivers).
+void launch_gather_points(const float4 *pos, const uint32_t *ids, uint32_t n, float4 *out,
+                          cudaStream_t s);
+// Candidates found from the receiver side (word 0 = source index, word 1 =
+// transmitter, faces in the order met from the receiver) rewritten in place
+// in forward orientation: word 0 = transmitter, word 1 = ids[source] (or the
+// source index when ids is null), faces reversed; depth, flags and ray index
+// kept.  Records [0, min(*n, cap)).
+void launch_reverse_candidates(uint32_t *cand, const uint32_t *n, uint32_t cap,
+                               const uint32_t *ids, cudaStream_t s);
 
 }  // namespace emrt

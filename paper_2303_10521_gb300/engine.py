@@ -150,11 +150,46 @@ class Scene:
               keep_rejected=False, capacity=None, stream=None, retries=3,
               sort_rays=True, wide_bvh=False) -> Paths:
         """Plain discovery; grows scratch and output on capacity errors."""
+        return self._retry(lambda out: self.trace_async(
+            out, n_rays, max_depth, offset, stride, count, keep_rejected, sort_rays=sort_rays,
+            stream=stream, wide_bvh=wide_bvh), capacity, stream, retries, "emrt_trace")
+
+    def trace_backward_async(self, out: Paths, rx_ids: Optional[torch.Tensor] = None,
+                             n_rays=None, max_depth=None, offset=0, stride=1, count=0,
+                             keep_rejected=False, sort_rays=True, stream=None):
+        """Backward discovery from the receivers rx_ids (device int tensor;
+        None = every receiver); paths come out in forward orientation."""
+        p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
+                          int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
+                          int(stride), int(count),
+                          (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
+                          (N.TRACE_SORT_RAYS if sort_rays else 0))
+        ids, n_ids = None, 0
+        if rx_ids is not None:
+            ids = rx_ids.to(device=self.device, dtype=torch.int32).contiguous()
+            n_ids = int(ids.numel())
+            if n_ids == 0:  # an empty tensor has no address to pass
+                raise N.EmrtError(1, "emrt_trace_backward: empty receiver list")
+            self._keep_ids = ids  # alive until the stream has used it
+        pc = out.c()
+        N.check(self.lib.emrt_trace_backward(self.h, C.byref(p), _ptr(ids) if ids is not None
+                                             else None, n_ids, C.byref(pc), _stream(stream)),
+                "emrt_trace_backward")
+
+    def trace_backward(self, rx_ids: Optional[torch.Tensor] = None, n_rays=None, max_depth=None,
+                       offset=0, stride=1, count=0, keep_rejected=False, capacity=None,
+                       stream=None, retries=3, sort_rays=True) -> Paths:
+        """Backward discovery; grows scratch and output on capacity errors."""
+        return self._retry(lambda out: self.trace_backward_async(
+            out, rx_ids, n_rays, max_depth, offset, stride, count, keep_rejected,
+            sort_rays=sort_rays, stream=stream), capacity, stream, retries,
+            "emrt_trace_backward")
+
+    def _retry(self, launch, capacity, stream, retries, name) -> Paths:
         cap = capacity or max(4096, 8 * self.n_tx * self.n_rx)
         for _ in range(retries + 1):
             out = Paths(cap, self.device)
-            self.trace_async(out, n_rays, max_depth, offset, stride, count, keep_rejected,
-                             sort_rays=sort_rays, stream=stream, wide_bvh=wide_bvh)
+            launch(out)
             try:
                 self.last_stats = self.sync(stream)
                 return out
@@ -162,7 +197,7 @@ class Scene:
                 if e.code != 4:
                     raise
                 cap = max(cap, int(out.n()) + 1024)
-        raise N.EmrtError(4, "emrt_trace (after retries)")
+        raise N.EmrtError(4, name + " (after retries)")
 
     def revalidate(self, cache: Paths, keep=False, stream=None):
         pc = cache.c()

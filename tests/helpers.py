@@ -24,11 +24,13 @@ def keys(p) -> list:
     return [tuple(r) for r in oracle.key_fields(p)]
 
 
-def compare_candidates(gpu_unique, orc_cands, ray_marg):
+def compare_candidates(gpu_unique, orc_cands, ray_marg, rx_rows=None):
     """Discovery parity.  Every oracle candidate found by a ray whose outcome
     is outside the margin must be on the GPU; every GPU candidate must be an
     oracle candidate or come from a ray the oracle flags as marginal at or
-    before the candidate's depth.  Returns a summary dict."""
+    before the candidate's depth.  ray_marg rows are transmitters, or, for
+    backward discovery, receivers: rx_rows maps a receiver id to its row.
+    Returns a summary dict."""
     ou = oracle.dedup(orc_cands)
     okeys = keys(ou)
     oflag = dict(zip(okeys, ou["flag"].tolist()))
@@ -40,8 +42,9 @@ def compare_candidates(gpu_unique, orc_cands, ray_marg):
     for k, p in zip(gkeys, gpu_unique):
         if k in oflag:
             continue
-        tx, j, depth = int(p["tx"]), int(p["ray"]), int(p["depth"])
-        if ray_marg[tx, j] <= depth:
+        row = int(p["tx"]) if rx_rows is None else rx_rows[int(p["rx"])]
+        j, depth = int(p["ray"]), int(p["depth"])
+        if ray_marg[row, j] <= depth:
             extra_marg += 1
         else:
             extra_bad.append(k)

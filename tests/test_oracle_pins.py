@@ -456,3 +456,74 @@ def test_table1_constant_mode_two_ray_sum():
     k = 2 * math.pi * f / C
     h = _lam(f) / (4 * math.pi) * (np.exp(-1j * k * d1) / d1 + g["wall"] * np.exp(-1j * k * d2) / d2)
     assert abs(a.sum() - h) <= 1e-10 * abs(h)
+
+
+# ---------------------------------------------------------------------------
+# backward tracing (Sec. II-A): role exchange and record reversal
+# ---------------------------------------------------------------------------
+def test_reverse_paths_brute_force():
+    NO = oracle.NO_FACE
+    p = np.zeros(4, oracle.PATH_DTYPE)
+    p["tx"] = [0, 1, 2, 1]
+    p["rx"] = [3, 0, 1, 2]
+    p["depth"] = [0, 1, 3, 4]
+    p["face"] = [[NO, NO, NO, NO], [7, NO, NO, NO], [5, 9, 2, NO], [1, 2, 3, 4]]
+    p["ray"] = [11, 12, 13, 14]
+    p["flag"] = [0, 1, 2, 0]
+    r = oracle.reverse_paths(p, rx_ids=[10, 20, 30])
+    assert r["tx"].tolist() == [3, 0, 1, 2]
+    assert r["rx"].tolist() == [10, 20, 30, 20]
+    assert r["face"].tolist() == [[NO, NO, NO, NO], [7, NO, NO, NO], [2, 9, 5, NO],
+                                  [4, 3, 2, 1]]
+    assert r["depth"].tolist() == [0, 1, 3, 4]
+    assert r["ray"].tolist() == [11, 12, 13, 14] and r["flag"].tolist() == [0, 1, 2, 0]
+    # without an id list the source index is the receiver; turning a record
+    # round twice gives it back
+    q = oracle.reverse_paths(oracle.reverse_paths(p))
+    assert (q == p).all()
+
+
+def test_backward_discovery_matches_exhaustive_enumeration():
+    """Shooting from the receivers finds (almost) every path that the forward
+    exhaustive image enumeration proves valid, and nothing else."""
+    sc = S.toy_scene(seed=0)
+    fr = sc.frame(0)
+    ids = [0, 5, 10, 15]
+    o = oracle.OracleScene(sc, fr)
+    exact = oracle.enumerate_paths(o, 2)
+    exact = exact[np.isin(exact["rx"], ids)]
+    cands, marg, segs = oracle.trace_backward(sc, fr, sc.n_rays, 2, rx_ids=ids)
+    assert marg.shape == (len(ids), sc.n_rays)
+    assert set(cands["rx"].tolist()) <= set(ids) and set(cands["tx"].tolist()) == {0}
+    uniq = oracle.dedup(cands)
+    acc, _ = oracle.validate(o, uniq)
+    found = uniq[acc]
+    k_exact = {tuple(r) for r in oracle.key_fields(exact)}
+    k_found = {tuple(r) for r in oracle.key_fields(found)}
+    assert k_found <= k_exact
+    a, _, _ = oracle.field(o, exact, 3.5e9)
+    w = np.abs(a) ** 2
+    hit = np.array([tuple(r) in k_found for r in oracle.key_fields(exact)])
+    assert w[hit].sum() / w.sum() > 0.99
+    assert hit.mean() > 0.9
+    # the same paths as forward discovery, up to the rays that miss a path
+    fc, _, _ = oracle.trace(o, sc.n_rays, 2)
+    fu = oracle.dedup(fc[np.isin(fc["rx"], ids)])
+    fa, _ = oracle.validate(o, fu)
+    k_fwd = {tuple(r) for r in oracle.key_fields(fu[fa])}
+    both = k_fwd & k_found
+    wk = dict(zip([tuple(r) for r in oracle.key_fields(exact)], w))
+    assert sum(wk[k] for k in both) / w.sum() > 0.98
+
+
+def test_backward_subset_is_the_restriction_of_the_full_set():
+    """Receivers shoot independently: tracing from a subset gives exactly the
+    full backward candidates of those receivers (same rays, same indices)."""
+    sc = S.toy_scene(seed=2)
+    fr = sc.frame(0)
+    full, _, _ = oracle.trace_backward(sc, fr, 20000, 2)
+    sub, _, _ = oracle.trace_backward(sc, fr, 20000, 2, rx_ids=[3, 11])
+    ref = full[np.isin(full["rx"], [3, 11])]
+    key = lambda p: sorted(map(tuple, np.concatenate(
+        [oracle.key_fields(p), p["ray"][:, None].astype(np.int64)], 1).tolist()))
+    assert len(ref) > 10 and key(sub) == key(ref)
