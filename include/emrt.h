@@ -254,6 +254,34 @@ emrt_status emrt_channel_correlation(const double *h, uint32_t n_frames, uint32_
 emrt_status emrt_coherence_time(emrt_scene sc, double freq_hz, double r_threshold, double *tc,
                                 emrt_stream s);
 
+/* Per-receiver re-discovery schedule for cached frames.  Sec. III-A cuts a
+ * receiver's trajectory into segments where spatial consistency is lost --
+ * the LoS/NLoS condition or the position changes -- and reuses the channel
+ * within a segment; Sec. III-B reuses cached paths within the coherence time
+ * (Eq. 2).  Call once per frame after emrt_scene_update_dynamic.  Receiver r
+ * is due for re-discovery when any of these holds:
+ *   - it was never discovered (state[r][3] < 0);
+ *   - the line of sight of some (tx, r) pair -- its direct path accepted by
+ *     the image-method/occlusion test of emrt_trace, same margins -- differs
+ *     from the one recorded at r's last discovery;
+ *   - |p_r - state[r][0..2]|^2 >= d_seg^2 (FP64 from the float32 values);
+ *   - the frames since r's last discovery, plus this one, reach
+ *     min(max_interval, max(1, floor(T_c / dt_s))), T_c the smallest Eq. 2
+ *     coherence time of r over the transmitters (emrt_coherence_time with
+ *     freq_hz, r_threshold); dt_s = 0 leaves out T_c (interval max_interval).
+ * A due receiver's state becomes (p_r, 0) and its LoS conditions are
+ * recorded; another receiver's frame count (state[r][3]) advances by one.
+ * state: device float [n_rx][4], caller-owned, start with w = -1;
+ * los_ref: device uint8 [n_tx][n_rx], caller-owned (any initial value);
+ * ids: device uint32 [n_rx] receives the due receivers in ascending order
+ * and *n_due (device uint32) their number -- the list emrt_trace_backward
+ * takes.  max_interval >= 1, dt_s >= 0, d_seg >= 0, freq_hz > 0 and
+ * r_threshold in (0, 1], else EMRT_ERR_INVALID_ARG. */
+emrt_status emrt_refresh_schedule(emrt_scene sc, float *state, uint8_t *los_ref, double freq_hz,
+                                  double r_threshold, double dt_s, float d_seg,
+                                  uint32_t max_interval, uint32_t *ids, uint32_t *n_due,
+                                  emrt_stream s);
+
 typedef struct {
   uint64_t segments[EMRT_MAX_DEPTH + 1]; /* closest-hit segments per bounce */
   uint64_t candidates;        /* reception-sphere detections                 */

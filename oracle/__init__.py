@@ -435,3 +435,43 @@ def coherence_time(tx_pos, rx_pos, rx_vel, freq, r_threshold):
             if den > 0:
                 out[t, r] = num / den
     return out
+
+
+def refresh_schedule(os_: OracleScene, state, los_ref, freq, r_threshold, dt, d_seg,
+                     max_interval):
+    """Per-receiver re-discovery rule (Sec. III-A trajectory segments where
+    the LoS condition or position changes; Sec. III-B reuse within the Eq. 2
+    coherence time).  Receiver r is due when never discovered (state w < 0),
+    when the LoS of one of its pairs (direct path through the acceptance
+    test) differs from los_ref, when it moved d_seg or more since its last
+    discovery, or when the frames since then plus this one reach
+    min(max_interval, max(1, floor(min_tx T_c / dt))) (dt = 0: max_interval).  Returns (due ids,
+    new state, new los_ref); inputs are not modified."""
+    k = os_._keep
+    rx = k["rx"].astype(np.float64)
+    n_tx, n_rx = os_.n_tx, os_.n_rx
+    direct = np.zeros(n_tx * n_rx, PATH_DTYPE)
+    direct["tx"] = np.repeat(np.arange(n_tx), n_rx)
+    direct["rx"] = np.tile(np.arange(n_rx), n_tx)
+    direct["face"] = NO_FACE
+    los, _ = validate(os_, direct)
+    los = los.reshape(n_tx, n_rx).astype(np.uint8)
+    tc = coherence_time(k["tx"], k["rx"], k["rxv"], freq, r_threshold).min(axis=0)
+    state = np.array(state, np.float32, copy=True)
+    ref = np.array(los_ref, np.uint8, copy=True)
+    due = []
+    for r in range(n_rx):
+        never = state[r, 3] < 0
+        frames = 0 if never else int(state[r, 3]) + 1
+        moved2 = float(np.sum((rx[r] - state[r, :3].astype(np.float64)) ** 2))
+        iv = np.floor(tc[r] / dt) if dt > 0 else np.inf
+        interval = max_interval if iv >= max_interval else int(max(1.0, iv))
+        d = (never or bool(np.any(los[:, r] != ref[:, r])) or moved2 >= float(np.float32(d_seg)) ** 2
+             or frames >= interval)
+        if d:
+            due.append(r)
+            state[r] = (k["rx"][r][0], k["rx"][r][1], k["rx"][r][2], 0.0)
+            ref[:, r] = los[:, r]
+        else:
+            state[r, 3] = frames
+    return np.asarray(due, np.int64), state, ref

@@ -85,6 +85,8 @@ SIGNATURES = {
     "emrt_sync": (C.c_int, [vp, vp, C.POINTER(Stats)]),
     "emrt_channel_correlation": (C.c_int, [vp, u32, u32, u32, vp, vp]),
     "emrt_coherence_time": (C.c_int, [vp, dbl, dbl, vp, vp]),
+    "emrt_refresh_schedule": (C.c_int, [vp, vp, vp, dbl, dbl, dbl, C.c_float, u32, vp, vp,
+                                        vp]),
     "emrt_batch_create": (C.c_int, [C.POINTER(vp), u32, C.POINTER(TraceParams),
                                     C.POINTER(PathsC), u32, vp, C.POINTER(vp)]),
     "emrt_batch_trace": (C.c_int, [vp, vp]),

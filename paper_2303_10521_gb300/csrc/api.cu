@@ -640,6 +640,33 @@ emrt_status emrt_coherence_time(emrt_scene s, double freq_hz, double r_threshold
   return EMRT_OK;
 }
 
+emrt_status emrt_refresh_schedule(emrt_scene s, float *state, uint8_t *los_ref, double freq_hz,
+                                  double r_threshold, double dt_s, float d_seg,
+                                  uint32_t max_interval, uint32_t *ids, uint32_t *n_due,
+                                  emrt_stream stream) {
+  if (!s || !state || !los_ref || !ids || !n_due || !(freq_hz > 0) || !(r_threshold > 0) ||
+      !(r_threshold <= 1) || !(dt_s >= 0) || !(d_seg >= 0) || max_interval == 0)
+    return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t pairs = (uint64_t)s->n_tx * s->n_rx;
+  CK(ensure_cand(s, std::max<uint64_t>(s->want_cand, pairs)));
+  Counters *c = s->ctr;
+  GeomView g = geom(s);
+  // line of sight of every pair: its direct path through the acceptance
+  // kernel (occlusion by static faces and vehicle boxes, same margins)
+  launch_los_records(s->n_tx, s->n_rx, s->uniq, st);
+  launch_set_u32(&c->tmp, (uint32_t)pairs, st);
+  launch_accept(g, s->uniq, &c->tmp, c, st);
+  launch_schedule(g, s->uniq, reinterpret_cast<float4 *>(state), los_ref, freq_hz, r_threshold,
+                  dt_s, d_seg, max_interval, s->head, st);
+  launch_set_u32(&c->tmp, s->n_rx, st);
+  exclusive_scan(&c->tmp, s->head, s->pos, n_due, s->partial, st);
+  launch_compact_ids(s->head, s->pos, s->n_rx, ids, st);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
 emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
   if (!s) return EMRT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;

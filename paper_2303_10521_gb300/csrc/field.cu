@@ -474,10 +474,8 @@ __global__ void k_correlation(const double *h, uint32_t F, uint32_t P, uint32_t 
 // Eq. 2 as printed: T_c = sqrt(1/R^4 - 1) / (2 pi f_D theta^2), f_D = f |v| / c
 // the maximum Doppler shift of the receiver, theta the angle between its
 // motion and the direction from the transmitter to the receiver
-__global__ void k_coherence(GeomView g, double freq, double r_thr, double *tc) {
-  uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= g.n_tx * g.n_rx) return;
-  uint32_t t = id / g.n_rx, r = id % g.n_rx;
+__device__ double coherence_time(const GeomView &g, uint32_t t, uint32_t r, double freq,
+                                 double r_thr) {
   float3 a = f3(g.tx_pos[t]), b = f3(g.rx_pos[r]), v = f3(g.rx_vel[r]);
   double kx = (double)b.x - a.x, ky = (double)b.y - a.y, kz = (double)b.z - a.z;
   double kn = sqrt(kx * kx + ky * ky + kz * kz);
@@ -491,7 +489,63 @@ __global__ void k_coherence(GeomView g, double freq, double r_thr, double *tc) {
     double num = sqrt(fmax(0.0, 1.0 / (r_thr * r_thr * r_thr * r_thr) - 1.0));
     if (den > 0.0) out = num / den;
   }
-  tc[id] = out;
+  return out;
+}
+
+__global__ void k_coherence(GeomView g, double freq, double r_thr, double *tc) {
+  uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= g.n_tx * g.n_rx) return;
+  tc[id] = coherence_time(g, id / g.n_rx, id % g.n_rx, freq, r_thr);
+}
+
+// direct-path record of every (tx, rx) pair, pair i = tx * n_rx + rx
+__global__ void k_los_records(uint32_t n_tx, uint32_t n_rx, uint32_t *rec) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_tx * n_rx) return;
+  uint4 *c = reinterpret_cast<uint4 *>(rec + 8ull * i);
+  c[0] = make_uint4(i / n_rx, i % n_rx, 0u, EMRT_NO_FACE);
+  c[1] = make_uint4(EMRT_NO_FACE, EMRT_NO_FACE, EMRT_NO_FACE, 0u);
+}
+
+// Due rule of the per-receiver re-discovery schedule (see emrt.h).  los:
+// the accepted direct-path records (w2 valid bit = line of sight).
+__global__ void k_schedule(GeomView g, const uint32_t *los, float4 *state, uint8_t *los_ref,
+                           double freq, double r_thr, double dt, float d_seg,
+                           uint32_t max_interval, uint32_t *flag) {
+  uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.n_rx) return;
+  const float4 st = state[r];
+  const float3 p = f3(g.rx_pos[r]);
+  bool due = st.w < 0.f;
+  double tc = INFINITY;
+  for (uint32_t t = 0; t < g.n_tx; t++) {
+    const uint32_t i = t * g.n_rx + r;
+    const uint8_t now = (los[8ull * i + 2] & EMRT_PATH_VALID) ? 1 : 0;
+    if (now != los_ref[i]) due = true;
+    tc = fmin(tc, coherence_time(g, t, r, freq, r_thr));
+  }
+  const double dx = (double)p.x - st.x, dy = (double)p.y - st.y, dz = (double)p.z - st.z;
+  if (dx * dx + dy * dy + dz * dz >= (double)d_seg * d_seg) due = true;
+  double iv = dt > 0.0 ? floor(tc / dt) : INFINITY;  // frames within the coherence time
+  uint32_t interval = iv >= (double)max_interval ? max_interval : (uint32_t)fmax(1.0, iv);
+  const uint32_t frames = st.w < 0.f ? 0u : (uint32_t)st.w + 1u;
+  if (frames >= interval) due = true;
+  if (due) {
+    state[r] = make_float4(p.x, p.y, p.z, 0.f);
+    for (uint32_t t = 0; t < g.n_tx; t++) {
+      const uint32_t i = t * g.n_rx + r;
+      los_ref[i] = (los[8ull * i + 2] & EMRT_PATH_VALID) ? 1 : 0;
+    }
+  } else {
+    state[r].w = (float)frames;
+  }
+  flag[r] = due ? 1u : 0u;
+}
+
+__global__ void k_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n,
+                              uint32_t *ids) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) ids[pos[i]] = i;
 }
 
 }  // namespace
@@ -504,6 +558,23 @@ void launch_correlation(const double *h, uint32_t n_frames, uint32_t n_pairs, ui
 
 void launch_coherence(const GeomView &g, double freq, double r_thr, double *tc, cudaStream_t s) {
   emrt::note_launch(), k_coherence<<<ceil_div((uint64_t)g.n_tx * g.n_rx, 256), 256, 0, s>>>(g, freq, r_thr, tc);
+}
+
+void launch_los_records(uint32_t n_tx, uint32_t n_rx, uint32_t *rec, cudaStream_t s) {
+  uint64_t n = (uint64_t)n_tx * n_rx;
+  emrt::note_launch(), k_los_records<<<ceil_div(n, 256), 256, 0, s>>>(n_tx, n_rx, rec);
+}
+
+void launch_schedule(const GeomView &g, const uint32_t *los, float4 *state, uint8_t *los_ref,
+                     double freq, double r_thr, double dt, float d_seg, uint32_t max_interval,
+                     uint32_t *flag, cudaStream_t s) {
+  emrt::note_launch(), k_schedule<<<ceil_div(g.n_rx, 128), 128, 0, s>>>(g, los, state, los_ref, freq, r_thr, dt, d_seg,
+                                                        max_interval, flag);
+}
+
+void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, uint32_t *ids,
+                        cudaStream_t s) {
+  emrt::note_launch(), k_compact_ids<<<ceil_div(n, 256), 256, 0, s>>>(flag, pos, n, ids);
 }
 
 void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,

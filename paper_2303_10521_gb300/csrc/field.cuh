@@ -30,5 +30,14 @@ int adjoint_grid();
 void launch_correlation(const double *h, uint32_t n_frames, uint32_t n_pairs, uint32_t max_lag,
                         double *R, cudaStream_t s);
 void launch_coherence(const GeomView &g, double freq, double r_thr, double *tc, cudaStream_t s);
+// Per-receiver re-discovery schedule: direct-path records of every pair,
+// the due rule per receiver (flag[r] = 1 when due; state and los_ref updated)
+// and the compaction of due ids (pos = exclusive scan of flag).
+void launch_los_records(uint32_t n_tx, uint32_t n_rx, uint32_t *rec, cudaStream_t s);
+void launch_schedule(const GeomView &g, const uint32_t *los, float4 *state, uint8_t *los_ref,
+                     double freq, double r_thr, double dt, float d_seg, uint32_t max_interval,
+                     uint32_t *flag, cudaStream_t s);
+void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, uint32_t *ids,
+                        cudaStream_t s);
 
 }  // namespace emrt

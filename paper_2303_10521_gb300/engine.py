@@ -248,6 +248,15 @@ class Scene:
                                              _ptr(tc), _stream(stream)), "emrt_coherence_time")
         return tc
 
+    def refresh_schedule(self, sched: "RefreshSchedule", stream=None):
+        """Due receivers of this frame (emrt_refresh_schedule): fills
+        sched.ids[:n] and sched.n_due (device) and updates sched's state."""
+        N.check(self.lib.emrt_refresh_schedule(
+            self.h, _ptr(sched.state), _ptr(sched.los_ref), float(sched.freq),
+            float(sched.r_threshold), float(sched.dt), float(sched.d_seg),
+            int(sched.max_interval), _ptr(sched.ids), _ptr(sched.n_due), _stream(stream)),
+            "emrt_refresh_schedule")
+
     def refresh_interval(self, freq: float, dt: float, r_threshold: float = 0.5,
                          quantile: float = 0.5) -> int:
         """Frames a cached path set stays within the coherence time:
@@ -265,6 +274,27 @@ class Scene:
         self.last_stats = out
         N.check(code, "emrt_sync")
         return out
+
+
+class RefreshSchedule:
+    """Caller-owned state of the per-receiver re-discovery schedule: each
+    receiver's position and frame count at its last discovery and the LoS
+    condition of its pairs then (device tensors), with the rule's
+    parameters: segment length d_seg (m), Eq. 2 frequency and correlation
+    threshold, frame interval dt (s) and the longest reuse in frames."""
+
+    def __init__(self, n_tx: int, n_rx: int, device, freq: float, dt: float,
+                 d_seg: float = 10.0, r_threshold: float = 0.5, max_interval: int = 50):
+        self.state = torch.full((n_rx, 4), -1.0, dtype=torch.float32, device=device)
+        self.los_ref = torch.zeros((n_tx, n_rx), dtype=torch.uint8, device=device)
+        self.ids = torch.zeros(n_rx, dtype=torch.int32, device=device)
+        self.n_due = torch.zeros(1, dtype=torch.int32, device=device)
+        self.freq, self.dt, self.d_seg = freq, dt, d_seg
+        self.r_threshold, self.max_interval = r_threshold, max_interval
+
+    def due(self) -> torch.Tensor:
+        """Due receiver ids of the last call (synchronises on the count)."""
+        return self.ids[:int(self.n_due.item())]
 
 
 class Batch:

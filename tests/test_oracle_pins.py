@@ -527,3 +527,54 @@ def test_backward_subset_is_the_restriction_of_the_full_set():
     key = lambda p: sorted(map(tuple, np.concatenate(
         [oracle.key_fields(p), p["ray"][:, None].astype(np.int64)], 1).tolist()))
     assert len(ref) > 10 and key(sub) == key(ref)
+
+
+# ---------------------------------------------------------------------------
+# per-receiver re-discovery schedule (Sec. III-A segments, Sec. III-B Eq. 2)
+# ---------------------------------------------------------------------------
+def test_refresh_schedule_rule_by_hand():
+    f, dt = 3.5e9, 1e-3
+    tx = (0.0, 0.0, 10.0)
+    rx = [(50.0, 0.0, 10.0),     # at rest: reused up to max_interval
+          (0.0, 60.0, 10.0),     # moves across the Tx direction at 1 m/s
+          (-40.0, 0.0, 10.0)]    # LoS blocked later by a vehicle
+    vel = [(0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, 0.0, 0.0)]
+    box = ((-22.0, -1.0, 0.0), (-18.0, 1.0, 20.0))
+    sc = S.custom_scene([], [], tx, rx, rx_vel=vel, boxes=[box], freq=f)
+    fr = sc.frame(0)
+    far = dataclasses.replace(fr, veh_pos=np.float32([[300.0, 300.0, 10.0]]))
+    o = oracle.OracleScene(sc, far)
+    state = np.full((3, 4), -1.0, np.float32)
+    ref = np.zeros((1, 3), np.uint8)
+    # Eq. 2 by hand for receiver 1: theta = pi/2, f_D = f * 1 / c, R = 0.5
+    tc = math.sqrt(1 / 0.5 ** 4 - 1) / (2 * math.pi * f / C * (math.pi / 2) ** 2)
+    assert 0.021 < tc < 0.022          # 21 frames of 1 ms
+    due, state, ref = oracle.refresh_schedule(o, state, ref, f, 0.5, dt, 10.0, 50)
+    assert due.tolist() == [0, 1, 2] and ref.tolist() == [[1, 1, 1]]
+    assert state[:, 3].tolist() == [0, 0, 0]
+    for k in range(1, 21):             # frames 1..20: nothing due
+        due, state, ref = oracle.refresh_schedule(o, state, ref, f, 0.5, dt, 10.0, 50)
+        assert due.tolist() == [], k
+    due, state, ref = oracle.refresh_schedule(o, state, ref, f, 0.5, dt, 10.0, 50)
+    assert due.tolist() == [1]         # frame 21 reaches floor(T_c / dt)
+    # the vehicle moves onto the line of sight of receiver 2
+    o2 = oracle.OracleScene(sc, fr)
+    due, state, ref = oracle.refresh_schedule(o2, state, ref, f, 0.5, dt, 10.0, 50)
+    assert due.tolist() == [2] and ref.tolist() == [[1, 1, 0]]
+    # segment length: moved exactly 10 m is due, 9.5 m is not
+    moved = dataclasses.replace(fr, rx_pos=np.float32([[60.0, 0.0, 10.0], [0.0, 60.0, 10.0],
+                                                       [-49.5, 0.0, 10.0]]))
+    o3 = oracle.OracleScene(sc, moved)
+    due, state, ref = oracle.refresh_schedule(o3, state, ref, f, 0.5, dt, 10.0, 50)
+    assert 0 in due.tolist() and 2 not in due.tolist()
+    # max_interval caps the reuse of a receiver at rest
+    st = np.zeros((3, 4), np.float32)
+    st[:, :3] = moved.rx_pos
+    st[:, 3] = 49                      # this frame is the 50th since discovery
+    due, _, _ = oracle.refresh_schedule(o3, st, np.array([[1, 1, 0]], np.uint8), f, 0.5, dt,
+                                        10.0, 50)
+    assert 0 in due.tolist() and 2 in due.tolist()
+    st[:, 3] = 48
+    due, _, _ = oracle.refresh_schedule(o3, st, np.array([[1, 1, 0]], np.uint8), f, 0.5, dt,
+                                        10.0, 50)
+    assert 0 not in due.tolist() and 2 not in due.tolist()
