@@ -52,6 +52,14 @@ def parse():
                     help="trace rays offset + stride*j only (profiling captures)")
     ap.add_argument("--no-sort-rays", action="store_true",
                     help="do not reorder reflected rays between bounces")
+    ap.add_argument("--per-rx-frames", type=int, default=30,
+                    help="per-receiver schedule leg: frames (0: skip)")
+    ap.add_argument("--backward-rays", type=int, default=50_000,
+                    help="per-receiver schedule leg: rays per due receiver")
+    ap.add_argument("--seg-len", type=float, default=10.0,
+                    help="per-receiver schedule leg: trajectory segment length (m)")
+    ap.add_argument("--max-interval", type=int, default=50,
+                    help="per-receiver schedule leg: longest reuse (frames)")
     ap.add_argument("--profile", action="store_true",
                     help="timed plain frames only (no e2e, cache or CPU legs)")
     return ap.parse_args()
@@ -423,6 +431,7 @@ def main():
         return rec, float(np.mean(db > 0.5)), float(np.median(db))
 
     acc_c, acc_p = [], []
+    plain_ref = {}
     for k in range(4, nc, 8):  # plain references, untimed
         g.update(cframes[k])
         g.trace_async(fresh, sort_rays=sort_rays)
@@ -430,9 +439,74 @@ def main():
         g.trace_async(fresh, n_rays=int(sc.n_rays * 0.9), sort_rays=sort_rays)
         pq = g.channel(fresh, sc.freqs[0]).rx[:, 0].cpu().numpy()
         g.sync()
+        plain_ref[k] = pp
         acc_c.append(agree(cached_rx[k - 1].cpu().numpy(), pp))
         acc_p.append(agree(pq, pp))
     acc_c, acc_p = np.array(acc_c), np.array(acc_p)
+
+    # ---------------- per-receiver schedule: the cache is revalidated every
+    # frame and only the receivers whose trajectory segment ended (LoS
+    # condition changed, moved seg_len, or max_interval frames) are
+    # re-discovered, by backward tracing from those receivers.
+    per_rx = None
+    nr = min(args.per_rx_frames, nc)
+    if nr > 1:
+        NB = args.backward_rays
+        sched = engine.RefreshSchedule(g.n_tx, n_rx, dev, freq=sc.freqs[0], dt=0.0,
+                                       d_seg=args.seg_len, max_interval=args.max_interval)
+        cache2 = engine.Paths(cap * 4, dev)
+        fresh2 = engine.Paths(cap * 2, dev)
+        warm_ids = torch.arange(min(n_rx, 2000), dtype=torch.int32, device=dev)
+        g.update(cframes[0])                  # untimed: sizes backward scratch
+        g.trace_backward_async(fresh2, warm_ids, n_rays=NB, sort_rays=sort_rays)
+        g.merge(cache2, fresh2)
+        g.sync()
+        g.trace_async(cache2, sort_rays=sort_rays)   # frame 0: full discovery
+        g.refresh_schedule(sched)
+        g.sync()
+        tc = g.coherence_time(sc.freqs[0]).min(dim=0).values
+        eq2_every_frame = float((tc < sc.dt * 2).float().mean())
+        rx_rec, n_due = [], []
+        torch.cuda.synchronize()
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(nr)]
+        for k in range(1, nr):
+            fe[k - 1].record(stream)
+            g.update(cframes[k])
+            g.revalidate(cache2)
+            g.refresh_schedule(sched)
+            ids = sched.due()
+            n_due.append(len(ids))
+            if len(ids):
+                g.trace_backward_async(fresh2, ids, n_rays=NB, sort_rays=sort_rays)
+                g.merge(cache2, fresh2)
+            for i, f in enumerate(sc.freqs):
+                chs[i] = g.channel(cache2, f, out=chs[i])
+            rx_rec.append(chs[0].rx[:, 0].clone())
+            g.sync()
+        fe[nr - 1].record(stream)
+        torch.cuda.synchronize()
+        pr_ms = [fe[k].elapsed_time(fe[k + 1]) for k in range(nr - 1)]
+        pr_ms_tot = max_over_ranks(sum(pr_ms), dev)
+        acc_r = np.array([agree(rx_rec[k - 1].cpu().numpy(), pp)
+                          for k, pp in plain_ref.items() if k < nr])
+        per_rx = {
+            "receiver_frames_per_s": job_throughput(n_rx * (nr - 1), ws, pr_ms_tot),
+            "frames": nr, "backward_rays_per_due_rx": NB,
+            "rule": {"segment_m": args.seg_len, "los_change": True,
+                     "max_interval": args.max_interval, "eq2": "off (dt = 0)"},
+            "eq2_note": "Eq. 2 at 3.5 GHz gives T_c under two frame intervals for this "
+                        "fraction of receivers, which the coherence-time rule would "
+                        "re-discover every frame or two",
+            "eq2_frac_under_two_frames": eq2_every_frame,
+            "due_per_frame_mean": float(np.mean(n_due)),
+            "due_per_frame_max": int(np.max(n_due)),
+            "frame_ms_median": float(np.median(pr_ms)),
+            "frame_ms_max": float(np.max(pr_ms)),
+            "accuracy_vs_plain": {"power_recall_mean": float(acc_r[:, 0].mean()),
+                                  "power_recall_min": float(acc_r[:, 0].min()),
+                                  "frac_rx_over_0p5db": float(acc_r[:, 1].mean()),
+                                  "median_abs_db": float(acc_r[:, 2].mean())}
+            if len(acc_r) else None}
     accuracy = {
         "frames": nc, "refresh_every": REFRESH, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
         "frame_ms_median": float(np.median(cached_frame_ms)),
@@ -471,6 +545,7 @@ def main():
             "mrays_per_s": mrays,
             "receiver_frames_per_s_cached": cached_val,
             "cached": accuracy,
+            "cached_per_receiver": per_rx,
             "segments_per_frame": seg / len(stats),
             "paths_per_frame": last["accepted"],
             "candidates_per_frame": last["candidates"],
