@@ -61,6 +61,9 @@ extern "C" {
                                           its 4-wide BVH (same results; on
                                           GB300 the binary LBVH is faster for
                                           the city scenes measured)           */
+#define EMRT_TRACE_STATIC_CACHE 0x8u   /* keep the static-geometry closest hit of
+                                          every ray segment between calls (see
+                                          emrt_trace); same results bit for bit */
 /* emrt_revalidate flags */
 #define EMRT_REVALIDATE_KEEP 0x1u      /* do not compact: flag only          */
 
@@ -141,6 +144,20 @@ typedef struct {
  * the excess is dropped and emrt_sync returns EMRT_ERR_CAPACITY. */
 emrt_status emrt_trace(emrt_scene sc, const emrt_trace_params *p,
                        emrt_paths *out, emrt_stream s);
+/* With EMRT_TRACE_STATIC_CACHE (temporal coherence of the static geometry,
+ * Sec. II-A/III-B: coherence between successive frames): every ray of the
+ * ray set follows one specular chain, segment b of ray (tx, j) having a
+ * static closest hit (t, face) that depends only on the transmitter position,
+ * the direction and the static faces hit before.  The scene keeps that hit
+ * per (bounce, tx, ray) -- 16 B each, (K+1) n_tx count entries, allocated with
+ * the ray set's direction table -- tagged with an epoch of the transmitter's
+ * position.  A later call reuses the entry of a segment whose chain hit only
+ * static faces so far (then its origin, direction and excluded face are
+ * those the entry was computed from) and still tests that segment against
+ * the vehicles and the receivers of this frame; every other segment is
+ * traced in full and, when its chain is still static, stored.  The output is
+ * the output of the same call without the flag, bit for bit.  Forward
+ * emrt_trace only (ignored by emrt_trace_backward and the batched form). */
 
 /* Backward discovery (Sec. II-A: ray tracing from the receiver in the
  * visibility step): shoot-and-bounce from receivers, with the same Fibonacci
@@ -304,6 +321,10 @@ typedef struct {
    * kernels alone (sum over bounces) */
   float traverse_ms, dedup_ms, accept_ms, trace_ms, bounce_ms;
   uint32_t pad2;
+  uint64_t static_reused;     /* segments whose static closest hit came from
+                                 the static-hit cache (EMRT_TRACE_STATIC_CACHE) */
+  uint64_t deferred;          /* chain segments handed from the cache walker
+                                 to the per-bounce traversal                  */
 } emrt_stats;
 
 /* Waits for the stream, reads and clears the device error word, returns the

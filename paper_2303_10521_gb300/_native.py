@@ -19,6 +19,7 @@ PATH_MARGINAL = 0x200
 TRACE_KEEP_REJECTED = 0x1
 TRACE_SORT_RAYS = 0x2
 TRACE_WIDE_BVH = 0x4
+TRACE_STATIC_CACHE = 0x8
 REVALIDATE_KEEP = 0x1
 NOALLOC_MAX_PATHS = 65536
 BATCH_AUTOTUNE = 0x1
@@ -59,7 +60,7 @@ class Stats(C.Structure):
                 ("error_bits", u32), ("required_candidates", u32), ("required_paths", u32),
                 ("pad", u32), ("traverse_ms", C.c_float), ("dedup_ms", C.c_float),
                 ("accept_ms", C.c_float), ("trace_ms", C.c_float), ("bounce_ms", C.c_float),
-                ("pad2", u32)]
+                ("pad2", u32), ("static_reused", u64), ("deferred", u64)]
 
 
 STATUS = {0: "EMRT_OK", 1: "EMRT_ERR_INVALID_ARG", 2: "EMRT_ERR_OOM", 3: "EMRT_ERR_CUDA",

@@ -227,7 +227,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if (s->V) emrt::note_launch(), k_half<<<ceil_div(s->V, 256), 256, 0, st>>>(d->veh_half, s->V, s->veh_half);
   for (int k = 0; k < 4; k++)
     if ((e = cudaEventCreate(&s->ev[k]))) return fail(e);
-  for (int k = 0; k < 2 * (EMRT_MAX_DEPTH + 1); k++)
+  for (int k = 0; k < 2 * (EMRT_MAX_DEPTH + 2); k++)
     if ((e = cudaEventCreate(&s->evb[k]))) return fail(e);
   e = cudaStreamSynchronize(st);
   if (!e) e = cudaGetLastError();
@@ -244,7 +244,13 @@ void emrt_scene_destroy(emrt_scene s) {
   cudaFree(s->veh_half); cudaFree(s->veh_lo); cudaFree(s->veh_hi); cudaFree(s->veh_vel);
   cudaFree(s->rx_pos); cudaFree(s->rx_vel); cudaFree(s->tx_pos); cudaFree(s->tx_vel);
   cudaFree(s->ctr); cudaFree(s->hist); cudaFree(s->partial);
-  for (auto &t : s->dt) cudaFree(t.dirs);
+  for (auto &t : s->dt) {
+    cudaFree(t.dirs);
+    cudaFree(t.stab);
+    cudaFree(t.tx_ref);
+    cudaFree(t.tx_epoch);
+  }
+  for (auto &r : s->defer) cudaFree(r);
   cudaFree(s->dt_scratch);
   cudaFree(s->rays[0]); cudaFree(s->rays[1]);
   for (int k = 0; k < 2; k++) { cudaFree(s->rkeys[k]); cudaFree(s->rvals[k]); }
@@ -253,7 +259,7 @@ void emrt_scene_destroy(emrt_scene s) {
   cudaFree(s->contrib);
   for (int k = 0; k < 4; k++)
     if (s->ev[k]) cudaEventDestroy(s->ev[k]);
-  for (int k = 0; k < 2 * (EMRT_MAX_DEPTH + 1); k++)
+  for (int k = 0; k < 2 * (EMRT_MAX_DEPTH + 2); k++)
     if (s->evb[k]) cudaEventDestroy(s->evb[k]);
   delete s;
 }
@@ -323,6 +329,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     for (auto &t : s->dt)
       if (t.last_use < tab->last_use) tab = &t;
     CK(grow(&tab->dirs, tab->cap, count));
+    tab->stab_slots = 0;  // a new ray set: its static-hit cache starts empty
     CK(grow(&s->dt_scratch, s->dt_scratch_cap, 4 * count));
     KeyW<1> *k0 = reinterpret_cast<KeyW<1> *>(s->dt_scratch), *k1 = k0 + count;
     uint32_t *v0 = s->dt_scratch + 2 * count, *v1 = v0 + count;
@@ -359,6 +366,39 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     }
     s->rsort_cap = nrays;
   }
+  const bool cache = (p->flags & EMRT_TRACE_STATIC_CACHE) && !backward;
+  if (cache) {
+    const uint32_t depth = p->max_depth + 1;
+    if (tab->stab_slots != nrays || tab->stab_depth < depth || !tab->stab) {
+      const uint64_t need = nrays * depth;
+      if (need > tab->stab_cap) {
+        cudaFree(tab->stab);
+        tab->stab = nullptr;
+        tab->stab_cap = 0;
+        CK(cudaMalloc(&tab->stab, sizeof(uint4) * need));
+        tab->stab_cap = need;
+      }
+      if (!tab->tx_ref) CK(cudaMalloc(&tab->tx_ref, sizeof(float4) * s->max_tx));
+      if (!tab->tx_epoch) CK(cudaMalloc(&tab->tx_epoch, sizeof(uint32_t) * s->max_tx));
+      // epochs restart at 0 and every entry at epoch 0: nothing is current
+      // until the epoch kernel has seen the transmitter positions
+      cudaMemsetAsync(tab->stab, 0, sizeof(uint4) * need, st);
+      cudaMemsetAsync(tab->tx_ref, 0xff, sizeof(float4) * s->max_tx, st);
+      cudaMemsetAsync(tab->tx_epoch, 0, sizeof(uint32_t) * s->max_tx, st);
+      tab->stab_slots = nrays;
+      tab->stab_depth = depth;
+    }
+    if (nrays > s->defer_cap) {
+      for (auto &r : s->defer) {
+        cudaFree(r);
+        r = nullptr;
+      }
+      s->defer_cap = 0;
+      for (uint32_t b = 0; b <= EMRT_MAX_DEPTH; b++)
+        CK(cudaMalloc(&s->defer[b], sizeof(Ray) * nrays));
+      s->defer_cap = nrays;
+    }
+  }
   uint64_t want = std::max<uint64_t>(s->want_cand,
                                      std::max<uint64_t>(1u << 16, 4ull * s->n_tx * s->n_rx * (p->max_depth + 1)));
   want = std::max<uint64_t>(want, out->capacity);
@@ -371,10 +411,38 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
                                     (3.0 * sqrt(3.0) * (double)p->n_rays)));
   int grid = bounce_grid();
   cudaEventRecord(s->ev[0], st);
-  for (uint32_t b = 0; b <= p->max_depth; b++) {
-    BounceLaunch L;
+  uint32_t nev = 0;  // traversal launches timed
+  if (cache) {
+    // static-hit cache: epochs of the transmitter positions, then the chain
+    // walker; what it cannot finish continues in the per-bounce traversal
+    launch_tx_epoch(s->tx_pos, tab->tx_ref, tab->tx_epoch, s->n_tx, st);
+    BounceLaunch L{};
     L.g = gt;
-    L.rin = b ? s->rays[(b - 1) & 1] : nullptr;
+    L.n_primary = (uint32_t)nrays;
+    L.dirs = tab->dirs;
+    L.count = (uint32_t)count;
+    L.cand = s->cand;
+    L.cand_cap = s->cand_cap;
+    L.n_cand = &c->n_cand;
+    L.work = &c->chain_work;
+    L.ctr = c;
+    L.kappa = kappa;
+    L.K = (int)p->max_depth;
+    L.jbits = jbits;
+    L.stab = tab->stab;
+    L.tx_epoch = tab->tx_epoch;
+    L.n_slots = (uint32_t)nrays;
+    ChainBufs D;
+    for (int b = 0; b <= EMRT_MAX_DEPTH; b++) D.rays[b] = s->defer[b];
+    cudaEventRecord(s->evb[0], st);
+    launch_chain(L, D, chain_grid(), st);
+    cudaEventRecord(s->evb[1], st);
+    nev = 1;
+  }
+  for (uint32_t b = 0; b <= p->max_depth; b++) {
+    BounceLaunch L{};
+    L.g = gt;
+    L.rin = cache ? s->defer[b] : (b ? s->rays[(b - 1) & 1] : nullptr);
     L.order = nullptr;
     if (b > 0 && sort_rays) {  // reorder reflected rays for coherent traversal
       launch_ray_keys(L.rin, &c->n_ray[b], s->bbox, s->rkeys[0], s->rvals[0], st);
@@ -386,7 +454,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.n_primary = (uint32_t)nrays;
     L.dirs = tab->dirs;
     L.count = (uint32_t)count;
-    L.rout = s->rays[b & 1];
+    L.rout = cache ? (b < p->max_depth ? s->defer[b + 1] : nullptr) : s->rays[b & 1];
     L.n_out = &c->n_ray[b + 1];
     L.cand = s->cand;
     L.cand_cap = s->cand_cap;
@@ -397,11 +465,17 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.b = (int)b;
     L.K = (int)p->max_depth;
     L.jbits = jbits;
-    cudaEventRecord(s->evb[2 * b], st);
+    if (cache) {
+      L.stab = tab->stab;
+      L.tx_epoch = tab->tx_epoch;
+      L.n_slots = (uint32_t)nrays;
+    }
+    cudaEventRecord(s->evb[2 * nev], st);
     launch_bounce(L, grid, st, (p->flags & EMRT_TRACE_WIDE_BVH) != 0);
-    cudaEventRecord(s->evb[2 * b + 1], st);
+    cudaEventRecord(s->evb[2 * nev + 1], st);
+    nev++;
   }
-  s->ev_bounces = p->max_depth + 1;
+  s->ev_bounces = nev;
   cudaEventRecord(s->ev[1], st);
   emrt::note_launch(), k_check_cand<<<1, 1, 0, st>>>(c, s->cand_cap);
   if (backward) launch_reverse_candidates(s->cand, &c->n_cand, s->cand_cap, rx_ids, st);
@@ -690,6 +764,8 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
     out->box_tests = h.box_tests;
     out->rx_node_visits = h.rx_node_visits;
     out->rx_tests = h.rx_tests;
+    out->static_reused = h.static_reused;
+    out->deferred = h.deferred;
     if (s->ev_recorded) {
       cudaEventElapsedTime(&out->traverse_ms, s->ev[0], s->ev[1]);
       cudaEventElapsedTime(&out->dedup_ms, s->ev[1], s->ev[2]);

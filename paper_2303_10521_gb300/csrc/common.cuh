@@ -26,6 +26,7 @@ struct Counters {
   uint32_t n_unique;
   uint32_t n_accepted;
   uint32_t tmp;
+  uint32_t chain_work;                     // work cursor of the cache walker
   unsigned long long segments[EMRT_MAX_DEPTH + 1];
   unsigned long long node_visits;     // static BVH inner nodes visited
   unsigned long long tri_tests;       // triangles tested
@@ -34,6 +35,8 @@ struct Counters {
   unsigned long long rx_node_visits;  // receiver BVH inner nodes visited
   unsigned long long rx_tests;        // receivers tested against a sphere
   unsigned long long occl_rays;
+  unsigned long long static_reused;   // static hits taken from the cache
+  unsigned long long deferred;        // chain segments handed to k_bounce
 };
 
 // ---------------------------------------------------------------------------
@@ -98,6 +101,20 @@ __device__ inline uint32_t warp_append(uint32_t *counter) {
   if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
   base = __shfl_sync(m, base, leader);
   return base + __popc(m & lanemask_lt());
+}
+
+// Warp-aggregated append to one of several counters: every active lane gets
+// a distinct slot of counters[key]; lanes are grouped by key first, one
+// atomicAdd per group.
+__device__ inline uint32_t warp_append_keyed(uint32_t *counters, uint32_t key) {
+  uint32_t m = __activemask();
+  uint32_t grp = __match_any_sync(m, key);
+  uint32_t lane = threadIdx.x & 31;
+  uint32_t leader = __ffs(grp) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(counters + key, (uint32_t)__popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  return base + __popc(grp & lanemask_lt());
 }
 
 // scene geometry (device views) shared by trace, acceptance and field

@@ -29,6 +29,13 @@ struct emrt_scene_s {
     uint64_t n = 0, off = 0, stride = 0, cap = 0, last_use = 0;
     uint32_t count = 0;
     float4 *dirs = nullptr;
+    // static-hit cache of this ray set: (depth) x (slots) entries, transmitter
+    // positions they were computed for and their epochs
+    uint4 *stab = nullptr;
+    uint64_t stab_cap = 0, stab_slots = 0;
+    uint32_t stab_depth = 0;
+    float4 *tx_ref = nullptr;
+    uint32_t *tx_epoch = nullptr;
   } dt[4];
   uint64_t dt_clock = 0;
   uint32_t *dt_scratch = nullptr;  // key/value scratch for building a table
@@ -36,6 +43,9 @@ struct emrt_scene_s {
   // ray ping-pong buffers and the coherence-sort scratch
   Ray *rays[2] = {nullptr, nullptr};
   uint64_t ray_cap = 0;
+  // per-bounce ray buffers of the static-hit cache form
+  Ray *defer[EMRT_MAX_DEPTH + 1] = {};
+  uint64_t defer_cap = 0;
   KeyW<1> *rkeys[2] = {nullptr, nullptr};
   uint32_t *rvals[2] = {nullptr, nullptr};
   uint64_t rsort_cap = 0;
@@ -49,7 +59,7 @@ struct emrt_scene_s {
   uint64_t contrib_cap = 0;
   emrt_status sticky = EMRT_OK;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t evb[2 * (EMRT_MAX_DEPTH + 1)] = {};  // around each k_bounce launch
+  cudaEvent_t evb[2 * (EMRT_MAX_DEPTH + 2)] = {};  // around each traversal launch
   uint32_t ev_bounces = 0;
   bool ev_recorded = false;
 };

@@ -135,24 +135,29 @@ class Scene:
             "emrt_scene_update_dynamic")
 
     def trace_async(self, out: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
-                    keep_rejected=False, sort_rays=True, stream=None, wide_bvh=False):
+                    keep_rejected=False, sort_rays=True, stream=None, wide_bvh=False,
+                    static_cache=False):
+        """Plain discovery into out (no sync).  static_cache: reuse the static
+        closest hits of earlier calls with this ray set (identical output)."""
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
                           (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
                           (N.TRACE_SORT_RAYS if sort_rays else 0) |
-                          (N.TRACE_WIDE_BVH if wide_bvh else 0))
+                          (N.TRACE_WIDE_BVH if wide_bvh else 0) |
+                          (N.TRACE_STATIC_CACHE if static_cache else 0))
         pc = out.c()
         N.check(self.lib.emrt_trace(self.h, C.byref(p), C.byref(pc), _stream(stream)),
                 "emrt_trace")
 
     def trace(self, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
               keep_rejected=False, capacity=None, stream=None, retries=3,
-              sort_rays=True, wide_bvh=False) -> Paths:
+              sort_rays=True, wide_bvh=False, static_cache=False) -> Paths:
         """Plain discovery; grows scratch and output on capacity errors."""
         return self._retry(lambda out: self.trace_async(
             out, n_rays, max_depth, offset, stride, count, keep_rejected, sort_rays=sort_rays,
-            stream=stream, wide_bvh=wide_bvh), capacity, stream, retries, "emrt_trace")
+            stream=stream, wide_bvh=wide_bvh, static_cache=static_cache), capacity, stream,
+            retries, "emrt_trace")
 
     def trace_backward_async(self, out: Paths, rx_ids: Optional[torch.Tensor] = None,
                              n_rays=None, max_depth=None, offset=0, stride=1, count=0,

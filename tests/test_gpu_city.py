@@ -95,3 +95,22 @@ def test_city_discovery_sampled_rays(city):
             bad.append(tuple(k))
     assert not bad, bad[:5]
     assert checked >= 250 and len(okeys) >= 250
+
+
+def test_city_static_cache_identical(city):
+    """The static-hit cache gives the plain trace's unique candidates bit for
+    bit at the benchmark size, on the cold frame and two frames later."""
+    sc, fr, g, allc, acc, o = city
+    ref = allc.records()
+    cold = g.trace(keep_rejected=True, sort_rays=True, static_cache=True).records()
+    assert np.array_equal(ref, cold)
+    for k in (2,):
+        g.update(sc.frame(k))
+        a = g.trace(keep_rejected=True, sort_rays=True).records()
+        sa = dict(g.last_stats)
+        b = g.trace(keep_rejected=True, sort_rays=True, static_cache=True).records()
+        sb = dict(g.last_stats)
+        assert np.array_equal(a, b)
+        assert sa["segments"] == sb["segments"]
+        assert sb["static_reused"] > 0.9 * sum(sb["segments"])
+    g.update(fr)
