@@ -60,6 +60,8 @@ def parse():
                     help="per-receiver schedule leg: trajectory segment length (m)")
     ap.add_argument("--max-interval", type=int, default=50,
                     help="per-receiver schedule leg: longest reuse (frames)")
+    ap.add_argument("--no-static-cache", action="store_true",
+                    help="cached legs: trace without the static-hit cache")
     ap.add_argument("--profile", action="store_true",
                     help="timed plain frames only (no e2e, cache or CPU legs)")
     return ap.parse_args()
@@ -329,10 +331,50 @@ def main():
                 "launch_ms": trav_ms / launches_trav}
     mrays = seg / (trav_ms / 1e3) / 1e6
 
+    # ---------------- the same frames with the static-hit cache: static
+    # closest hits kept between frames (transmitters fixed), vehicles and
+    # receivers tested every frame; output identical to the plain retrace
+    def step_c(k, st_list):
+        g.update(frames[k])
+        g.trace_async(out, stride=rs, sort_rays=sort_rays, static_cache=True)
+        for i, f in enumerate(sc.freqs):
+            chs[i] = g.channel(out, f, out=chs[i])
+        st_list.append(g.sync())
+
+    for k in range(args.warmup):                    # first call fills the cache
+        step_c(k, [])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    stats_c = []
+    e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e6.record(stream)
+    for k in range(args.warmup, total):
+        step_c(k, stats_c)
+    e7.record(stream)
+    torch.cuda.synchronize()
+    sc_ms = max_over_ranks(e6.elapsed_time(e7), dev)
+    rec_c = out.records()
+    g.trace_async(out, stride=rs, sort_rays=sort_rays)      # plain, same last frame
+    g.sync()
+    static_cache = {
+        "receiver_frames_per_s": job_throughput(n_rx * args.steps, ws, sc_ms),
+        "ms_per_step": sc_ms / args.steps,
+        "identical_to_plain": bool(np.array_equal(rec_c, out.records())),
+        "segments_per_frame": sum(sum(s["segments"]) for s in stats_c) / len(stats_c),
+        "static_reused_frac": sum(s["static_reused"] for s in stats_c) /
+                              max(1, sum(sum(s["segments"]) for s in stats_c)),
+        "deferred_per_frame": sum(s["deferred"] for s in stats_c) / len(stats_c),
+        "traversal_ms": sum(s["bounce_ms"] for s in stats_c) / len(stats_c),
+        "discovery_ms": sum(s["traverse_ms"] for s in stats_c) / len(stats_c),
+        "mrays_per_s": sum(sum(s["segments"]) for s in stats_c) /
+                       (sum(s["bounce_ms"] for s in stats_c) / 1e3) / 1e6}
+
     if args.profile:
         if rank == 0:
             last = stats[-1]
         print(json.dumps({"profile": True, "ms_per_step": t_ms / args.steps,
+                          "static_cache": static_cache,
                           "mrays_per_s": mrays, "roofline": roofline,
                           "per_segment": {k: last[k] / max(1, sum(last["segments"])) for k in
                                           ("node_visits", "tri_tests", "dyn_node_visits",
@@ -379,22 +421,24 @@ def main():
     # for that density) merged into the cache, and a full-density
     # rediscovery replaces it every REFRESH frames.
     nc = args.cached_frames
+    use_sc = not args.no_static_cache
     REFRESH, R_LOW = args.refresh, args.rediscovery_fraction
     cframes = [F(frame_dev(total + 1 + k)) for k in range(nc)]
     cache = engine.Paths(cap * 4, dev)
     fresh = engine.Paths(cap * 2, dev)
     for k in (nc - 2, nc - 1):  # untimed warm-up of the cached pipeline (sizes scratch)
         g.update(cframes[k])
-        g.trace_async(cache, sort_rays=sort_rays)
+        g.trace_async(cache, sort_rays=sort_rays, static_cache=use_sc)
         g.revalidate(cache)
-        g.trace_async(fresh, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays)
+        g.trace_async(fresh, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays,
+                      static_cache=use_sc)
         g.merge(cache, fresh)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
         chs[0].rx[:, 0].clone()  # the accuracy record below; loads its copy kernel
         g.sync()
     g.update(cframes[0])
-    g.trace_async(cache, sort_rays=sort_rays)
+    g.trace_async(cache, sort_rays=sort_rays, static_cache=use_sc)
     g.sync()
     cached_rx = []
     torch.cuda.synchronize()
@@ -406,10 +450,11 @@ def main():
         g.update(cframes[k])
         g.revalidate(cache)
         if REFRESH and k % REFRESH == 0:
-            g.trace_async(fresh, sort_rays=sort_rays)
+            g.trace_async(fresh, sort_rays=sort_rays, static_cache=use_sc)
             g.merge(cache, fresh)
         elif R_LOW:
-            g.trace_async(fresh, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays)
+            g.trace_async(fresh, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays,
+                          static_cache=use_sc)
             g.merge(cache, fresh)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
@@ -461,7 +506,7 @@ def main():
         g.trace_backward_async(fresh2, warm_ids, n_rays=NB, sort_rays=sort_rays)
         g.merge(cache2, fresh2)
         g.sync()
-        g.trace_async(cache2, sort_rays=sort_rays)   # frame 0: full discovery
+        g.trace_async(cache2, sort_rays=sort_rays, static_cache=use_sc)  # frame 0: full
         g.refresh_schedule(sched)
         g.sync()
         tc = g.coherence_time(sc.freqs[0]).min(dim=0).values
@@ -508,7 +553,7 @@ def main():
                                   "median_abs_db": float(acc_r[:, 2].mean())}
             if len(acc_r) else None}
     accuracy = {
-        "frames": nc, "refresh_every": REFRESH, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
+        "frames": nc, "refresh_every": REFRESH, "static_cache": use_sc, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
         "frame_ms_median": float(np.median(cached_frame_ms)),
         "frame_ms_max": float(np.max(cached_frame_ms)),
         "frame_ms": [round(x, 2) for x in cached_frame_ms],
@@ -544,6 +589,7 @@ def main():
                        "l2": "inputs larger than L2 (3.8 GB ray buffers per bounce)"},
             "mrays_per_s": mrays,
             "receiver_frames_per_s_cached": cached_val,
+            "plain_with_static_cache": static_cache,
             "cached": accuracy,
             "cached_per_receiver": per_rx,
             "segments_per_frame": seg / len(stats),
