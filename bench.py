@@ -114,9 +114,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_per_segment():
-    """DRAM bytes per closest-hit segment of k_bounce from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def ncu_summary():
+    """Figures of the committed ncu capture of k_bounce (DRAM bytes per
+    closest-hit segment, memory-hierarchy and issue counters), if it was
+    taken on the current kernel source; else None."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     kv = {}
@@ -124,11 +125,11 @@ def traffic_per_segment():
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_hash") != kernel_hash():
+    if kv.pop("kernel_hash", None) != kernel_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_segment"])
-    except (KeyError, ValueError):
+        return {k: float(v) for k, v in kv.items()}
+    except ValueError:
         return None
 
 
@@ -322,10 +323,12 @@ def main():
     launches_trav = (K + 1) * len(stats)
     peak, peak_kind = measured_peaks()
     achieved = (byt / launches_trav) / (trav_ms / launches_trav / 1e3) / 1e9
-    tps = traffic_per_segment()
+    ncu = ncu_summary()
+    tps = ncu.pop("dram_bytes_per_segment", None) if ncu else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": (tps * seg / launches_trav) if tps else None,
+                "ncu": ncu,
                 "kernel": "k_bounce (closest-hit traversal + reception spheres)",
                 "algorithmic_bytes_per_launch": byt / launches_trav,
                 "launch_ms": trav_ms / launches_trav}

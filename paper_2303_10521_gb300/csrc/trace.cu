@@ -135,7 +135,7 @@ __device__ inline bool static_chain(const uint32_t *fc, uint32_t b, uint32_t fs)
 // whose chain is still static comes from L.stab when its entry is current,
 // and is stored there otherwise.
 template <bool BATCH, int BLOCK, int FETCH, bool WIDE, bool TABLE = false>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
                                                   uint32_t n_scenes) {
   int stk[kStack];
   float stt[kStack];
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_bounce(BounceLaunch L, 
 // the per-bounce traversal, which continues the chain.  Segments, candidates
 // and continuations are exactly those of k_bounce.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_chain(BounceLaunch L, ChainBufs D) {
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, ChainBufs D) {
   int stk[kStack];
   float stt[kStack];
   TravStats st;
