@@ -444,7 +444,9 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.g = gt;
     L.rin = cache ? s->defer[b] : (b ? s->rays[(b - 1) & 1] : nullptr);
     L.order = nullptr;
-    if (b > 0 && sort_rays) {  // reorder reflected rays for coherent traversal
+    // reorder reflected rays for coherent traversal; the few segments the
+    // cache walker defers are not worth the sort's fixed cost (measured)
+    if (b > 0 && sort_rays && !cache) {
       launch_ray_keys(L.rin, &c->n_ray[b], s->bbox, s->rkeys[0], s->rvals[0], st);
       bool alt = radix_sort<1>(&c->n_ray[b], s->rkeys[0], s->rvals[0], s->rkeys[1], s->rvals[1],
                                32, s->hist, st, nrays);
