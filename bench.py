@@ -32,8 +32,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Mrays/s traversal and receiver-frames/s channel update (2x2km,10k Rx), cached vs plain"
 UNIT = "receiver-frames/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bounce_city_traffic.txt")
-KERNEL_SOURCES = ["paper_2303_10521_gb300/csrc/trace.cu",
-                  "paper_2303_10521_gb300/csrc/traverse.cuh"]
+# sources of k_bounce (the figures of the committed ncu capture hold while
+# these are unchanged)
+KERNEL_SOURCES = ["paper_2303_10521_gb300/csrc/bounce.cuh",
+                  "paper_2303_10521_gb300/csrc/traverse.cuh",
+                  "paper_2303_10521_gb300/csrc/common.cuh"]
 
 
 def parse():

@@ -116,6 +116,7 @@ cudaError_t ensure_cand(emrt_scene_s *s, uint64_t need) {
   e = grow(&s->uniq, c, cap * 8); if (e) return e; c = 0;
   e = grow(&s->head, c, cap); if (e) return e; c = 0;
   e = grow(&s->pos, c, cap); if (e) return e; c = 0;
+  e = grow(&s->apts, c, cap * (EMRT_MAX_DEPTH + 2)); if (e) return e; c = 0;
   for (int k = 0; k < 2; k++) {
     e = grow(&s->keys[k], c, cap); if (e) return e; c = 0;
     e = grow(&s->vals[k], c, cap); if (e) return e; c = 0;
@@ -254,7 +255,7 @@ void emrt_scene_destroy(emrt_scene s) {
   cudaFree(s->dt_scratch);
   cudaFree(s->rays[0]); cudaFree(s->rays[1]);
   for (int k = 0; k < 2; k++) { cudaFree(s->rkeys[k]); cudaFree(s->rvals[k]); }
-  cudaFree(s->cand); cudaFree(s->uniq); cudaFree(s->head); cudaFree(s->pos);
+  cudaFree(s->cand); cudaFree(s->uniq); cudaFree(s->head); cudaFree(s->pos); cudaFree(s->apts);
   for (int k = 0; k < 2; k++) { cudaFree(s->keys[k]); cudaFree(s->vals[k]); }
   cudaFree(s->contrib);
   for (int k = 0; k < 4; k++)
@@ -483,7 +484,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   if (backward) launch_reverse_candidates(s->cand, &c->n_cand, s->cand_cap, rx_ids, st);
   dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
   cudaEventRecord(s->ev[2], st);
-  launch_accept(g, s->uniq, &c->n_unique, c, st);
+  launch_accept(g, s->uniq, &c->n_unique, c, s->apts, s->cand_cap, st);
   launch_keep_flags(s->uniq, &c->n_unique, (p->flags & EMRT_TRACE_KEEP_REJECTED) ? 1 : 0, s->head,
                     st);
   exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_accepted, s->partial, st);
@@ -558,7 +559,7 @@ emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emr
   // clamp the count to the capacity before acceptance
   emrt::note_launch(), k_clamp_count<<<1, 1, 0, st>>>(cache->count, cache->capacity, &c->n_eff);
   launch_copy_records(cache->rec, &c->n_eff, s->uniq, cache->capacity, st);
-  launch_accept(g, s->uniq, &c->n_eff, c, st);
+  launch_accept(g, s->uniq, &c->n_eff, c, s->apts, s->cand_cap, st);
   int keep_all = (flags & EMRT_REVALIDATE_KEEP) ? 1 : 0;
   launch_keep_flags(s->uniq, &c->n_eff, keep_all, s->head, st);
   exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_accepted, s->partial, st);
@@ -733,7 +734,7 @@ emrt_status emrt_refresh_schedule(emrt_scene s, float *state, uint8_t *los_ref, 
   // kernel (occlusion by static faces and vehicle boxes, same margins)
   launch_los_records(s->n_tx, s->n_rx, s->uniq, st);
   launch_set_u32(&c->tmp, (uint32_t)pairs, st);
-  launch_accept(g, s->uniq, &c->tmp, c, st);
+  launch_accept(g, s->uniq, &c->tmp, c, s->apts, s->cand_cap, st);
   launch_schedule(g, s->uniq, reinterpret_cast<float4 *>(state), los_ref, freq_hz, r_threshold,
                   dt_s, d_seg, max_interval, s->head, st);
   launch_set_u32(&c->tmp, s->n_rx, st);

@@ -33,6 +33,7 @@ struct emrt_batch_s {
   uint32_t *rvals[2] = {nullptr, nullptr};
   uint32_t cand_cap = 0, want_cand = 0;
   uint32_t *cand = nullptr, *uniq = nullptr, *head = nullptr, *pos = nullptr;
+  float4 *apts = nullptr;  // acceptance scratch (reflection points)
   KeyW<4> *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
   uint32_t *first = nullptr, *cnt = nullptr;
@@ -62,9 +63,10 @@ emrt_status st_of(cudaError_t e) {
   } while (0)
 
 void free_scratch(emrt_batch_s *b) {
-  cudaFree(b->cand); cudaFree(b->uniq); cudaFree(b->head); cudaFree(b->pos);
+  cudaFree(b->cand); cudaFree(b->uniq); cudaFree(b->head); cudaFree(b->pos); cudaFree(b->apts);
   for (int k = 0; k < 2; k++) { cudaFree(b->keys[k]); cudaFree(b->vals[k]); }
   b->cand = b->uniq = b->head = b->pos = nullptr;
+  b->apts = nullptr;
   b->keys[0] = b->keys[1] = nullptr;
   b->vals[0] = b->vals[1] = nullptr;
   b->cand_cap = 0;
@@ -78,6 +80,7 @@ cudaError_t alloc_cand(emrt_batch_s *b, uint64_t cap) {
   if ((e = cudaMalloc(&b->uniq, 32 * cap))) return e;
   if ((e = cudaMalloc(&b->head, 4 * cap))) return e;
   if ((e = cudaMalloc(&b->pos, 4 * cap))) return e;
+  if ((e = cudaMalloc(&b->apts, sizeof(float4) * (EMRT_MAX_DEPTH + 2) * cap))) return e;
   for (int k = 0; k < 2; k++) {
     if ((e = cudaMalloc(&b->keys[k], sizeof(KeyW<4>) * cap))) return e;
     if ((e = cudaMalloc(&b->vals[k], 4 * cap))) return e;
@@ -155,7 +158,7 @@ void enqueue(emrt_batch_s *b, int variant, bool sort_rays, cudaStream_t st) {
   launch_heads(ks, &c->n_eff, b->head, st);
   exclusive_scan(&c->n_eff, b->head, b->pos, &c->n_unique, b->partial, st);
   launch_unique(b->cand, ks, vs, b->head, b->pos, &c->n_eff, b->uniq, st);
-  launch_accept_batched(b->d_tab, b->uniq, &c->n_unique, c, st);
+  launch_accept_batched(b->d_tab, b->uniq, &c->n_unique, c, b->apts, b->cand_cap, st);
   launch_keep_flags(b->uniq, &c->n_unique, 0, b->head, st);
   exclusive_scan(&c->n_unique, b->head, b->pos, &c->n_accepted, b->partial, st);
   launch_batch_scatter(b->d_tab, b->n, b->uniq, &c->n_unique, b->head, b->pos, b->first, b->cnt,

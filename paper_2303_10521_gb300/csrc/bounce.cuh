@@ -1,0 +1,316 @@
+// Closest-hit traversal kernels of one discovery bounce (k_bounce) and the
+// static-hit cache walker (k_chain), with their device helpers.  Included by
+// trace.cu only, inside its anonymous namespace.
+#pragma once
+
+__device__ inline float3 face_normal_f(const GeomView &g, uint32_t f) {
+  if (f < g.n_static_faces) {
+    double4 p = g.face_plane[f];
+    return make_float3((float)p.x, (float)p.y, (float)p.z);
+  }
+  uint32_t j = (f - g.n_static_faces) % 6u;
+  float s = (j & 1u) ? 1.f : -1.f;
+  int ax = j >> 1;
+  return make_float3(ax == 0 ? s : 0.f, ax == 1 ? s : 0.f, ax == 2 ? s : 0.f);
+}
+
+__device__ inline void rx_bounds(const BVHView &b, float3 &lo, float3 &hi) {
+  if (b.n_prims >= 2) {
+    float4 n0 = ldg4(b.nodes), n1 = ldg4(b.nodes + 1), n2 = ldg4(b.nodes + 2);
+    lo = make_float3(fminf(n0.x, n1.x), fminf(n0.z, n1.z), fminf(n2.x, n2.z));
+    hi = make_float3(fmaxf(n0.y, n1.y), fmaxf(n0.w, n1.w), fmaxf(n2.y, n2.w));
+  } else if (b.n_prims == 1) {
+    lo = hi = f3(ldg4(b.prims));
+  } else {
+    lo = hi = make_float3(0.f, 0.f, 0.f);
+  }
+}
+
+__device__ inline void add_u64(unsigned long long *p, unsigned long long v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(p, v);
+}
+
+// Specular continuation of a segment that hit `face` at t: hit point p and
+// mirrored unit direction r.  Explicit roundings, so that every kernel that
+// continues a chain produces the same bits.
+__device__ inline void reflect_step(const GeomView &g, uint32_t face, float3 o, float3 d, float t,
+                                    float3 &p, float3 &r) {
+  const float3 n = face_normal_f(g, face);
+  p = make_float3(__fmaf_rn(d.x, t, o.x), __fmaf_rn(d.y, t, o.y), __fmaf_rn(d.z, t, o.z));
+  const float dn = __fmul_rn(2.f, __fmaf_rn(d.z, n.z, __fmaf_rn(d.y, n.y, __fmul_rn(d.x, n.x))));
+  r = make_float3(__fmaf_rn(-n.x, dn, d.x), __fmaf_rn(-n.y, dn, d.y), __fmaf_rn(-n.z, dn, d.z));
+  const float inv = rsqrtf(__fmaf_rn(r.z, r.z, __fmaf_rn(r.y, r.y, __fmul_rn(r.x, r.x))));
+  r = make_float3(__fmul_rn(r.x, inv), __fmul_rn(r.y, inv), __fmul_rn(r.z, inv));
+}
+
+// Escape distance of a ray that hit nothing: the furthest projection of the
+// receiver bounds on the ray.
+__device__ inline float escape_t(float3 o, float3 d, float3 rlo, float3 rhi) {
+  return fmaxf(d.x * (rlo.x - o.x), d.x * (rhi.x - o.x)) +
+         fmaxf(d.y * (rlo.y - o.y), d.y * (rhi.y - o.y)) +
+         fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
+}
+
+// true when the first b reflections of a chain were all on static faces
+__device__ inline bool static_chain(const uint32_t *fc, uint32_t b, uint32_t fs) {
+  bool ok = true;
+#pragma unroll
+  for (uint32_t k = 0; k < EMRT_MAX_DEPTH; k++)
+    if (k < b && fc[k] >= fs) ok = false;
+  return ok;
+}
+
+// Closest-hit traversal of one bounce for every ray (persistent threads: each
+// warp takes FETCH rays at a time from a global cursor).  BATCH: rays of many
+// scenes, each ray's scene read from the table; otherwise the single scene in
+// L.g.  Per ray: nearest hit over the static triangles and the vehicle
+// boxes, reception-sphere detections on the traced segment (appended as
+// candidates), and the specular continuation (appended to the next buffer).
+// TABLE: static-hit cache form (single scene): the static hit of a segment
+// whose chain is still static comes from L.stab when its entry is current,
+// and is stored there otherwise.
+template <bool BATCH, int BLOCK, int FETCH, bool WIDE, bool TABLE = false>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
+                                                  uint32_t n_scenes) {
+  int stk[kStack];
+  float stt[kStack];
+  TravStats st;
+  uint32_t segs = 0, reused = 0;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t n_items = (L.b == 0 && !TABLE) ? L.n_primary : *L.n_in;
+  float3 rlo, rhi;
+  if (!BATCH) rx_bounds(L.g.rxb, rlo, rhi);
+  const uint32_t NO = EMRT_NO_FACE;
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(L.work, (uint32_t)FETCH);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_items) break;
+    for (uint32_t sub = 0; sub < (uint32_t)FETCH; sub += 32) {
+      uint32_t i = base + sub + lane;
+      if (i >= n_items) break;
+      segs++;
+      float3 o, d;
+      float Lacc;
+      uint32_t tx, j, sc = 0;
+      uint32_t fc[EMRT_MAX_DEPTH] = {NO, NO, NO, NO};
+      if (L.b == 0 && !TABLE) {
+        uint32_t local = i, count = L.count;
+        const float4 *dirs = L.dirs;
+        if (BATCH) {  // scene of a primary item: last scene whose range starts <= i
+          uint32_t lo = 0, hi = n_scenes;
+          while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (tab[mid].prim_begin <= i) lo = mid;
+            else hi = mid;
+          }
+          sc = lo;
+          local = i - tab[sc].prim_begin;
+          count = tab[sc].count;
+          dirs = tab[sc].dirs;
+        }
+        tx = local / count;
+        uint32_t k = local - tx * count;
+        float4 dj = dirs[k];
+        d = f3(dj);
+        j = __float_as_uint(dj.w);
+        o = f3((BATCH ? tab[sc].g : L.g).tx_pos[tx]);
+        Lacc = 0.f;
+      } else {
+        Ray R = L.rin[L.order ? L.order[i] : i];
+        o = f3(R.o_L);
+        Lacc = R.o_L.w;
+        d = f3(R.d_id);
+        uint32_t id = __float_as_uint(R.d_id.w);
+        if (BATCH) {
+          sc = id >> 26;
+          tx = (id >> 22) & 15u;
+          j = id & 0x3fffffu;
+        } else {
+          tx = id >> L.jbits;
+          j = id & ((1u << L.jbits) - 1u);  // TABLE: direction-table position
+        }
+        fc[0] = R.faces.x; fc[1] = R.faces.y; fc[2] = R.faces.z; fc[3] = R.faces.w;
+      }
+      const GeomView &g = BATCH ? tab[sc].g : L.g;
+      const float kappa = BATCH ? tab[sc].kappa : L.kappa;
+      const int K = BATCH ? (int)tab[sc].K : L.K;
+      if (BATCH) rx_bounds(g.rxb, rlo, rhi);
+      uint32_t prev = L.b > 0 ? fc[L.b - 1] : NO;
+      RayQ q;
+      ray_setup(q, o, d);
+      float tbest = FLT_MAX;
+      uint32_t face = NO;
+      bool have = false;
+      uint32_t slot = 0, ep = 0;
+      const bool keep = TABLE && static_chain(fc, (uint32_t)L.b, g.n_static_faces);
+      if (keep) {
+        slot = (uint32_t)L.b * L.n_slots + tx * L.count + j;
+        ep = L.tx_epoch[tx];
+        const uint4 e = L.stab[slot];
+        if (e.z == ep) {
+          tbest = __uint_as_float(e.x);
+          face = e.y;
+          have = true;
+          reused++;
+        }
+      }
+      if (!have) {
+        trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+        if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
+      }
+      uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
+      trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
+      bool hit = face != NO;
+      float t_end = hit ? tbest : escape_t(o, d, rlo, rhi);
+      t_end = fmaxf(t_end, 0.f);
+      float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
+      const uint32_t b = (uint32_t)L.b;
+      const uint32_t w0 = BATCH ? (sc << 8 | tx) : tx;
+      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, [&](uint32_t rx) {
+        uint32_t slot = warp_append(L.n_cand);
+        if (slot < L.cand_cap) {
+          const uint32_t jj = TABLE ? __float_as_uint(L.dirs[j].w) : j;
+          uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
+          c[0] = make_uint4(w0, rx, b, fc[0]);
+          c[1] = make_uint4(fc[1], fc[2], fc[3], jj);
+        }
+      });
+      if (hit && L.b < K) {
+        float3 p, r;
+        reflect_step(g, face, o, d, tbest, p, r);
+        fc[L.b] = face;
+        uint32_t slot = warp_append(L.n_out);
+        Ray R;
+        R.o_L = make_float4(p.x, p.y, p.z, Lacc + tbest);
+        uint32_t id = BATCH ? (sc << 26 | tx << 22 | j) : (tx << L.jbits | j);
+        R.d_id = make_float4(r.x, r.y, r.z, __uint_as_float(id));
+        R.faces = make_uint4(fc[0], fc[1], fc[2], fc[3]);
+        L.rout[slot] = R;
+      }
+    }
+  }
+  __syncwarp();
+  add_u64(&L.ctr->segments[L.b], segs);
+  add_u64(&L.ctr->node_visits, st.nodes);
+  add_u64(&L.ctr->tri_tests, st.tris);
+  add_u64(&L.ctr->dyn_node_visits, st.dnodes);
+  add_u64(&L.ctr->box_tests, st.boxes);
+  add_u64(&L.ctr->rx_node_visits, st.rnodes);
+  add_u64(&L.ctr->rx_tests, st.rxs);
+  if (TABLE) add_u64(&L.ctr->static_reused, reused);
+  if (st.overflow) atomicOr(&L.ctr->err, ERR_STACK);
+}
+
+// Chain walker of the static-hit cache: one thread follows the whole specular
+// chain of a primary ray (tx, direction-table position k) as long as its
+// segments have current cache entries and its reflections stay on static
+// faces: static hit from the cache, vehicle boxes and reception spheres of
+// this frame, reflection.  The first segment it cannot finish that way (no
+// current entry, or the chain reflected off a vehicle) goes to D.rays[b] for
+// the per-bounce traversal, which continues the chain.  Segments, candidates
+// and continuations are exactly those of k_bounce.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, ChainBufs D) {
+  int stk[kStack];
+  float stt[kStack];
+  TravStats st;
+  uint32_t segs[EMRT_MAX_DEPTH + 1] = {0, 0, 0, 0, 0};
+  uint32_t reused = 0, deferred = 0;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t n_items = L.n_primary;
+  const uint32_t fs = L.g.n_static_faces;
+  const uint32_t NO = EMRT_NO_FACE;
+  float3 rlo, rhi;
+  rx_bounds(L.g.rxb, rlo, rhi);
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(L.work, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_items) break;
+    const uint32_t i = base + lane;
+    if (i >= n_items) continue;
+    const uint32_t tx = i / L.count;
+    const uint32_t k = i - tx * L.count;
+    const float4 dj = L.dirs[k];
+    const uint32_t j = __float_as_uint(dj.w);
+    const uint32_t ep = L.tx_epoch[tx];
+    const uint32_t id = tx << L.jbits | k;
+    float3 o = f3(L.g.tx_pos[tx]), d = f3(dj);
+    float Lacc = 0.f;
+    uint32_t f0 = NO, f1 = NO, f2 = NO, f3_ = NO;
+    int defer_b = -1;
+    for (int b = 0; b <= L.K; b++) {
+      const uint4 e = L.stab[(uint32_t)b * L.n_slots + i];
+      if (e.z != ep) {
+        defer_b = b;
+        break;
+      }
+      float tbest = __uint_as_float(e.x);
+      uint32_t face = e.y;
+      reused++;
+      segs[b]++;
+      RayQ q;
+      ray_setup(q, o, d);
+      // the face just left is static, so no vehicle is excluded
+      trace_boxes<false>(L.g.dyn, q, 0.f, tbest, face, fs, NO, NO, stk, stt, st);
+      const bool hit = face != NO;
+      float t_end = hit ? tbest : escape_t(o, d, rlo, rhi);
+      t_end = fmaxf(t_end, 0.f);
+      const float rmax = L.kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
+      const uint32_t bb = (uint32_t)b;
+      query_rx(L.g.rxb, q, t_end, Lacc, L.kappa, rmax, stk, stt, st, [&](uint32_t rx) {
+        uint32_t slot = warp_append(L.n_cand);
+        if (slot < L.cand_cap) {
+          uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
+          c[0] = make_uint4(tx, rx, bb, f0);
+          c[1] = make_uint4(f1, f2, f3_, j);
+        }
+      });
+      if (!hit || b == L.K) break;
+      float3 p, r;
+      reflect_step(L.g, face, o, d, tbest, p, r);
+      f0 = b == 0 ? face : f0;
+      f1 = b == 1 ? face : f1;
+      f2 = b == 2 ? face : f2;
+      f3_ = b == 3 ? face : f3_;
+      Lacc = Lacc + tbest;
+      o = p;
+      d = r;
+      if (face >= fs) {  // off a vehicle: the rest of the chain is not cached
+        defer_b = b + 1;
+        break;
+      }
+    }
+    if (defer_b >= 0) {
+      uint32_t slot = warp_append_keyed(L.ctr->n_ray, (uint32_t)defer_b);
+      Ray R;
+      R.o_L = make_float4(o.x, o.y, o.z, Lacc);
+      R.d_id = make_float4(d.x, d.y, d.z, __uint_as_float(id));
+      R.faces = make_uint4(f0, f1, f2, f3_);
+      D.rays[defer_b][slot] = R;
+      deferred++;
+    }
+  }
+  __syncwarp();
+  for (int b = 0; b <= EMRT_MAX_DEPTH; b++) add_u64(&L.ctr->segments[b], segs[b]);
+  add_u64(&L.ctr->dyn_node_visits, st.dnodes);
+  add_u64(&L.ctr->box_tests, st.boxes);
+  add_u64(&L.ctr->rx_node_visits, st.rnodes);
+  add_u64(&L.ctr->rx_tests, st.rxs);
+  add_u64(&L.ctr->static_reused, reused);
+  add_u64(&L.ctr->deferred, deferred);
+  if (st.overflow) atomicOr(&L.ctr->err, ERR_STACK);
+}
+
+__global__ void k_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n) {
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float4 a = pos[t], r = ref[t];
+  if (__float_as_uint(a.x) != __float_as_uint(r.x) || __float_as_uint(a.y) != __float_as_uint(r.y) ||
+      __float_as_uint(a.z) != __float_as_uint(r.z)) {
+    epoch[t] += 1u;
+    ref[t] = a;
+  }
+}

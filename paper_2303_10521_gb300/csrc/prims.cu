@@ -36,11 +36,20 @@ __global__ void __launch_bounds__(kPrimBlock) k_hist(const uint32_t *d_n, const 
 
 // Digit offsets from the block-major histogram hist[b][d] (G blocks):
 // offs[b][d] = sum_{d' < d} total[d'] + sum_{b' < b} hist[b'][d].  1024
-// threads: four groups of 256 (one thread per digit) split the G rows, so
-// every row access is a coalesced 1 KB load.
-__global__ void __launch_bounds__(1024) k_digit_offsets(uint32_t *hist, int G) {
+// threads: four groups of 256 (one thread per digit) split the rows, so
+// every row access is a coalesced 1 KB load.  Only the rows of blocks that
+// received keys (block_range's split of *d_n over G blocks) are read and
+// written; the others scatter nothing.
+__global__ void __launch_bounds__(1024) k_digit_offsets(const uint32_t *d_n, uint32_t *hist,
+                                                        int G) {
   __shared__ uint32_t part[4][256];
   __shared__ uint32_t base[256];
+  {
+    const uint32_t n = *d_n;
+    uint32_t per = (n + G - 1) / G;
+    per = (per + kPrimBlock - 1) / kPrimBlock * kPrimBlock;
+    G = per ? min(G, (int)((n + per - 1) / per)) : 0;
+  }
   const int d = threadIdx.x & 255, grp = threadIdx.x >> 8;
   const int per = (G + 3) / 4, b0 = min(G, grp * per), b1 = min(G, b0 + per);
   uint32_t s = 0;
@@ -202,7 +211,7 @@ bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *key
     KeyW<W> *ki = alt ? keys2 : keys, *ko = alt ? keys : keys2;
     uint32_t *vi = alt ? vals2 : vals, *vo = alt ? vals : vals2;
     emrt::note_launch(), k_hist<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
-    emrt::note_launch(), k_digit_offsets<<<1, 1024, 0, s>>>(hist, G);
+    emrt::note_launch(), k_digit_offsets<<<1, 1024, 0, s>>>(d_n, hist, G);
     emrt::note_launch(), k_scatter<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
     alt = !alt;
   }

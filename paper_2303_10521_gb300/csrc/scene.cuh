@@ -52,6 +52,7 @@ struct emrt_scene_s {
   // candidate and path scratch
   uint32_t cand_cap = 0, want_cand = 0;
   uint32_t *cand = nullptr, *uniq = nullptr, *head = nullptr, *pos = nullptr;
+  float4 *apts = nullptr;  // acceptance scratch: reflection points, point-major
   KeyW<4> *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
   // adjoint scratch

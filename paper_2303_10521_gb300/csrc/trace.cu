@@ -67,317 +67,7 @@ __global__ void k_dir_table(uint64_t n, uint64_t off, uint64_t stride, uint32_t 
 }
 
 // ----------------------------------------------------------------------------
-__device__ inline float3 face_normal_f(const GeomView &g, uint32_t f) {
-  if (f < g.n_static_faces) {
-    double4 p = g.face_plane[f];
-    return make_float3((float)p.x, (float)p.y, (float)p.z);
-  }
-  uint32_t j = (f - g.n_static_faces) % 6u;
-  float s = (j & 1u) ? 1.f : -1.f;
-  int ax = j >> 1;
-  return make_float3(ax == 0 ? s : 0.f, ax == 1 ? s : 0.f, ax == 2 ? s : 0.f);
-}
-
-__device__ inline void rx_bounds(const BVHView &b, float3 &lo, float3 &hi) {
-  if (b.n_prims >= 2) {
-    float4 n0 = ldg4(b.nodes), n1 = ldg4(b.nodes + 1), n2 = ldg4(b.nodes + 2);
-    lo = make_float3(fminf(n0.x, n1.x), fminf(n0.z, n1.z), fminf(n2.x, n2.z));
-    hi = make_float3(fmaxf(n0.y, n1.y), fmaxf(n0.w, n1.w), fmaxf(n2.y, n2.w));
-  } else if (b.n_prims == 1) {
-    lo = hi = f3(ldg4(b.prims));
-  } else {
-    lo = hi = make_float3(0.f, 0.f, 0.f);
-  }
-}
-
-__device__ inline void add_u64(unsigned long long *p, unsigned long long v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(p, v);
-}
-
-// Specular continuation of a segment that hit `face` at t: hit point p and
-// mirrored unit direction r.  Explicit roundings, so that every kernel that
-// continues a chain produces the same bits.
-__device__ inline void reflect_step(const GeomView &g, uint32_t face, float3 o, float3 d, float t,
-                                    float3 &p, float3 &r) {
-  const float3 n = face_normal_f(g, face);
-  p = make_float3(__fmaf_rn(d.x, t, o.x), __fmaf_rn(d.y, t, o.y), __fmaf_rn(d.z, t, o.z));
-  const float dn = __fmul_rn(2.f, __fmaf_rn(d.z, n.z, __fmaf_rn(d.y, n.y, __fmul_rn(d.x, n.x))));
-  r = make_float3(__fmaf_rn(-n.x, dn, d.x), __fmaf_rn(-n.y, dn, d.y), __fmaf_rn(-n.z, dn, d.z));
-  const float inv = rsqrtf(__fmaf_rn(r.z, r.z, __fmaf_rn(r.y, r.y, __fmul_rn(r.x, r.x))));
-  r = make_float3(__fmul_rn(r.x, inv), __fmul_rn(r.y, inv), __fmul_rn(r.z, inv));
-}
-
-// Escape distance of a ray that hit nothing: the furthest projection of the
-// receiver bounds on the ray.
-__device__ inline float escape_t(float3 o, float3 d, float3 rlo, float3 rhi) {
-  return fmaxf(d.x * (rlo.x - o.x), d.x * (rhi.x - o.x)) +
-         fmaxf(d.y * (rlo.y - o.y), d.y * (rhi.y - o.y)) +
-         fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
-}
-
-// true when the first b reflections of a chain were all on static faces
-__device__ inline bool static_chain(const uint32_t *fc, uint32_t b, uint32_t fs) {
-  bool ok = true;
-#pragma unroll
-  for (uint32_t k = 0; k < EMRT_MAX_DEPTH; k++)
-    if (k < b && fc[k] >= fs) ok = false;
-  return ok;
-}
-
-// Closest-hit traversal of one bounce for every ray (persistent threads: each
-// warp takes FETCH rays at a time from a global cursor).  BATCH: rays of many
-// scenes, each ray's scene read from the table; otherwise the single scene in
-// L.g.  Per ray: nearest hit over the static triangles and the vehicle
-// boxes, reception-sphere detections on the traced segment (appended as
-// candidates), and the specular continuation (appended to the next buffer).
-// TABLE: static-hit cache form (single scene): the static hit of a segment
-// whose chain is still static comes from L.stab when its entry is current,
-// and is stored there otherwise.
-template <bool BATCH, int BLOCK, int FETCH, bool WIDE, bool TABLE = false>
-__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
-                                                  uint32_t n_scenes) {
-  int stk[kStack];
-  float stt[kStack];
-  TravStats st;
-  uint32_t segs = 0, reused = 0;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t n_items = (L.b == 0 && !TABLE) ? L.n_primary : *L.n_in;
-  float3 rlo, rhi;
-  if (!BATCH) rx_bounds(L.g.rxb, rlo, rhi);
-  const uint32_t NO = EMRT_NO_FACE;
-  for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(L.work, (uint32_t)FETCH);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n_items) break;
-    for (uint32_t sub = 0; sub < (uint32_t)FETCH; sub += 32) {
-      uint32_t i = base + sub + lane;
-      if (i >= n_items) break;
-      segs++;
-      float3 o, d;
-      float Lacc;
-      uint32_t tx, j, sc = 0;
-      uint32_t fc[EMRT_MAX_DEPTH] = {NO, NO, NO, NO};
-      if (L.b == 0 && !TABLE) {
-        uint32_t local = i, count = L.count;
-        const float4 *dirs = L.dirs;
-        if (BATCH) {  // scene of a primary item: last scene whose range starts <= i
-          uint32_t lo = 0, hi = n_scenes;
-          while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (tab[mid].prim_begin <= i) lo = mid;
-            else hi = mid;
-          }
-          sc = lo;
-          local = i - tab[sc].prim_begin;
-          count = tab[sc].count;
-          dirs = tab[sc].dirs;
-        }
-        tx = local / count;
-        uint32_t k = local - tx * count;
-        float4 dj = dirs[k];
-        d = f3(dj);
-        j = __float_as_uint(dj.w);
-        o = f3((BATCH ? tab[sc].g : L.g).tx_pos[tx]);
-        Lacc = 0.f;
-      } else {
-        Ray R = L.rin[L.order ? L.order[i] : i];
-        o = f3(R.o_L);
-        Lacc = R.o_L.w;
-        d = f3(R.d_id);
-        uint32_t id = __float_as_uint(R.d_id.w);
-        if (BATCH) {
-          sc = id >> 26;
-          tx = (id >> 22) & 15u;
-          j = id & 0x3fffffu;
-        } else {
-          tx = id >> L.jbits;
-          j = id & ((1u << L.jbits) - 1u);  // TABLE: direction-table position
-        }
-        fc[0] = R.faces.x; fc[1] = R.faces.y; fc[2] = R.faces.z; fc[3] = R.faces.w;
-      }
-      const GeomView &g = BATCH ? tab[sc].g : L.g;
-      const float kappa = BATCH ? tab[sc].kappa : L.kappa;
-      const int K = BATCH ? (int)tab[sc].K : L.K;
-      if (BATCH) rx_bounds(g.rxb, rlo, rhi);
-      uint32_t prev = L.b > 0 ? fc[L.b - 1] : NO;
-      RayQ q;
-      ray_setup(q, o, d);
-      float tbest = FLT_MAX;
-      uint32_t face = NO;
-      bool have = false;
-      uint32_t slot = 0, ep = 0;
-      const bool keep = TABLE && static_chain(fc, (uint32_t)L.b, g.n_static_faces);
-      if (keep) {
-        slot = (uint32_t)L.b * L.n_slots + tx * L.count + j;
-        ep = L.tx_epoch[tx];
-        const uint4 e = L.stab[slot];
-        if (e.z == ep) {
-          tbest = __uint_as_float(e.x);
-          face = e.y;
-          have = true;
-          reused++;
-        }
-      }
-      if (!have) {
-        trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
-        if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
-      }
-      uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
-      trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
-      bool hit = face != NO;
-      float t_end = hit ? tbest : escape_t(o, d, rlo, rhi);
-      t_end = fmaxf(t_end, 0.f);
-      float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
-      const uint32_t b = (uint32_t)L.b;
-      const uint32_t w0 = BATCH ? (sc << 8 | tx) : tx;
-      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, [&](uint32_t rx) {
-        uint32_t slot = warp_append(L.n_cand);
-        if (slot < L.cand_cap) {
-          const uint32_t jj = TABLE ? __float_as_uint(L.dirs[j].w) : j;
-          uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
-          c[0] = make_uint4(w0, rx, b, fc[0]);
-          c[1] = make_uint4(fc[1], fc[2], fc[3], jj);
-        }
-      });
-      if (hit && L.b < K) {
-        float3 p, r;
-        reflect_step(g, face, o, d, tbest, p, r);
-        fc[L.b] = face;
-        uint32_t slot = warp_append(L.n_out);
-        Ray R;
-        R.o_L = make_float4(p.x, p.y, p.z, Lacc + tbest);
-        uint32_t id = BATCH ? (sc << 26 | tx << 22 | j) : (tx << L.jbits | j);
-        R.d_id = make_float4(r.x, r.y, r.z, __uint_as_float(id));
-        R.faces = make_uint4(fc[0], fc[1], fc[2], fc[3]);
-        L.rout[slot] = R;
-      }
-    }
-  }
-  __syncwarp();
-  add_u64(&L.ctr->segments[L.b], segs);
-  add_u64(&L.ctr->node_visits, st.nodes);
-  add_u64(&L.ctr->tri_tests, st.tris);
-  add_u64(&L.ctr->dyn_node_visits, st.dnodes);
-  add_u64(&L.ctr->box_tests, st.boxes);
-  add_u64(&L.ctr->rx_node_visits, st.rnodes);
-  add_u64(&L.ctr->rx_tests, st.rxs);
-  if (TABLE) add_u64(&L.ctr->static_reused, reused);
-  if (st.overflow) atomicOr(&L.ctr->err, ERR_STACK);
-}
-
-// Chain walker of the static-hit cache: one thread follows the whole specular
-// chain of a primary ray (tx, direction-table position k) as long as its
-// segments have current cache entries and its reflections stay on static
-// faces: static hit from the cache, vehicle boxes and reception spheres of
-// this frame, reflection.  The first segment it cannot finish that way (no
-// current entry, or the chain reflected off a vehicle) goes to D.rays[b] for
-// the per-bounce traversal, which continues the chain.  Segments, candidates
-// and continuations are exactly those of k_bounce.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, ChainBufs D) {
-  int stk[kStack];
-  float stt[kStack];
-  TravStats st;
-  uint32_t segs[EMRT_MAX_DEPTH + 1] = {0, 0, 0, 0, 0};
-  uint32_t reused = 0, deferred = 0;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t n_items = L.n_primary;
-  const uint32_t fs = L.g.n_static_faces;
-  const uint32_t NO = EMRT_NO_FACE;
-  float3 rlo, rhi;
-  rx_bounds(L.g.rxb, rlo, rhi);
-  for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(L.work, 32u);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n_items) break;
-    const uint32_t i = base + lane;
-    if (i >= n_items) continue;
-    const uint32_t tx = i / L.count;
-    const uint32_t k = i - tx * L.count;
-    const float4 dj = L.dirs[k];
-    const uint32_t j = __float_as_uint(dj.w);
-    const uint32_t ep = L.tx_epoch[tx];
-    const uint32_t id = tx << L.jbits | k;
-    float3 o = f3(L.g.tx_pos[tx]), d = f3(dj);
-    float Lacc = 0.f;
-    uint32_t f0 = NO, f1 = NO, f2 = NO, f3_ = NO;
-    int defer_b = -1;
-    for (int b = 0; b <= L.K; b++) {
-      const uint4 e = L.stab[(uint32_t)b * L.n_slots + i];
-      if (e.z != ep) {
-        defer_b = b;
-        break;
-      }
-      float tbest = __uint_as_float(e.x);
-      uint32_t face = e.y;
-      reused++;
-      segs[b]++;
-      RayQ q;
-      ray_setup(q, o, d);
-      // the face just left is static, so no vehicle is excluded
-      trace_boxes<false>(L.g.dyn, q, 0.f, tbest, face, fs, NO, NO, stk, stt, st);
-      const bool hit = face != NO;
-      float t_end = hit ? tbest : escape_t(o, d, rlo, rhi);
-      t_end = fmaxf(t_end, 0.f);
-      const float rmax = L.kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
-      const uint32_t bb = (uint32_t)b;
-      query_rx(L.g.rxb, q, t_end, Lacc, L.kappa, rmax, stk, stt, st, [&](uint32_t rx) {
-        uint32_t slot = warp_append(L.n_cand);
-        if (slot < L.cand_cap) {
-          uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
-          c[0] = make_uint4(tx, rx, bb, f0);
-          c[1] = make_uint4(f1, f2, f3_, j);
-        }
-      });
-      if (!hit || b == L.K) break;
-      float3 p, r;
-      reflect_step(L.g, face, o, d, tbest, p, r);
-      f0 = b == 0 ? face : f0;
-      f1 = b == 1 ? face : f1;
-      f2 = b == 2 ? face : f2;
-      f3_ = b == 3 ? face : f3_;
-      Lacc = Lacc + tbest;
-      o = p;
-      d = r;
-      if (face >= fs) {  // off a vehicle: the rest of the chain is not cached
-        defer_b = b + 1;
-        break;
-      }
-    }
-    if (defer_b >= 0) {
-      uint32_t slot = warp_append_keyed(L.ctr->n_ray, (uint32_t)defer_b);
-      Ray R;
-      R.o_L = make_float4(o.x, o.y, o.z, Lacc);
-      R.d_id = make_float4(d.x, d.y, d.z, __uint_as_float(id));
-      R.faces = make_uint4(f0, f1, f2, f3_);
-      D.rays[defer_b][slot] = R;
-      deferred++;
-    }
-  }
-  __syncwarp();
-  for (int b = 0; b <= EMRT_MAX_DEPTH; b++) add_u64(&L.ctr->segments[b], segs[b]);
-  add_u64(&L.ctr->dyn_node_visits, st.dnodes);
-  add_u64(&L.ctr->box_tests, st.boxes);
-  add_u64(&L.ctr->rx_node_visits, st.rnodes);
-  add_u64(&L.ctr->rx_tests, st.rxs);
-  add_u64(&L.ctr->static_reused, reused);
-  add_u64(&L.ctr->deferred, deferred);
-  if (st.overflow) atomicOr(&L.ctr->err, ERR_STACK);
-}
-
-__global__ void k_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n) {
-  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const float4 a = pos[t], r = ref[t];
-  if (__float_as_uint(a.x) != __float_as_uint(r.x) || __float_as_uint(a.y) != __float_as_uint(r.y) ||
-      __float_as_uint(a.z) != __float_as_uint(r.z)) {
-    epoch[t] += 1u;
-    ref[t] = a;
-  }
-}
+#include "bounce.cuh"
 
 // ----------------------------------------------------------------------------
 // canonical key: tx | rx | depth | f0 | .. | f_{K-1}, most significant first
@@ -495,16 +185,19 @@ __device__ inline double inface_margin(const GeomView &g, uint32_t f, D3 P, D3 n
 
 constexpr double kMargin = 1e-4;
 
+// Acceptance runs in two phases so that the occlusion legs, long any-hit
+// traversals, get a thread each.  Phase 1, per record: images across the
+// face planes, reflection points backward from the receiver (FP64), the
+// parameter and in-face tests with their margin; writes the depth and the
+// geometric verdict to w2 and the k + 2 points, rounded to float32, to
+// pts[p * cap + i].  Phase 2, per (leg q, record i), leg-major: any-hit test
+// of the segment Q[q] -> Q[q+1] over static triangles and vehicle boxes with
+// the endpoint faces excluded; an occluded leg clears EMRT_PATH_VALID.
 template <bool BATCH>
-__global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView G, const BatchScene *__restrict__ tab,
-                                                         uint32_t *rec, const uint32_t *n,
-                                                         Counters *ctr) {
-  int stk[kStack];
-  float stt[kStack];
-  TravStats st;
-  uint32_t cnt = *n;
-  unsigned long long occl = 0;
-  const uint32_t NO = EMRT_NO_FACE;
+__global__ void __launch_bounds__(kBounceBlock) k_accept_geom(GeomView G, const BatchScene *__restrict__ tab,
+                                                              uint32_t *rec, const uint32_t *n,
+                                                              float4 *pts, uint32_t cap) {
+  const uint32_t cnt = min(*n, cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
     uint4 *r = reinterpret_cast<uint4 *>(rec + 8ull * i);
     uint4 a = r[0], b = r[1];
@@ -516,8 +209,8 @@ __global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView G, const Batch
     uint32_t nf = g.n_static_faces + 6u * g.n_veh;
     for (uint32_t q = 0; ok && q < k; q++) ok = f[q] < nf && (q == 0 || f[q] != f[q - 1]);
     bool marg = false;
-    D3 Q[EMRT_MAX_DEPTH + 2];
     if (ok) {
+      D3 Q[EMRT_MAX_DEPTH + 2];
       D3 I[EMRT_MAX_DEPTH + 1];
       D3 nn[EMRT_MAX_DEPTH];
       double dd[EMRT_MAX_DEPTH];
@@ -539,29 +232,52 @@ __global__ void __launch_bounds__(kBounceBlock) k_accept(GeomView G, const Batch
         if (m < 0.0) ok = false;
         if (fabs(m) < kMargin) marg = true;
       }
-      // occlusion of the k+1 legs, endpoint faces excluded
-      for (uint32_t q = 0; ok && q <= k; q++) {
-        float3 A = make_float3((float)Q[q].x, (float)Q[q].y, (float)Q[q].z);
-        float3 B = make_float3((float)Q[q + 1].x, (float)Q[q + 1].y, (float)Q[q + 1].z);
-        uint32_t e0 = q >= 1 ? f[q - 1] : NO, e1 = q < k ? f[q] : NO;
-        uint32_t v0 = (e0 != NO && e0 >= g.n_static_faces) ? (e0 - g.n_static_faces) / 6u : NO;
-        uint32_t v1 = (e1 != NO && e1 >= g.n_static_faces) ? (e1 - g.n_static_faces) / 6u : NO;
-        RayQ rq;
-        ray_setup(rq, A, B - A);
-        float tmax = 1.f;
-        uint32_t hf = NO;
-        occl++;
-        TravStats s2;
-        if (trace_tris<true>(g.stat, rq, 0.f, tmax, hf, e0, e1, stk, stt, s2)) ok = false;
-        tmax = 1.f;
-        if (ok && trace_boxes<true>(g.dyn, rq, 0.f, tmax, hf, g.n_static_faces, v0, v1, stk, stt, s2))
-          ok = false;
-        st.overflow |= s2.overflow;
-      }
+      if (ok)
+        for (uint32_t q = 0; q <= k + 1; q++)
+          pts[(uint64_t)q * cap + i] = make_float4((float)Q[q].x, (float)Q[q].y, (float)Q[q].z, 0.f);
     }
-    uint32_t flags = (ok ? EMRT_PATH_VALID : 0u) | (marg ? EMRT_PATH_MARGINAL : 0u);
+    const uint32_t flags = (ok ? EMRT_PATH_VALID : 0u) | (marg ? EMRT_PATH_MARGINAL : 0u);
     a.z = (a.z & 15u) | flags;
     r[0] = a;
+  }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kBounceBlock) k_accept_occl(GeomView G, const BatchScene *__restrict__ tab,
+                                                              uint32_t *rec, const uint32_t *n,
+                                                              const float4 *pts, uint32_t cap,
+                                                              Counters *ctr) {
+  int stk[kStack];
+  float stt[kStack];
+  TravStats st;
+  const uint32_t cnt = min(*n, cap);
+  const uint32_t NO = EMRT_NO_FACE;
+  unsigned long long occl = 0;
+  const uint64_t items = (uint64_t)(EMRT_MAX_DEPTH + 1) * cnt;
+  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
+       it += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t q = (uint32_t)(it / cnt), i = (uint32_t)(it - (uint64_t)q * cnt);
+    const uint4 *r = reinterpret_cast<const uint4 *>(rec + 8ull * i);
+    const uint4 a = r[0];
+    const uint32_t k = a.z & 15u;
+    if (q > k || !(a.z & EMRT_PATH_VALID)) continue;
+    const uint4 b = r[1];
+    const uint32_t f[EMRT_MAX_DEPTH] = {a.w, b.x, b.y, b.z};
+    const uint32_t sc = BATCH ? (a.x >> 8) : 0u;
+    const GeomView &g = BATCH ? tab[sc].g : G;
+    const float3 A = f3(pts[(uint64_t)q * cap + i]), B = f3(pts[(uint64_t)(q + 1) * cap + i]);
+    const uint32_t e0 = q >= 1 ? f[q - 1] : NO, e1 = q < k ? f[q] : NO;
+    const uint32_t v0 = (e0 != NO && e0 >= g.n_static_faces) ? (e0 - g.n_static_faces) / 6u : NO;
+    const uint32_t v1 = (e1 != NO && e1 >= g.n_static_faces) ? (e1 - g.n_static_faces) / 6u : NO;
+    RayQ rq;
+    ray_setup(rq, A, B - A);
+    float tmax = 1.f;
+    uint32_t hf = NO;
+    occl++;
+    bool hit = trace_tris<true>(g.stat, rq, 0.f, tmax, hf, e0, e1, stk, stt, st);
+    tmax = 1.f;
+    if (!hit) hit = trace_boxes<true>(g.dyn, rq, 0.f, tmax, hf, g.n_static_faces, v0, v1, stk, stt, st);
+    if (hit) atomicAnd(&rec[8ull * i + 2], ~EMRT_PATH_VALID);
   }
   add_u64(&ctr->occl_rays, occl);
   if (st.overflow) atomicOr(&ctr->err, ERR_STACK);
@@ -805,9 +521,10 @@ void launch_bounce_batched(int variant, const BounceLaunch &L, const BatchScene 
 }
 
 void launch_accept_batched(const BatchScene *tab, uint32_t *rec, const uint32_t *n, Counters *ctr,
-                           cudaStream_t s) {
+                           float4 *pts, uint32_t cap, cudaStream_t s) {
   GeomView none{};
-  emrt::note_launch(), k_accept<true><<<kPrimGrid * 4, kBounceBlock, 0, s>>>(none, tab, rec, n, ctr);
+  emrt::note_launch(), k_accept_geom<true><<<kPrimGrid * 4, kBounceBlock, 0, s>>>(none, tab, rec, n, pts, cap);
+  emrt::note_launch(), k_accept_occl<true><<<kPrimGrid * 8, kBounceBlock, 0, s>>>(none, tab, rec, n, pts, cap, ctr);
 }
 
 void launch_batch_scatter(const BatchScene *tab, uint32_t n_scenes, const uint32_t *rec,
@@ -857,8 +574,9 @@ void launch_unique(const uint32_t *rec, const KeyW<4> *keys, const uint32_t *val
   emrt::note_launch(), k_unique<<<kPrimGrid * 4, 256, 0, s>>>(rec, keys, vals, head, pos, n, uniq);
 }
 void launch_accept(const GeomView &g, uint32_t *rec, const uint32_t *n, Counters *ctr,
-                   cudaStream_t s) {
-  emrt::note_launch(), k_accept<false><<<kPrimGrid * 4, kBounceBlock, 0, s>>>(g, nullptr, rec, n, ctr);
+                   float4 *pts, uint32_t cap, cudaStream_t s) {
+  emrt::note_launch(), k_accept_geom<false><<<kPrimGrid * 4, kBounceBlock, 0, s>>>(g, nullptr, rec, n, pts, cap);
+  emrt::note_launch(), k_accept_occl<false><<<kPrimGrid * 8, kBounceBlock, 0, s>>>(g, nullptr, rec, n, pts, cap, ctr);
 }
 void launch_keep_flags(const uint32_t *rec, const uint32_t *n, int keep_all, uint32_t *flag,
                        cudaStream_t s) {

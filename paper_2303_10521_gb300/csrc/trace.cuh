@@ -86,8 +86,10 @@ const char *bounce_variant_name(int v);
 int bounce_variant_grid(int v);
 void launch_bounce_batched(int variant, const BounceLaunch &L, const BatchScene *tab,
                            uint32_t n_scenes, cudaStream_t s);
+// pts: scratch of (EMRT_MAX_DEPTH + 2) * cap float4 (reflection points);
+// records [0, min(*n, cap))
 void launch_accept_batched(const BatchScene *tab, uint32_t *rec, const uint32_t *n, Counters *ctr,
-                           cudaStream_t s);
+                           float4 *pts, uint32_t cap, cudaStream_t s);
 // writes kept, sorted batched records to each scene's output (positions
 // relative to the scene's first kept record); first[] and cnt[] are
 // kBatchMaxScenes words of scratch
@@ -110,9 +112,10 @@ void launch_heads(const KeyW<4> *keys, const uint32_t *n, uint32_t *head, cudaSt
 void launch_unique(const uint32_t *rec, const KeyW<4> *keys, const uint32_t *vals,
                    const uint32_t *head, const uint32_t *pos, const uint32_t *n, uint32_t *uniq,
                    cudaStream_t s);
-// Image-method acceptance and occlusion of n records in place (w2 flags).
+// Image-method acceptance and occlusion of min(*n, cap) records in place
+// (w2 flags); pts: scratch of (EMRT_MAX_DEPTH + 2) * cap float4.
 void launch_accept(const GeomView &g, uint32_t *rec, const uint32_t *n, Counters *ctr,
-                   cudaStream_t s);
+                   float4 *pts, uint32_t cap, cudaStream_t s);
 // flag[i] = 1 if record i is kept (valid, or every record when keep_all).
 void launch_keep_flags(const uint32_t *rec, const uint32_t *n, int keep_all, uint32_t *flag,
                        cudaStream_t s);
