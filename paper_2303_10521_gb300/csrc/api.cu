@@ -450,7 +450,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     if (b > 0 && sort_rays && !cache) {
       launch_ray_keys(L.rin, &c->n_ray[b], s->bbox, s->rkeys[0], s->rvals[0], st);
       bool alt = radix_sort<1>(&c->n_ray[b], s->rkeys[0], s->rvals[0], s->rkeys[1], s->rvals[1],
-                               32, s->hist, st, nrays);
+                               24, s->hist, st, nrays);
       L.order = s->rvals[alt ? 1 : 0];
     }
     L.n_in = &c->n_ray[b];

@@ -422,7 +422,7 @@ __global__ void k_ray_keys(const Ray *r, const uint32_t *n, const float4 *bb, Ke
     uint32_t m = spread7(c[0]) << 2 | spread7(c[1]) << 1 | spread7(c[2]);
     uint32_t oc = oct_code(make_float3(d.x, d.y, d.z));
     keys[i].w[0] = batched ? ((__float_as_uint(d.w) >> 26) << 26 | (m >> 1) << 6 | oc >> 26)
-                           : (m << 11 | oc >> 21);
+                           : ((m >> 6) << 9 | oc >> 23);
     vals[i] = i;
   }
 }

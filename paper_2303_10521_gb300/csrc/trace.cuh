@@ -97,8 +97,9 @@ void launch_batch_scatter(const BatchScene *tab, uint32_t n_scenes, const uint32
                           const uint32_t *n, const uint32_t *flag, const uint32_t *pos,
                           uint32_t *first, uint32_t *cnt, Counters *ctr, cudaStream_t s);
 
-// Coherence keys of the *n rays: origin cell (7-bit Morton per axis in the
-// scene box) then direction bin (11 bits of the octahedral code).
+// Coherence keys of the *n rays (24 bits, three radix passes): origin cell
+// (5-bit Morton per axis in the scene box) then direction bin (9 bits of the
+// octahedral code).
 // batched: scene (6 bits) | origin cell (20 bits) | direction bin (6 bits)
 void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1> *keys,
                      uint32_t *vals, cudaStream_t s, bool batched = false);
