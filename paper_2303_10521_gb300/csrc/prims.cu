@@ -99,53 +99,116 @@ __global__ void __launch_bounds__(1024) k_scan_single(uint32_t *v, uint32_t n, u
   if (threadIdx.x == 1023 && total) *total = part[1023];
 }
 
-template <int W>
+// Stable scatter of one radix pass.  The block's key range (block_range) is
+// processed in tiles of kPrimBlock * IPT keys held in registers; warp w owns
+// tile elements [w * 32 * IPT, (w + 1) * 32 * IPT), its lane l the elements
+// w * 32 * IPT + r * 32 + l (coalesced loads).  Ranks among equal digits
+// follow element order: within a warp, round by round from
+// __match_any_sync and the warp's own digit counters (warp-synchronous);
+// across warps, from a prefix of the warps' counts per digit.  The tile is
+// then rearranged by digit in shared memory and written out so that each
+// digit's run lands on consecutive addresses (coalesced sectors instead of
+// one sector per key).
+template <int W, int IPT>
 __global__ void __launch_bounds__(kPrimBlock) k_scatter(const uint32_t *d_n, const KeyW<W> *kin,
                                                         const uint32_t *vin, KeyW<W> *kout,
                                                         uint32_t *vout, int pass,
                                                         const uint32_t *offs) {
-  constexpr int NW = kPrimBlock / 32;
-  __shared__ uint32_t s_base[256];
-  __shared__ uint32_t s_tot[256];
-  __shared__ uint32_t s_cnt[NW][256];
+  constexpr int NW = kPrimBlock / 32, TILE = kPrimBlock * IPT;
+  __shared__ uint32_t s_base[256];   // next global position per digit
+  __shared__ uint32_t s_run[256];    // keys of the digit in the tile
+  __shared__ uint32_t s_start[256];  // first tile position of the digit
+  __shared__ uint32_t s_cnt[NW][256];  // per warp: count, then exclusive prefix
+  __shared__ KeyW<W> s_key[TILE];
+  __shared__ uint32_t s_val[TILE];
+  __shared__ uint16_t s_dig[TILE];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   s_base[t] = offs[blockIdx.x * 256 + t];
+  const uint32_t n = *d_n;
   uint32_t lo, hi;
-  block_range(*d_n, lo, hi);
-  for (uint32_t r0 = lo; r0 < hi; r0 += kPrimBlock) {
+  block_range(n, lo, hi);
+  for (uint32_t r0 = lo; r0 < hi; r0 += TILE) {
     for (int w = 0; w < NW; w++) s_cnt[w][t] = 0;
-    __syncthreads();
-    uint32_t i = r0 + t;
-    bool valid = i < hi;
-    KeyW<W> k;
-    uint32_t v = 0, dg = 256;
-    if (valid) {
-      k = kin[i];
-      v = vin[i];
-      dg = digit_of<W>(k, pass);
+    KeyW<W> k[IPT];
+    uint32_t v[IPT], dg[IPT], rank[IPT];
+    const uint32_t wbase = r0 + (uint32_t)warp * 32u * IPT + lane;
+#pragma unroll
+    for (int r = 0; r < IPT; r++) {
+      const uint32_t i = wbase + 32u * r;
+      dg[r] = 256;
+      v[r] = 0;
+      if (i < hi) {
+        k[r] = kin[i];
+        v[r] = vin[i];
+        dg[r] = digit_of<W>(k[r], pass);
+      }
     }
-    uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && rank == 0) s_cnt[warp][dg] = __popc(peers);
     __syncthreads();
-    {
+    // ranks within the warp, in element order
+#pragma unroll
+    for (int r = 0; r < IPT; r++) {
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg[r]);
+      const uint32_t c = dg[r] < 256 ? s_cnt[warp][dg[r]] : 0u;
+      rank[r] = c + __popc(peers & lt);
+      __syncwarp();
+      if (dg[r] < 256 && (peers & lt) == 0) s_cnt[warp][dg[r]] = c + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {  // per digit t: exclusive prefix over the warps, tile total
       uint32_t run = 0;
       for (int w = 0; w < NW; w++) {
-        uint32_t c = s_cnt[w][t];
+        const uint32_t c = s_cnt[w][t];
         s_cnt[w][t] = run;
         run += c;
       }
-      s_tot[t] = run;
+      s_run[t] = run;
     }
     __syncthreads();
-    if (valid) {
-      uint32_t pos = s_base[dg] + s_cnt[warp][dg] + rank;
-      kout[pos] = k;
-      vout[pos] = v;
+    // digit starts within the tile: exclusive scan of s_run (one warp)
+    if (warp == 0) {
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        c[q] = s_run[lane * 8 + q];
+        sum += c[q];
+      }
+      uint32_t incl = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint32_t run = incl - sum;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        s_start[lane * 8 + q] = run;
+        run += c[q];
+      }
     }
     __syncthreads();
-    s_base[t] += s_tot[t];
+#pragma unroll
+    for (int r = 0; r < IPT; r++) {
+      const uint32_t p =
+          dg[r] < 256 ? s_start[dg[r]] + s_cnt[warp][dg[r]] + rank[r] : (uint32_t)TILE;
+      if (p < (uint32_t)TILE) {
+        s_key[p] = k[r];
+        s_val[p] = v[r];
+        s_dig[p] = (uint16_t)dg[r];
+      }
+    }
     __syncthreads();
+    const uint32_t n_tile = min((uint32_t)TILE, hi - r0);
+    for (uint32_t p = t; p < n_tile; p += kPrimBlock) {
+      const uint32_t d = s_dig[p] & 255u;
+      const uint32_t pos = s_base[d] + (p - s_start[d]);
+      if (pos < n) {
+        kout[pos] = s_key[p];
+        vout[pos] = s_val[p];
+      }
+    }
+    __syncthreads();
+    s_base[t] += s_run[t];
   }
 }
 
@@ -212,7 +275,7 @@ bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *key
     uint32_t *vi = alt ? vals2 : vals, *vo = alt ? vals : vals2;
     emrt::note_launch(), k_hist<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
     emrt::note_launch(), k_digit_offsets<<<1, 1024, 0, s>>>(d_n, hist, G);
-    emrt::note_launch(), k_scatter<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
+    emrt::note_launch(), k_scatter<W, (W == 4 ? 4 : 8)><<<G, kPrimBlock, 0, s>>>(d_n, ki, vi, ko, vo, p, hist);
     alt = !alt;
   }
   return alt;
