@@ -440,18 +440,23 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     cudaEventRecord(s->evb[1], st);
     nev = 1;
   }
+  int key_buf = 0;  // sort buffer that receives the next bounce's keys
   for (uint32_t b = 0; b <= p->max_depth; b++) {
     BounceLaunch L{};
     L.g = gt;
     L.rin = cache ? s->defer[b] : (b ? s->rays[(b - 1) & 1] : nullptr);
     L.order = nullptr;
-    // reorder reflected rays for coherent traversal; the few segments the
-    // cache walker defers are not worth the sort's fixed cost (measured)
-    if (b > 0 && sort_rays && !cache) {
-      launch_ray_keys(L.rin, &c->n_ray[b], s->bbox, s->rkeys[0], s->rvals[0], st);
-      bool alt = radix_sort<1>(&c->n_ray[b], s->rkeys[0], s->rvals[0], s->rkeys[1], s->rvals[1],
+    // reorder reflected rays for coherent traversal (keys written by the
+    // previous bounce into key_buf); the few segments the cache walker
+    // defers are not worth the sort's fixed cost (measured)
+    const bool sort_here = b > 0 && sort_rays && !cache;
+    if (sort_here) {
+      const int o = key_buf, q = 1 - key_buf;
+      bool alt = radix_sort<1>(&c->n_ray[b], s->rkeys[o], s->rvals[o], s->rkeys[q], s->rvals[q],
                                24, s->hist, st, nrays);
-      L.order = s->rvals[alt ? 1 : 0];
+      const int res = alt ? q : o;
+      L.order = s->rvals[res];
+      key_buf = 1 - res;  // the next keys go to the buffer not read as order
     }
     L.n_in = &c->n_ray[b];
     L.n_primary = (uint32_t)nrays;
@@ -468,6 +473,11 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.b = (int)b;
     L.K = (int)p->max_depth;
     L.jbits = jbits;
+    if (sort_rays && !cache && b < p->max_depth) {
+      L.okeys = s->rkeys[key_buf];
+      L.ovals = s->rvals[key_buf];
+      L.bbox = s->bbox;
+    }
     if (cache) {
       L.stab = tab->stab;
       L.tx_epoch = tab->tx_epoch;

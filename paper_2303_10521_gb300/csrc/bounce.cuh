@@ -188,6 +188,10 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
         R.d_id = make_float4(r.x, r.y, r.z, __uint_as_float(id));
         R.faces = make_uint4(fc[0], fc[1], fc[2], fc[3]);
         L.rout[slot] = R;
+        if (!BATCH && L.okeys) {
+          L.okeys[slot].w[0] = ray_key(p, r, L.bbox[0], L.bbox[1]);
+          L.ovals[slot] = slot;
+        }
       }
     }
   }

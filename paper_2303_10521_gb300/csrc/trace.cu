@@ -67,6 +67,33 @@ __global__ void k_dir_table(uint64_t n, uint64_t off, uint64_t stride, uint32_t 
 }
 
 // ----------------------------------------------------------------------------
+__device__ inline uint32_t spread7(uint32_t v) {  // 7 bits -> every third bit
+  uint32_t x = v & 0x7fu;
+  x = (x | (x << 8)) & 0x0000f00fu;
+  x = (x | (x << 4)) & 0x000c30c3u;
+  x = (x | (x << 2)) & 0x00249249u;
+  return x;
+}
+
+// Coherence cell of a ray: 7-bit-per-axis Morton code of its origin in the
+// scene box and its 32-bit octahedral direction code.
+__device__ inline void ray_cell(float3 o, float3 d, float4 lo, float4 hi, uint32_t &m,
+                                uint32_t &oc) {
+  uint32_t c[3];
+  float q[3] = {(o.x - lo.x) / (hi.x - lo.x), (o.y - lo.y) / (hi.y - lo.y), (o.z - lo.z) / (hi.z - lo.z)};
+  for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 127.f);
+  m = spread7(c[0]) << 2 | spread7(c[1]) << 1 | spread7(c[2]);
+  oc = oct_code(d);
+}
+// single-scene coherence key (24 bits): 5-bit-per-axis origin cell, 9-bit
+// direction bin
+__device__ inline uint32_t ray_key(float3 o, float3 d, float4 lo, float4 hi) {
+  uint32_t m, oc;
+  ray_cell(o, d, lo, hi, m, oc);
+  return (m >> 6) << 9 | oc >> 23;
+}
+
+// ----------------------------------------------------------------------------
 #include "bounce.cuh"
 
 // ----------------------------------------------------------------------------
@@ -402,25 +429,14 @@ __global__ void k_batch_init(uint32_t *first, uint32_t *cnt) {
   }
 }
 
-__device__ inline uint32_t spread7(uint32_t v) {  // 7 bits -> every third bit
-  uint32_t x = v & 0x7fu;
-  x = (x | (x << 8)) & 0x0000f00fu;
-  x = (x | (x << 4)) & 0x000c30c3u;
-  x = (x | (x << 2)) & 0x00249249u;
-  return x;
-}
-
 __global__ void k_ray_keys(const Ray *r, const uint32_t *n, const float4 *bb, KeyW<1> *keys,
                            uint32_t *vals, bool batched) {
   uint32_t cnt = *n;
   float4 lo = bb[0], hi = bb[1];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
     float4 o = r[i].o_L, d = r[i].d_id;
-    uint32_t c[3];
-    float q[3] = {(o.x - lo.x) / (hi.x - lo.x), (o.y - lo.y) / (hi.y - lo.y), (o.z - lo.z) / (hi.z - lo.z)};
-    for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 127.f);
-    uint32_t m = spread7(c[0]) << 2 | spread7(c[1]) << 1 | spread7(c[2]);
-    uint32_t oc = oct_code(make_float3(d.x, d.y, d.z));
+    uint32_t m, oc;
+    ray_cell(f3(o), f3(d), lo, hi, m, oc);
     keys[i].w[0] = batched ? ((__float_as_uint(d.w) >> 26) << 26 | (m >> 1) << 6 | oc >> 26)
                            : ((m >> 6) << 9 | oc >> 23);
     vals[i] = i;

@@ -44,6 +44,11 @@ struct BounceLaunch {
   uint4 *stab;
   const uint32_t *tx_epoch;
   uint32_t n_slots;
+  // optional (single scene): coherence key and index of every reflected ray
+  // written, at the ray's slot, for the next bounce's sort (box: scene bbox)
+  KeyW<1> *okeys;
+  uint32_t *ovals;
+  const float4 *bbox;
 };
 // Chain walker of the static-hit cache: rays[b] receives the segments that
 // the per-bounce traversal must trace at bounce b (count in ctr->n_ray[b]).
