@@ -164,13 +164,27 @@ __device__ inline Box prim_box(const float4 *prims, uint32_t g) {
   return b;
 }
 
-template <int KIND>
+// Bottom-up boxes: one thread per leaf walks to the root; the second child
+// to arrive at a node continues.  MULTI: leaves of 1-4 prims (leaf code
+// ~(first << 2 | count - 1)); prims other than a leaf's first have
+// leaf_parent 0xFFFFFFFF.
+template <int KIND, bool MULTI = false>
 __global__ void k_refit(const float4 *prims, uint32_t n, float4 *nodes, const uint32_t *leaf_parent,
                         uint32_t *flags) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n || n < 2) return;
+  if (MULTI && leaf_parent[g] == 0xffffffffu) return;
   Box b = prim_box<KIND>(prims, g);
   int code = (int)leaf_parent[g];
+  if (MULTI) {
+    const int lc = reinterpret_cast<const int *>(nodes + 4ll * (code >> 1) + 3)[code & 1];
+    const uint32_t cnt = ((uint32_t)(~lc) & 3u) + 1u;
+    for (uint32_t q = 1; q < cnt && g + q < n; q++) {
+      Box c = prim_box<KIND>(prims, g + q);
+      b.lo = make_float3(fminf(b.lo.x, c.lo.x), fminf(b.lo.y, c.lo.y), fminf(b.lo.z, c.lo.z));
+      b.hi = make_float3(fmaxf(b.hi.x, c.hi.x), fmaxf(b.hi.y, c.hi.y), fmaxf(b.hi.z, c.hi.z));
+    }
+  }
   for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
     int p = code >> 1, side = code & 1;
     float4 *np = nodes + 4ll * p;
@@ -342,6 +356,7 @@ BVHView BVHBuf::view() const {
   v.prims = prims;
   v.root = n >= 2 ? 0 : ~0;
   v.n_prims = n;
+  v.leaf_bits = leaf_bits;
   return v;
 }
 
@@ -428,6 +443,10 @@ namespace {
 constexpr int kSahBins = 32;
 constexpr int kSahBlock = 256;
 constexpr int kSahMaxDepth = 60;  // levels; the traversal stack holds 64 entries
+// ranges of up to this many triangles become leaves (1-4; on the city 1 is
+// fastest: 4-triangle leaves cut node visits 29.0 -> 25.7 per segment but
+// raised triangle tests 2.5 -> 6.7 and the traversal 16.0 -> 18.8 ms)
+constexpr uint32_t kSahLeafMax = 1;
 
 struct SahTask {
   uint32_t b, e, node, pad;
@@ -645,9 +664,11 @@ __global__ void __launch_bounds__(kSahBlock) k_sah_level(
     uint32_t rb[2] = {b, b + nl}, re[2] = {b + nl, e};
     int code[2];
     for (int side = 0; side < 2; side++) {
-      if (re[side] - rb[side] == 1) {
-        code[side] = ~(int)rb[side];
+      const uint32_t rn = re[side] - rb[side];
+      if (rn <= kSahLeafMax) {
+        code[side] = ~(int)(rb[side] << 2 | (rn - 1));
         leaf_parent[rb[side]] = 2 * T.node + side;
+        for (uint32_t q = 1; q < rn; q++) leaf_parent[rb[side] + q] = 0xffffffffu;
       } else {
         uint32_t ni = atomicAdd(n_alloc, 1u);
         code[side] = (int)ni;
@@ -706,9 +727,10 @@ cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *
     emrt::note_launch(), k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
     if (n >= 2) {
       cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
-      emrt::note_launch(), k_refit<PRIM_TRI><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+      emrt::note_launch(), k_refit<PRIM_TRI, true><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
     }
     e = cudaStreamSynchronize(s);
+    if (!e) b.leaf_bits = 2;
   }
   cudaFree(cen); cudaFree(lo); cudaFree(hi); cudaFree(tmp);
   cudaFree(tasks[0]); cudaFree(tasks[1]); cudaFree(ctr);

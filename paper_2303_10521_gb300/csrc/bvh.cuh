@@ -21,6 +21,7 @@ struct BVHBuf {
   uint32_t *d_n = nullptr;       // device copy of n
   float4 *nodes4 = nullptr;      // 4-wide collapse (static BVH), or null
   uint32_t n4 = 0;
+  uint32_t leaf_bits = 0;        // see BVHView (2: multi-triangle SAH leaves)
   BVHView view() const;
 };
 

@@ -56,6 +56,9 @@ struct BVHView {
                         // .w, hi); points: 1 float4 (xyz, receiver id bits)
   int root;             // 0 (inner), ~0 (single leaf)
   uint32_t n_prims;     // 0 = empty
+  uint32_t leaf_bits;   // leaf code ~c: c = first prim (0), or first << 2 |
+                        // (count - 1) for leaves of 1-4 prims (2); ~0 is
+                        // prim 0 alone either way
 };
 
 // ray state between bounces: 48 B

@@ -101,28 +101,35 @@ struct TravStats {
     return hit;                        \
   }
 
-// One triangle leaf: watertight test, exclusion of faces ex0/ex1, closest-hit
-// tie to the lower face ID.  Returns true when tmax/face changed.
+// One triangle leaf (1-4 triangles, see BVHView::leaf_bits): watertight
+// tests, exclusion of faces ex0/ex1, closest-hit tie to the lower face ID.
+// Returns true when tmax/face changed.
 template <bool ANY>
-__device__ inline bool leaf_tri(const BVHView &b, uint32_t g, const RayQ &r, float tmin,
+__device__ inline bool leaf_tri(const BVHView &b, uint32_t code, const RayQ &r, float tmin,
                                 float &tmax, uint32_t &face, uint32_t ex0, uint32_t ex1,
                                 TravStats &st) {
-  const float4 *tp = b.prims + 3ull * g;
-  float4 a = ldg4(tp), bb = ldg4(tp + 1), c = ldg4(tp + 2);
-  st.tris++;
-  uint32_t f = __float_as_uint(a.w);
-  float t;
-  // closest hit: widen the bound slightly so that an exact tie can go to
-  // the lower face ID; any hit: strictly inside (tmin, tmax)
-  if (f != ex0 && f != ex1 &&
-      tri_hit(r, f3(a), f3(bb), f3(c), tmin, ANY ? tmax : tmax * 1.0000001f, t)) {
-    if (t < tmax || (!ANY && t == tmax && f < face)) {
-      tmax = t;
-      face = f;
-      return true;
+  const uint32_t g0 = b.leaf_bits ? code >> 2 : code;
+  const uint32_t cnt = b.leaf_bits ? (code & 3u) + 1u : 1u;
+  bool changed = false;
+  for (uint32_t q = 0; q < cnt; q++) {
+    const float4 *tp = b.prims + 3ull * (g0 + q);
+    float4 a = ldg4(tp), bb = ldg4(tp + 1), c = ldg4(tp + 2);
+    st.tris++;
+    uint32_t f = __float_as_uint(a.w);
+    float t;
+    // closest hit: widen the bound slightly so that an exact tie can go to
+    // the lower face ID; any hit: strictly inside (tmin, tmax)
+    if (f != ex0 && f != ex1 &&
+        tri_hit(r, f3(a), f3(bb), f3(c), tmin, ANY ? tmax : tmax * 1.0000001f, t)) {
+      if (t < tmax || (!ANY && t == tmax && f < face)) {
+        tmax = t;
+        face = f;
+        changed = true;
+        if (ANY) return true;
+      }
     }
   }
-  return false;
+  return changed;
 }
 
 // 4-wide traversal: each node fetch (8 x 16 B) tests four child boxes; the
