@@ -63,6 +63,8 @@ def parse():
                     help="per-receiver schedule leg: trajectory segment length (m)")
     ap.add_argument("--max-interval", type=int, default=50,
                     help="per-receiver schedule leg: longest reuse (frames)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched leg (64 uneven scenes, one CUDA graph)")
     ap.add_argument("--no-static-cache", action="store_true",
                     help="cached legs: trace without the static-hit cache")
     ap.add_argument("--profile", action="store_true",
@@ -184,6 +186,51 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+def run_batched(engine, scenes, dev, reps=5):
+    """Batched form: 64 seeded scenes of uneven size (50-2000 buildings,
+    0-500 vehicles, 16-4000 receivers, 1-4 Tx, K 2-4, 1e5-4e6 rays) traced by
+    one persistent launch per bounce replayed from a CUDA graph (autotuned
+    variant), against the same 64 traces issued one after another; best of
+    `reps`, CUDA events; records compared scene by scene."""
+    import torch
+    descs = scenes.batched_scenes(seed=0, n=64)
+    scs = []
+    for d in descs:
+        g = engine.Scene(d, device=dev)
+        g.update(d.frame(0))
+        scs.append(g)
+    caps = [max(4096, 8 * g.n_tx * g.n_rx) for g in scs]
+    outs = [engine.Paths(c, dev) for c in caps]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seq = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record()
+        for g, o in zip(scs, outs):
+            g.trace_async(o)
+        e1.record()
+        for g in scs:
+            g.sync()
+        seq.append(e0.elapsed_time(e1))
+    b = engine.Batch(scs, capacity=caps, autotune=True)
+    bat, segs = [], 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record()
+        b.trace_async()
+        e1.record()
+        st = b.sync()
+        bat.append(e0.elapsed_time(e1))
+        segs = sum(st["segments"])
+    same = all(np.array_equal(o.records(), ob.records()) for o, ob in zip(outs, b.outs))
+    return {"scenes": len(scs), "primary_rays": int(sum(d.n_rays * len(d.frame(0).tx_pos)
+                                                       for d in descs)),
+            "segments": int(segs), "batched_ms": min(bat), "sequential_ms": min(seq),
+            "speedup": min(seq) / min(bat), "identical_to_sequential": bool(same),
+            "variant": b.config(), "timing": "CUDA events around the enqueue of all work, "
+                                             "best of %d" % reps}
+
+
 def run_cpu_baseline(sc, fr, stride, budget_s=25.0):
     """The oracle as it stands on a strided ray sample of the same frame:
     discovery, deduplication, acceptance, field at both frequencies and the
@@ -576,6 +623,8 @@ def main():
                                 "frac_rx_over_0p5db": float(acc_p[:, 1].mean()),
                                 "median_abs_db": float(acc_p[:, 2].mean())}}
 
+    batched = None if args.no_batched else run_batched(engine, scenes, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(sc, sc.frame(base + args.warmup), stride=2000)
@@ -598,6 +647,7 @@ def main():
             "plain_with_static_cache": static_cache,
             "cached": accuracy,
             "cached_per_receiver": per_rx,
+            "batched": batched,
             "segments_per_frame": seg / len(stats),
             "paths_per_frame": last["accepted"],
             "candidates_per_frame": last["candidates"],
