@@ -129,7 +129,7 @@ void enqueue(emrt_batch_s *b, int variant, bool sort_rays, cudaStream_t st) {
     if (bb > 0 && sort_rays) {
       launch_ray_keys(L.rin, &c->n_ray[bb], b->scenes[b->largest]->bbox, b->rkeys[0], b->rvals[0],
                       st, true);
-      bool alt = radix_sort<1>(&c->n_ray[bb], b->rkeys[0], b->rvals[0], b->rkeys[1], b->rvals[1], 32,
+      bool alt = radix_sort<1>(&c->n_ray[bb], b->rkeys[0], b->rvals[0], b->rkeys[1], b->rvals[1], 24,
                                b->hist, st, b->total);
       L.order = b->rvals[alt ? 1 : 0];
     }

@@ -437,7 +437,7 @@ __global__ void k_ray_keys(const Ray *r, const uint32_t *n, const float4 *bb, Ke
     float4 o = r[i].o_L, d = r[i].d_id;
     uint32_t m, oc;
     ray_cell(f3(o), f3(d), lo, hi, m, oc);
-    keys[i].w[0] = batched ? ((__float_as_uint(d.w) >> 26) << 26 | (m >> 1) << 6 | oc >> 26)
+    keys[i].w[0] = batched ? ((__float_as_uint(d.w) >> 26) << 18 | (m >> 9) << 6 | oc >> 26)
                            : ((m >> 6) << 9 | oc >> 23);
     vals[i] = i;
   }

@@ -105,7 +105,8 @@ void launch_batch_scatter(const BatchScene *tab, uint32_t n_scenes, const uint32
 // Coherence keys of the *n rays (24 bits, three radix passes): origin cell
 // (5-bit Morton per axis in the scene box) then direction bin (9 bits of the
 // octahedral code).
-// batched: scene (6 bits) | origin cell (20 bits) | direction bin (6 bits)
+// batched (24 bits): scene (6) | origin cell (4-bit Morton per axis, 12) |
+// direction bin (6)
 void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1> *keys,
                      uint32_t *vals, cudaStream_t s, bool batched = false);
 
