@@ -99,7 +99,9 @@ typedef struct {
   uint32_t max_rx;           /* capacity for receivers                      */
   uint32_t max_tx;           /* capacity for transmitters (<= 255)          */
   uint32_t rebuild_every;    /* dynamic BVH: full rebuild every n updates,
-                                refit otherwise (0 = default 10)            */
+                                refit otherwise (0 = default 1: on the city
+                                a refitted tree cost more traversal than
+                                the rebuild it saves)                       */
 } emrt_scene_desc;
 
 /* Sec. II-A/III-A: builds the static LBVH once (Morton codes, radix sort,

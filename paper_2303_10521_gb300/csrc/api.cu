@@ -181,7 +181,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   s->max_rx = d->max_rx;
   s->max_tx = d->max_tx;
   s->veh_mat = d->veh_mat;
-  s->rebuild_every = d->rebuild_every ? d->rebuild_every : 10;
+  s->rebuild_every = d->rebuild_every ? d->rebuild_every : 1;
   auto fail = [&](cudaError_t e) {
     emrt_scene_destroy(s);
     return cuda_status(e);

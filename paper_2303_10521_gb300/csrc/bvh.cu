@@ -20,17 +20,25 @@ __device__ inline uint64_t spread3(uint32_t v) {
   return x;
 }
 
-// 63-bit Morton code of p quantised in the cube spanned by the largest extent
-// of the box (all axes share one scale), so that a flat scene is split along
-// its long axes first instead of slicing it into thin horizontal slabs.
-__device__ inline uint64_t morton63(float3 p, const float4 *bb) {
+// Morton code (3 AB bits, AB <= 21 per axis) of p quantised in the cube
+// spanned by the largest extent of the box (all axes share one scale), so
+// that a flat scene is split along its long axes first instead of slicing it
+// into thin horizontal slabs.  Equal codes are told apart by index in the
+// hierarchy (delta), so coarse codes only cost tree quality.
+template <int AB>
+__device__ inline uint64_t morton_code(float3 p, const float4 *bb) {
   float4 lo = bb[0], hi = bb[1];
   float ext = fmaxf(fmaxf(hi.x - lo.x, hi.y - lo.y), fmaxf(hi.z - lo.z, 1e-6f));
   float q[3] = {(p.x - lo.x) / ext, (p.y - lo.y) / ext, (p.z - lo.z) / ext};
   uint32_t c[3];
-  for (int k = 0; k < 3; k++) c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * 2097151.f);
+  for (int k = 0; k < 3; k++)
+    c[k] = (uint32_t)(fminf(fmaxf(q[k], 0.f), 1.f) * (float)((1u << AB) - 1u));
   return spread3(c[0]) << 2 | spread3(c[1]) << 1 | spread3(c[2]);
 }
+// code bits per primitive kind: the static triangles (LBVH fallback) use 63;
+// vehicle boxes and receiver points, rebuilt every frame, use 30 (2 m cells
+// over a 2 km cube) so that their sort takes four passes instead of eight
+constexpr int kMortonBitsTri = 21, kMortonBitsDyn = 10;
 
 __device__ inline void put_key(KeyW<2> &k, uint64_t v) {
   k.w[0] = (uint32_t)v;
@@ -47,7 +55,7 @@ __global__ void k_morton_tris(const float *t, uint32_t n, const float4 *bb, KeyW
   const float *v = t + 9ull * i;
   float3 c = make_float3((v[0] + v[3] + v[6]) * (1.f / 3.f), (v[1] + v[4] + v[7]) * (1.f / 3.f),
                          (v[2] + v[5] + v[8]) * (1.f / 3.f));
-  put_key(keys[i], morton63(c, bb));
+  put_key(keys[i], morton_code<kMortonBitsTri>(c, bb));
   idx[i] = i;
 }
 
@@ -56,7 +64,8 @@ __global__ void k_morton_boxes(const float4 *lo, const float4 *hi, uint32_t n, c
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 a = lo[i], b = hi[i];
-  put_key(keys[i], morton63(make_float3(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)), bb));
+  put_key(keys[i], morton_code<kMortonBitsDyn>(
+                       make_float3(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)), bb));
   idx[i] = i;
 }
 
@@ -64,7 +73,7 @@ __global__ void k_morton_points(const float4 *p, uint32_t n, const float4 *bb, K
                                 uint32_t *idx) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  put_key(keys[i], morton63(f3(p[i]), bb));
+  put_key(keys[i], morton_code<kMortonBitsDyn>(f3(p[i]), bb));
   idx[i] = i;
 }
 
@@ -339,7 +348,8 @@ __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
 template <int KIND>
 cudaError_t sort_codes(BVHBuf &b, uint32_t *hist, cudaStream_t s) {
   emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(b.d_n, b.n);
-  bool alt = radix_sort<2>(b.d_n, b.keys, b.idx, b.keys2, b.idx2, 63, hist, s, b.n);
+  const int bits = 3 * (KIND == PRIM_TRI ? kMortonBitsTri : kMortonBitsDyn);
+  bool alt = radix_sort<2>(b.d_n, b.keys, b.idx, b.keys2, b.idx2, bits, hist, s, b.n);
   if (alt) {
     std::swap(b.keys, b.keys2);
     std::swap(b.idx, b.idx2);

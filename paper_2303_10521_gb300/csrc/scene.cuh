@@ -9,7 +9,7 @@ using namespace emrt;  // internal header: included by the C-ABI units only
 struct emrt_scene_s {
   int device = 0;
   uint32_t Fs = 0, T = 0, V = 0, NV = 0, max_rx = 0, max_tx = 0, veh_mat = 0;
-  uint32_t rebuild_every = 10, n_updates = 0;
+  uint32_t rebuild_every = 1, n_updates = 0;
   double4 *face_plane = nullptr;
   uint4 *face_info = nullptr;
   float4 *face_vert = nullptr;

@@ -74,7 +74,7 @@ class Scene:
     dynamic state, scratch buffers.  Wraps ``emrt_scene``."""
 
     def __init__(self, scene, device=None, max_rx: Optional[int] = None,
-                 max_tx: Optional[int] = None, rebuild_every: int = 10, stream=None):
+                 max_tx: Optional[int] = None, rebuild_every: int = 1, stream=None):
         self.lib = N.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.desc = scene
