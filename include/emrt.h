@@ -178,6 +178,12 @@ emrt_status emrt_trace_backward(emrt_scene sc, const emrt_trace_params *p,
                                 const uint32_t *rx_ids, uint32_t n_ids,
                                 emrt_paths *out, emrt_stream s);
 
+/* The cached frame of emrt_revalidate without flags (invalid paths removed,
+ * order kept); *n_evicted (device uint32, may be NULL) receives the number
+ * of records removed. */
+emrt_status emrt_revalidate_cache(emrt_scene sc, emrt_paths *cache, uint32_t *n_evicted,
+                                  emrt_stream s);
+
 /* Cached frame (Sec. II-A path caching, Sec. III-B): re-runs image-method
  * acceptance and occlusion on every record of `cache` with the current
  * poses; removes the paths that failed (keeps order) unless
@@ -364,6 +370,15 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n,
 emrt_status emrt_batch_trace(emrt_batch b, emrt_stream s);
 /* Waits and reports errors as emrt_sync (stats summed over the batch). */
 emrt_status emrt_batch_sync(emrt_batch b, emrt_stream s, emrt_stats *st);
+/* One call for a batch: the first call with a given (scenes, params, outs)
+ * creates the batch (emrt_batch_create, no autotuning) and captures its graph;
+ * later calls with the same arrays replay it.  Traces, then synchronises the
+ * stream and returns as emrt_batch_sync (the outputs' counts are written).
+ * params and outs are arrays of n.  Destroying one of the scenes discards the
+ * batches that use it. */
+emrt_status emrt_trace_batched(const emrt_scene *scenes, uint32_t n,
+                               const emrt_trace_params *params, emrt_paths *outs,
+                               emrt_stream s);
 /* Human-readable traversal variant chosen for the batch. */
 emrt_status emrt_batch_config(emrt_batch b, char *buf, uint32_t len);
 void emrt_batch_destroy(emrt_batch b);

@@ -76,6 +76,9 @@ SIGNATURES = {
     "emrt_trace_backward": (C.c_int, [vp, C.POINTER(TraceParams), vp, C.c_uint32,
                                       C.POINTER(PathsC), vp]),
     "emrt_revalidate": (C.c_int, [vp, C.POINTER(PathsC), u32, vp]),
+    "emrt_revalidate_cache": (C.c_int, [vp, C.POINTER(PathsC), vp, vp]),
+    "emrt_trace_batched": (C.c_int, [C.POINTER(vp), u32, C.POINTER(TraceParams),
+                                     C.POINTER(PathsC), vp]),
     "emrt_cache_merge": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(PathsC), vp]),
     "emrt_channel": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, dbl,
                                C.POINTER(ChannelOut), vp]),

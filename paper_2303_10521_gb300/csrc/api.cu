@@ -106,6 +106,12 @@ __global__ void k_publish_count(const Counters *c, uint32_t *count) { *count = c
 
 __global__ void k_clamp_count(const uint32_t *n, uint32_t cap, uint32_t *out) { *out = min(*n, cap); }
 
+// records removed by the last revalidation: entered - kept
+__global__ void k_evicted(const Counters *c, uint32_t *out) { *out = c->n_eff - c->n_accepted; }
+void launch_evicted(const Counters *c, uint32_t *out, cudaStream_t s) {
+  emrt::note_launch(), k_evicted<<<1, 1, 0, s>>>(c, out);
+}
+
 cudaError_t ensure_cand(emrt_scene_s *s, uint64_t need) {
   if (need <= s->cand_cap && s->cand) return cudaSuccess;
   uint64_t c = 0;
@@ -239,6 +245,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
 
 void emrt_scene_destroy(emrt_scene s) {
   if (!s) return;
+  batch_forget_scene(s);
   cudaFree(s->face_plane); cudaFree(s->face_info); cudaFree(s->face_vert); cudaFree(s->bbox);
   bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb); bvh_free(s->txb);
   cudaFree(s->src_pos);
@@ -576,6 +583,15 @@ emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emr
   launch_scatter(s->uniq, &c->n_eff, s->head, s->pos, cache->rec, cache->capacity, &c->n_accepted,
                  c, st);
   emrt::note_launch(), k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+  CK(cudaGetLastError());
+  return EMRT_OK;
+}
+
+emrt_status emrt_revalidate_cache(emrt_scene s, emrt_paths *cache, uint32_t *n_evicted,
+                                  emrt_stream stream) {
+  emrt_status e = emrt_revalidate(s, cache, 0u, stream);
+  if (e != EMRT_OK || !n_evicted) return e;
+  launch_evicted(s->ctr, n_evicted, (cudaStream_t)stream);
   CK(cudaGetLastError());
   return EMRT_OK;
 }

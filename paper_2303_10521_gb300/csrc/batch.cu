@@ -369,6 +369,72 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n, const emrt_t
   return EMRT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// batches of emrt_trace_batched, keyed by the bytes of their argument arrays
+std::mutex g_reg_mu;
+std::map<std::string, emrt_batch> g_reg;
+std::string batch_key(const emrt_scene *scenes, uint32_t n, const emrt_trace_params *params,
+                      const emrt_paths *outs) {
+  std::string k;
+  auto put = [&](uint64_t v) { k.append(reinterpret_cast<const char *>(&v), sizeof(v)); };
+  for (uint32_t i = 0; i < n; i++) {  // field by field: struct padding is not part of it
+    put((uint64_t)(uintptr_t)scenes[i]);
+    const emrt_trace_params &p = params[i];
+    put(p.max_depth);
+    put(p.n_rays);
+    put(p.ray_offset);
+    put(p.ray_stride);
+    put(p.ray_count);
+    put(p.flags);
+    put((uint64_t)(uintptr_t)outs[i].rec);
+    put(outs[i].capacity);
+    put((uint64_t)(uintptr_t)outs[i].count);
+  }
+  return k;
+}
+}  // namespace
+
+// Drops the registered batches that use scene s (called by emrt_scene_destroy).
+void batch_forget_scene(emrt_scene s) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  for (auto it = g_reg.begin(); it != g_reg.end();) {
+    bool uses = false;
+    for (emrt_scene q : it->second->scenes) uses |= q == s;
+    if (uses) {
+      emrt_batch_destroy(it->second);
+      it = g_reg.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+extern "C" {
+
+emrt_status emrt_trace_batched(const emrt_scene *scenes, uint32_t n,
+                               const emrt_trace_params *params, emrt_paths *outs,
+                               emrt_stream s) {
+  if (!scenes || !params || !outs || n == 0 || n > kBatchMaxScenes) return EMRT_ERR_INVALID_ARG;
+  emrt_batch b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    const std::string key = batch_key(scenes, n, params, outs);
+    auto it = g_reg.find(key);
+    if (it != g_reg.end()) {
+      b = it->second;
+    } else {
+      emrt_status e = emrt_batch_create(scenes, n, params, outs, 0u, s, &b);
+      if (e != EMRT_OK) return e;
+      g_reg[key] = b;
+    }
+  }
+  emrt_status e = emrt_batch_trace(b, s);
+  if (e != EMRT_OK) return e;
+  return emrt_batch_sync(b, s, nullptr);
+}
+
 void emrt_batch_destroy(emrt_batch b) {
   if (!b) return;
   drop_graph(b);

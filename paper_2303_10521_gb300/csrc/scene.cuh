@@ -66,6 +66,9 @@ struct emrt_scene_s {
 };
 
 
+// batch.cu: discards the emrt_trace_batched batches that use scene s
+void batch_forget_scene(emrt_scene s);
+
 namespace emrt {
 inline GeomView geom(const emrt_scene_s *s) {
   GeomView g;

@@ -134,6 +134,16 @@ class Scene:
             self.n_rx, _ptr(t["tx_pos"]), _ptr(t["tx_vel"]), self.n_tx, _stream(stream)),
             "emrt_scene_update_dynamic")
 
+    def set_transmitters(self, tx_pos, stream=None):
+        """Moves the transmitters to tx_pos (rounded to float32), keeping the
+        rest of the current frame; no call when they are already there."""
+        t = _dev(tx_pos, torch.float32, self.device).reshape(-1, 3).contiguous()
+        if t.shape == self._frame["tx_pos"].shape and torch.equal(t, self._frame["tx_pos"]):
+            return
+        fr = dict(self._frame)
+        fr["tx_pos"] = t
+        self.update(type("Frame", (), fr), stream)
+
     def trace_async(self, out: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
                     keep_rejected=False, sort_rays=True, stream=None, wide_bvh=False,
                     static_cache=False):
@@ -209,6 +219,15 @@ class Scene:
         N.check(self.lib.emrt_revalidate(self.h, C.byref(pc),
                                          N.REVALIDATE_KEEP if keep else 0, _stream(stream)),
                 "emrt_revalidate")
+
+    def revalidate_cache(self, cache: Paths, stream=None) -> torch.Tensor:
+        """revalidate (invalid paths removed); returns the device count of
+        records evicted."""
+        ev = torch.zeros(1, dtype=torch.int32, device=self.device)
+        pc = cache.c()
+        N.check(self.lib.emrt_revalidate_cache(self.h, C.byref(pc), _ptr(ev), _stream(stream)),
+                "emrt_revalidate_cache")
+        return ev
 
     def merge(self, cache: Paths, fresh: Paths, stream=None):
         a, b = cache.c(), fresh.c()
@@ -357,6 +376,27 @@ class Batch:
         buf = C.create_string_buffer(128)
         N.check(self.lib.emrt_batch_config(self.h, buf, 128), "emrt_batch_config")
         return buf.value.decode()
+
+
+def trace_batched(scenes, outs, params=None, stream=None):
+    """One-call batched discovery (emrt_trace_batched) into the caller's Paths
+    outs[i]; the graph is captured on the first call with these scenes,
+    params and outputs and replayed afterwards.  Synchronises."""
+    lib = N.load()
+    n = len(scenes)
+    ps = []
+    for i, sc in enumerate(scenes):
+        p = dict(n_rays=sc.desc.n_rays, max_depth=sc.desc.max_depth, offset=0, stride=1,
+                 count=0)
+        if params is not None:
+            p.update(params[i])
+        ps.append(N.TraceParams(int(p["max_depth"]), int(p["n_rays"]), int(p["offset"]),
+                                int(p["stride"]), int(p["count"]), 0))
+    hs = (C.c_void_p * n)(*[sc.h for sc in scenes])
+    pa = (N.TraceParams * n)(*ps)
+    oa = (N.PathsC * n)(*[o.c() for o in outs])
+    N.check(lib.emrt_trace_batched(hs, n, pa, oa, _stream(stream)), "emrt_trace_batched")
+    return outs
 
 
 def channel_correlation(h_series: torch.Tensor, max_lag: int, stream=None) -> torch.Tensor:

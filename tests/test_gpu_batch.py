@@ -47,3 +47,37 @@ def test_batched_equals_sequential(tmp_path, monkeypatch):
                 assert got.shape == ref.shape, (d.name, got.shape, ref.shape)
                 assert np.array_equal(got, ref), d.name
     assert "block" in b.config()
+
+
+def test_trace_batched_one_call():
+    """emrt_trace_batched: the first call captures, later calls replay, the
+    outputs equal the per-scene traces; destroying a scene drops its batch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_10521_gb300 import engine
+    descs = _small_batch(n=5, seed=7)
+    scs = []
+    for d in descs:
+        g = engine.Scene(d)
+        g.update(d.frame(0))
+        scs.append(g)
+    caps = [max(4096, 8 * g.n_tx * g.n_rx) for g in scs]
+    refs = [g.trace(capacity=c).records() for g, c in zip(scs, caps)]
+    outs = [engine.Paths(c, scs[0].device) for c in caps]
+    for _ in range(3):
+        engine.trace_batched(scs, outs)
+        for o, r in zip(outs, refs):
+            assert np.array_equal(o.records(), r)
+    # after a frame update the replay traces the new poses
+    for d, g in zip(descs, scs):
+        g.update(d.frame(1))
+    refs1 = [g.trace(capacity=c).records() for g, c in zip(scs, caps)]
+    engine.trace_batched(scs, outs)
+    for o, r in zip(outs, refs1):
+        assert np.array_equal(o.records(), r)
+    del scs[2]   # destroys that scene and with it the registered batch
+    import gc
+    gc.collect()
+    engine.trace_batched(scs, [outs[i] for i in (0, 1, 3, 4)])
+    for o, r in zip([outs[i] for i in (0, 1, 3, 4)], [refs1[i] for i in (0, 1, 3, 4)]):
+        assert np.array_equal(o.records(), r)

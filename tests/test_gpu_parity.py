@@ -142,6 +142,21 @@ def test_district_subsample_parity(engine, stride, offset):
     assert rf["ok"], rf
 
 
+def test_revalidate_cache_counts_evictions(engine):
+    """emrt_revalidate_cache keeps what emrt_revalidate keeps and reports the
+    number of records it removed."""
+    sc = S.district_scene(seed=1)
+    g = _gpu(engine, sc)
+    p0 = g.trace(stride=53)
+    p1 = g.trace(stride=53)
+    n0 = p0.n()
+    g.update(sc.frame(5))
+    ev = g.revalidate_cache(p0)
+    g.revalidate(p1)
+    assert np.array_equal(p0.records(), p1.records())
+    assert int(ev.item()) == n0 - p0.n() and int(ev.item()) > 0
+
+
 def test_revalidation_and_merge(engine):
     """Cached frame: paths discovered at frame 0 revalidated with the poses of
     frame 3, flag by flag against the oracle; merge is a sorted union."""
