@@ -104,8 +104,10 @@ typedef struct {
                                 the rebuild it saves)                       */
 } emrt_scene_desc;
 
-/* Sec. II-A/III-A: builds the static LBVH once (Morton codes, radix sort,
- * binary radix tree, bottom-up boxes).  Synchronises the stream. */
+/* Sec. II-A/III-A: builds the static BVH once (binned SAH top-down on the
+ * GPU, bottom-up boxes; a Morton-code LBVH if the SAH tree would be deeper
+ * than the 64-entry traversal stack) and allocates the scene's buffers.
+ * Synchronises the stream. */
 emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream s,
                               emrt_scene *out);
 void emrt_scene_destroy(emrt_scene sc);
