@@ -59,7 +59,7 @@ extern "C" {
                                           origin cell and direction bin       */
 #define EMRT_TRACE_WIDE_BVH 0x4u       /* traverse the static geometry through
                                           its 4-wide BVH (same results; on
-                                          GB300 the binary LBVH is faster for
+                                          GB300 the binary BVH is faster for
                                           the city scenes measured)           */
 #define EMRT_TRACE_STATIC_CACHE 0x8u   /* keep the static-geometry closest hit of
                                           every ray segment between calls (see

@@ -1,7 +1,7 @@
 """Python front end of the emrt C-ABI: device memory and streams come from
 PyTorch; every computation runs in libemrt.so's CUDA kernels.
 
-    sc = Scene(scenes.city_scene())           # static LBVH built once
+    sc = Scene(scenes.city_scene())           # static BVH built once
     sc.update(sc_desc.frame(k))               # per frame: vehicles, Rx, Tx
     paths = sc.trace()                         # plain discovery + acceptance
     ch = sc.channel(paths, 3.5e9)              # per-path field, per-Rx stats
@@ -70,7 +70,7 @@ class ChannelResult:
 
 
 class Scene:
-    """A scene on one GPU: static geometry (with its LBVH), per-frame
+    """A scene on one GPU: static geometry (with its BVH), per-frame
     dynamic state, scratch buffers.  Wraps ``emrt_scene``."""
 
     def __init__(self, scene, device=None, max_rx: Optional[int] = None,
