@@ -255,6 +255,15 @@ def run_cpu_baseline(sc, fr, stride, budget_s=25.0):
             "mrays_per_s": float(segs.sum()) / dt / 1e6}
 
 
+def arm_config(ws):
+    """The workload both arms report (the reference arm runs a strided sample
+    of it, stated in its cpu_baseline)."""
+    return {"workload": "city 2x2 km, 6400 buildings (~293k triangles), 5000 vehicles, "
+                        "10k Rx, 4 Tx, 1e7 rays/Tx, K=4, fields at 3.5 and 28 GHz",
+            "method": "plain per-frame retrace", "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (3.8 GB ray buffers per bounce)"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -274,8 +283,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 1e4 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "city 2x2 km, 6400 buildings, 5000 vehicles, 10k Rx, 4 Tx, "
-                                   "1e7 rays/Tx, K=4, 3.5+28 GHz", "sample_stride": stride},
+            "config": arm_config(ws),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
                              "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -638,10 +646,7 @@ def main():
             "precision": "FP32 traversal and intersection; FP64 image points, path length, "
                          "phase, Fresnel field and reductions",
             "data": "synthetic",
-            "config": {"workload": "city 2x2 km, 6400 buildings (~293k triangles), 5000 vehicles, "
-                                   "10k Rx, 4 Tx, 1e7 rays/Tx, K=4, fields at 3.5 and 28 GHz",
-                       "method": "plain per-frame retrace", "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (3.8 GB ray buffers per bounce)"},
+            "config": arm_config(ws),
             "mrays_per_s": mrays,
             "receiver_frames_per_s_cached": cached_val,
             "plain_with_static_cache": static_cache,
