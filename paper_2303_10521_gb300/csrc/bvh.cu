@@ -444,8 +444,8 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
 
 // ---------------------------------------------------------------------------
 // Binned SAH top-down build (static triangles; built once).  Level by level,
-// one block per node range: centroid bounds, 32 bins along the longest axis,
-// surface-area-heuristic sweep, stable partition of the range.  Ranges of one
+// one block per node range: centroid bounds, 32 bins along each axis,
+// surface-area-heuristic sweep over all three, stable partition of the range.  Ranges of one
 // triangle become leaves.  Writes the same node format as the LBVH (child
 // codes and parent links); boxes are filled by the bottom-up refit.
 namespace {
@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(kSahBlock) k_sah_level(
     const float4 *bhi, uint32_t *perm, uint32_t *tmp, float4 *nodes, uint32_t *leaf_parent,
     SahTask *out, uint32_t *n_out, uint32_t *n_alloc) {
   __shared__ float sh[64];
-  __shared__ uint32_t bcnt[kSahBins];
-  __shared__ uint32_t blo_s[kSahBins][3], bhi_s[kSahBins][3];
+  __shared__ uint32_t bcnt[3][kSahBins];
+  __shared__ uint32_t blo_s[3][kSahBins][3], bhi_s[3][kSahBins][3];
   __shared__ int s_axis, s_split;
   __shared__ float s_lo, s_ext;
   __shared__ uint32_t s_carry, s_wsum[kSahBlock / 32];
@@ -539,80 +539,83 @@ __global__ void __launch_bounds__(kSahBlock) k_sah_level(
     lo3[k] = mn;
     hi3[k] = mx;
   }
-  if (threadIdx.x == 0) {
-    int ax = 0;
-    float ext = hi3[0] - lo3[0];
-    for (int k = 1; k < 3; k++)
-      if (hi3[k] - lo3[k] > ext) { ext = hi3[k] - lo3[k]; ax = k; }
-    s_axis = ax;
-    s_lo = lo3[ax];
-    s_ext = ext;
-    s_split = -1;
+  // bins along every axis of non-zero centroid extent; the split with the
+  // lowest surface-area cost over all three axes is taken
+  for (int t = threadIdx.x; t < 3 * kSahBins; t += blockDim.x) {
+    const int k = t / kSahBins, q = t % kSahBins;
+    bcnt[k][q] = 0;
+    for (int c = 0; c < 3; c++) {
+      blo_s[k][q][c] = 0xffffffffu;
+      bhi_s[k][q][c] = 0u;
+    }
   }
-  if (threadIdx.x < kSahBins) {
-    bcnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_split = -1;
+  __syncthreads();
+  float ext3[3];
+  for (int k = 0; k < 3; k++) ext3[k] = hi3[k] - lo3[k];
+  for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    const uint32_t p = perm[i];
+    const float4 c4 = cen[p], a = blo[p], z = bhi[p];
     for (int k = 0; k < 3; k++) {
-      blo_s[threadIdx.x][k] = 0xffffffffu;
-      bhi_s[threadIdx.x][k] = 0u;
+      if (!(ext3[k] > 0.f)) continue;
+      const int bin = min(kSahBins - 1, (int)((sel(c4, k) - lo3[k]) / ext3[k] * kSahBins));
+      atomicAdd(&bcnt[k][bin], 1u);
+      for (int c = 0; c < 3; c++) {
+        atomicMin(&blo_s[k][bin][c], f2o_d(sel(a, c)));
+        atomicMax(&bhi_s[k][bin][c], f2o_d(sel(z, c)));
+      }
     }
   }
   __syncthreads();
-  const int ax = s_axis;
-  const float lo = s_lo, ext = s_ext;
-  if (ext > 0.f) {
-    for (uint32_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-      uint32_t p = perm[i];
-      int bin = min(kSahBins - 1, (int)((sel(cen[p], ax) - lo) / ext * kSahBins));
-      atomicAdd(&bcnt[bin], 1u);
-      float4 a = blo[p], z = bhi[p];
-      for (int k = 0; k < 3; k++) {
-        atomicMin(&blo_s[bin][k], f2o_d(sel(a, k)));
-        atomicMax(&bhi_s[bin][k], f2o_d(sel(z, k)));
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {  // SAH sweep over the 31 bin boundaries
+  if (threadIdx.x == 0) {  // SAH sweep over the 31 bin boundaries of each axis
+    float best = 3.4e38f;
+    int bax = -1, bs = -1;
+    for (int k = 0; k < 3; k++) {
+      if (!(ext3[k] > 0.f)) continue;
       float rl[kSahBins][3], rh[kSahBins][3];
       uint32_t rc[kSahBins];
       float l3[3] = {3.4e38f, 3.4e38f, 3.4e38f}, h3[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
       uint32_t c = 0;
       for (int q = kSahBins - 1; q >= 0; q--) {
-        if (bcnt[q]) {
-          for (int k = 0; k < 3; k++) {
-            l3[k] = fminf(l3[k], o2f_d(blo_s[q][k]));
-            h3[k] = fmaxf(h3[k], o2f_d(bhi_s[q][k]));
+        if (bcnt[k][q]) {
+          for (int d = 0; d < 3; d++) {
+            l3[d] = fminf(l3[d], o2f_d(blo_s[k][q][d]));
+            h3[d] = fmaxf(h3[d], o2f_d(bhi_s[k][q][d]));
           }
         }
-        c += bcnt[q];
+        c += bcnt[k][q];
         rc[q] = c;
-        for (int k = 0; k < 3; k++) { rl[q][k] = l3[k]; rh[q][k] = h3[k]; }
+        for (int d = 0; d < 3; d++) { rl[q][d] = l3[d]; rh[q][d] = h3[d]; }
       }
-      float best = 3.4e38f;
-      int bs = -1;
       float a3[3] = {3.4e38f, 3.4e38f, 3.4e38f}, z3[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
       uint32_t lc = 0;
       for (int q = 0; q < kSahBins - 1; q++) {
-        if (bcnt[q]) {
-          for (int k = 0; k < 3; k++) {
-            a3[k] = fminf(a3[k], o2f_d(blo_s[q][k]));
-            z3[k] = fmaxf(z3[k], o2f_d(bhi_s[q][k]));
+        if (bcnt[k][q]) {
+          for (int d = 0; d < 3; d++) {
+            a3[d] = fminf(a3[d], o2f_d(blo_s[k][q][d]));
+            z3[d] = fmaxf(z3[d], o2f_d(bhi_s[k][q][d]));
           }
         }
-        lc += bcnt[q];
-        uint32_t rcnt = rc[q + 1];
+        lc += bcnt[k][q];
+        const uint32_t rcnt = rc[q + 1];
         if (lc == 0 || rcnt == 0) continue;
-        float dl[3] = {z3[0] - a3[0], z3[1] - a3[1], z3[2] - a3[2]};
-        float dr[3] = {rh[q + 1][0] - rl[q + 1][0], rh[q + 1][1] - rl[q + 1][1],
-                       rh[q + 1][2] - rl[q + 1][2]};
-        float al = dl[0] * dl[1] + dl[1] * dl[2] + dl[2] * dl[0];
-        float ar = dr[0] * dr[1] + dr[1] * dr[2] + dr[2] * dr[0];
-        float cost = al * lc + ar * rcnt;
-        if (cost < best) { best = cost; bs = q + 1; }
+        const float dl[3] = {z3[0] - a3[0], z3[1] - a3[1], z3[2] - a3[2]};
+        const float dr[3] = {rh[q + 1][0] - rl[q + 1][0], rh[q + 1][1] - rl[q + 1][1],
+                             rh[q + 1][2] - rl[q + 1][2]};
+        const float al = dl[0] * dl[1] + dl[1] * dl[2] + dl[2] * dl[0];
+        const float ar = dr[0] * dr[1] + dr[1] * dr[2] + dr[2] * dr[0];
+        const float cost = al * lc + ar * rcnt;
+        if (cost < best) { best = cost; bax = k; bs = q + 1; }
       }
-      s_split = bs;
     }
-    __syncthreads();
+    s_split = bs;
+    s_axis = bax < 0 ? 0 : bax;
+    s_lo = lo3[s_axis];
+    s_ext = ext3[s_axis];
   }
+  __syncthreads();
+  const int ax = s_axis;
+  const float lo = s_lo, ext = s_ext;
   const int split = s_split;
   // stable partition of the range into tmp, then back into perm
   uint32_t nl;
