@@ -444,13 +444,13 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
 
 // ---------------------------------------------------------------------------
 // Binned SAH top-down build (static triangles; built once).  Level by level,
-// one block per node range: centroid bounds, 32 bins along each axis,
+// one block per node range: centroid bounds, 64 bins along each axis,
 // surface-area-heuristic sweep over all three, stable partition of the range.  Ranges of one
 // triangle become leaves.  Writes the same node format as the LBVH (child
 // codes and parent links); boxes are filled by the bottom-up refit.
 namespace {
 
-constexpr int kSahBins = 32;
+constexpr int kSahBins = 64;
 constexpr int kSahBlock = 256;
 constexpr int kSahMaxDepth = 60;  // levels; the traversal stack holds 64 entries
 // ranges of up to this many triangles become leaves (1-4; on the city 1 is
