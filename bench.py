@@ -32,11 +32,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Mrays/s traversal and receiver-frames/s channel update (2x2km,10k Rx), cached vs plain"
 UNIT = "receiver-frames/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bounce_city_traffic.txt")
-# sources of k_bounce (the figures of the committed ncu capture hold while
-# these are unchanged)
+# sources of k_bounce and of the trees it traverses (the figures of the
+# committed ncu capture hold while these are unchanged)
 KERNEL_SOURCES = ["paper_2303_10521_gb300/csrc/bounce.cuh",
                   "paper_2303_10521_gb300/csrc/traverse.cuh",
-                  "paper_2303_10521_gb300/csrc/common.cuh"]
+                  "paper_2303_10521_gb300/csrc/common.cuh",
+                  "paper_2303_10521_gb300/csrc/bvh.cu"]
 
 
 def parse():
