@@ -342,8 +342,8 @@ typedef struct {
 emrt_status emrt_sync(emrt_scene sc, emrt_stream s, emrt_stats *st);
 
 /* ---------------------------------------------------------------------
- * Batched discovery over many scenes of uneven size (spec: batching;
- * the paper runs one scene at a time).  One persistent traversal launch per
+ * Batched discovery over many scenes of uneven size (the paper runs one
+ * scene at a time).  One persistent traversal launch per
  * bounce serves the rays of every scene of the batch; deduplication,
  * acceptance and the scatter to each scene's output follow once.  The launch
  * sequence is captured into a CUDA graph on the first emrt_batch_trace and
