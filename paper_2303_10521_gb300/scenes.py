@@ -416,6 +416,53 @@ def toy_scene(seed: int = 0, n_rays: int = 100_000, depth: int = 2) -> Scene:
                  n_frames=1, static_frame=fr)
 
 
+def tiny_scene(seed: int = 0, n_rays: int = 200_000, depth: int = 3) -> Scene:
+    """Random tiny scene for property tests: 60x60 m ground, 2-4 concrete box
+    buildings (6 faces each, at most 25 static faces in all), 0-2 metal
+    vehicle boxes, 1-2 transmitters and 6 receivers placed outside the
+    buildings, K = 3, 3.5 GHz."""
+    rng = np.random.default_rng([seed, 777])
+    fb = _FaceBuilder()
+    fb.add_ground(-30.0, 30.0, -30.0, 30.0, 1)
+    boxes = []
+    n_b = int(rng.integers(2, 5))
+    while len(boxes) < n_b:
+        w, d = rng.uniform(5, 15, 2)
+        cx, cy = rng.uniform(-22, 22, 2)
+        b = (cx - w / 2, cy - d / 2, cx + w / 2, cy + d / 2)
+        if any(b[0] < o[2] + 2 and o[0] < b[2] + 2 and b[1] < o[3] + 2
+               and o[1] < b[3] + 2 for o in boxes):
+            continue
+        boxes.append(b)
+    for b in boxes:
+        fb.add_prism(_box_footprint(*b), rng.uniform(5, 20), MAT_CONCRETE)
+
+    def outside(x, y, m=1.0):
+        return not any(o[0] - m <= x <= o[2] + m and o[1] - m <= y <= o[3] + m for o in boxes)
+
+    def free_points(n, z_lo, z_hi):
+        pts = []
+        while len(pts) < n:
+            x, y = rng.uniform(-28, 28, 2)
+            if outside(x, y, 3.0):
+                pts.append((x, y, rng.uniform(z_lo, z_hi)))
+        return np.asarray(pts, np.float32)
+
+    tx = free_points(int(rng.integers(1, 3)), 4.0, 15.0)
+    rx = free_points(6, 1.0, 3.0)
+    vpos = free_points(int(rng.integers(0, 3)), 0.75, 0.75)
+    off, xyz, fmat, tris, tface = fb.arrays()
+    eps, sig, gam = material_table()
+    z = lambda n: np.zeros((n, 3), np.float32)
+    fr = Frame(vpos, z(len(vpos)), rx, z(len(rx)), tx, z(len(tx)))
+    return Scene(name=f"tiny{seed}", face_off=off, face_xyz=xyz, face_mat=fmat,
+                 tri_xyz=tris, tri_face=tface,
+                 veh_half=np.tile(np.float32([[2.25, 0.9, 0.75]]), (len(vpos), 1)),
+                 veh_mat=MAT_METAL, eps_r=eps, sigma=sig, gamma=gam, n_rays=n_rays,
+                 max_depth=depth, freqs=[3.5e9], tx_power_w=1.0, dt=0.1,
+                 n_frames=1, static_frame=fr)
+
+
 def district_scene(seed: int = 0, n_rays: int = 1_000_000, depth: int = 3,
                    n_veh: int = 200, n_rx: int = 1000) -> Scene:
     """500x500 m grid, 400 convex extruded buildings (~20k triangles),

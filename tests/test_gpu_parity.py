@@ -142,6 +142,35 @@ def test_district_subsample_parity(engine, stride, offset):
     assert rf["ok"], rf
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_random_tiny_scenes(engine, seed):
+    """Property test on random tiny scenes (<= 25 static faces, 0-2 vehicles,
+    K = 3): discovery equals the oracle's on the same rays except rays it
+    flags, acceptance agrees except flagged paths, and the accepted set lies
+    in the exhaustive image enumeration and holds >= 98 % of its power."""
+    sc = S.tiny_scene(seed)
+    fr = sc.frame(0)
+    g = _gpu(engine, sc)
+    o = oracle.OracleScene(sc, fr)
+    gu = rec_to_paths(g.trace(keep_rejected=True).records())
+    cands, ray_marg, _ = oracle.trace(o, sc.n_rays, sc.max_depth)
+    rc = compare_candidates(gu, cands, ray_marg)
+    assert not rc["missing"] and not rc["extra_bad"], rc
+    ra = compare_acceptance(o, gu)
+    assert ra["n_diff_unflagged"] == 0, ra
+    acc = rec_to_paths(g.trace().records())
+    ex = oracle.enumerate_paths(o, sc.max_depth)
+    kex = [tuple(r) for r in oracle.key_fields(ex).tolist()]
+    kacc = {tuple(r) for r in oracle.key_fields(acc).tolist()}
+    outside = [i for i, k in enumerate(oracle.key_fields(acc).tolist()) if tuple(k) not in set(kex)]
+    if outside:  # only paths the oracle places within the margin
+        _, vm = oracle.validate(o, acc[outside])
+        assert (vm != 0).all(), acc[outside]
+    a, _, _ = oracle.field(o, ex, sc.freqs[0])
+    w = np.abs(a) ** 2
+    assert sum(wi for k, wi in zip(kex, w) if k in kacc) >= 0.98 * w.sum()
+
+
 def test_revalidate_cache_counts_evictions(engine):
     """emrt_revalidate_cache keeps what emrt_revalidate keeps and reports the
     number of records it removed."""
