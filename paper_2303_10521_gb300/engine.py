@@ -61,6 +61,22 @@ class Paths:
         n = min(self.n(), self.capacity)
         return self.rec[:n].cpu().numpy().view(np.uint32)
 
+    def save(self, path: str):
+        """Checkpoint of the path set (e.g. the cache of a frame sequence):
+        its canonical records as a uint32 [n, 8] .npy file."""
+        np.save(path, self.records())
+
+    @classmethod
+    def load(cls, path: str, device, capacity: Optional[int] = None) -> "Paths":
+        """A path set from save(), on `device`, with room for `capacity`
+        records (default: the records saved)."""
+        r = np.load(path).astype(np.uint32).reshape(-1, N.PATH_WORDS)
+        p = cls(max(len(r), capacity or 0), device)
+        if len(r):
+            p.rec[:len(r)] = torch.from_numpy(r.view(np.int32)).to(device)
+        p.count.fill_(len(r))
+        return p
+
 
 @dataclass
 class ChannelResult:

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -39,3 +41,22 @@ def test_product_package_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "emrt_oracle" not in txt, f
+
+
+def test_paths_checkpoint_roundtrip(tmp_path):
+    """A path set saved and loaded again (checkpoint/resume of a cache) keeps
+    its records and count; the capacity can grow on load."""
+    import torch
+    from paper_2303_10521_gb300 import engine
+    p = engine.Paths(16, "cpu")
+    recs = np.arange(5 * 8, dtype=np.uint32).reshape(5, 8) * np.uint32(2654435761)
+    p.rec[:5] = torch.from_numpy(recs.view(np.int32))
+    p.count.fill_(5)
+    f = str(tmp_path / "cache.npy")
+    p.save(f)
+    q = engine.Paths.load(f, "cpu", capacity=64)
+    assert q.capacity == 64 and q.n() == 5
+    assert np.array_equal(q.records(), recs)
+    e = engine.Paths(4, "cpu")
+    e.save(f)
+    assert engine.Paths.load(f, "cpu").n() == 0
