@@ -377,7 +377,7 @@ def main():
         byt += 64 * (s["node_visits"] + s["dyn_node_visits"] + s["rx_node_visits"])
         byt += 48 * s["tri_tests"] + 32 * s["box_tests"] + 16 * s["rx_tests"]
         byt += 16 * sg[0] + 48 * sum(sg[1:])          # ray reads
-        byt += 48 * sum(sg[1:])                        # reflected rays written
+        byt += (48 + 8) * sum(sg[1:])                  # reflected rays written, with key
         byt += 32 * s["candidates"]
     launches_trav = (K + 1) * len(stats)
     peak, peak_kind = measured_peaks()
