@@ -98,6 +98,18 @@ __global__ void k_update(const float *vp, const float *vv, const float4 *half, u
   }
 }
 
+// corners of the merged per-frame tree: vehicle boxes, then receiver points
+__global__ void k_mix_prims(const float4 *vlo, const float4 *vhi, uint32_t V, const float4 *rx,
+                            uint32_t R, float4 *lo, float4 *hi) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < V) {
+    lo[i] = vlo[i];
+    hi[i] = vhi[i];
+  } else if (i < V + R) {
+    lo[i] = hi[i] = rx[i - V];
+  }
+}
+
 __global__ void k_check_cand(Counters *c, uint32_t cap) {
   if (c->n_cand > cap) atomicOr(&c->err, ERR_CAND_OVERFLOW);
 }
@@ -222,6 +234,9 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = bvh_alloc(s->dyn, PRIM_BOX, std::max(s->V, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->rxb, PRIM_POINT, std::max(s->max_rx, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->txb, PRIM_POINT, std::max(s->max_tx, 2u)))) return fail(e);
+  if ((e = bvh_alloc(s->mix, PRIM_BOX, std::max(s->V + s->max_rx, 2u)))) return fail(e);
+  if ((e = grow(&s->mix_lo, c, s->V + s->max_rx))) return fail(e); c = 0;
+  if ((e = grow(&s->mix_hi, c, s->V + s->max_rx))) return fail(e); c = 0;
   uint32_t V1 = std::max(s->V, 1u);
   if ((e = grow(&s->veh_half, c, V1))) return fail(e); c = 0;
   if ((e = grow(&s->veh_lo, c, V1))) return fail(e); c = 0;
@@ -247,7 +262,8 @@ void emrt_scene_destroy(emrt_scene s) {
   if (!s) return;
   batch_forget_scene(s);
   cudaFree(s->face_plane); cudaFree(s->face_info); cudaFree(s->face_vert); cudaFree(s->bbox);
-  bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb); bvh_free(s->txb);
+  bvh_free(s->stat); bvh_free(s->dyn); bvh_free(s->rxb); bvh_free(s->txb); bvh_free(s->mix);
+  cudaFree(s->mix_lo); cudaFree(s->mix_hi);
   cudaFree(s->src_pos);
   cudaFree(s->veh_half); cudaFree(s->veh_lo); cudaFree(s->veh_hi); cudaFree(s->veh_vel);
   cudaFree(s->rx_pos); cudaFree(s->rx_vel); cudaFree(s->tx_pos); cudaFree(s->tx_vel);
@@ -295,6 +311,12 @@ emrt_status emrt_scene_update_dynamic(emrt_scene s, const float *veh_pos, const 
       CK(bvh_refit_boxes(s->dyn, s->veh_lo, s->veh_hi, st));
   }
   CK(bvh_build_points(s->rxb, s->rx_pos, n_rx, s->bbox, s->hist, st));
+  // vehicles and receivers in one tree for discovery's per-segment query
+  const uint32_t nm = s->V + n_rx;
+  emrt::note_launch(), k_mix_prims<<<ceil_div(nm, 256), 256, 0, st>>>(s->veh_lo, s->veh_hi, s->V,
+                                                                     s->rx_pos, n_rx, s->mix_lo,
+                                                                     s->mix_hi);
+  CK(bvh_build_boxes(s->mix, s->mix_lo, s->mix_hi, nm, s->bbox, s->hist, st));
   s->n_updates++;
   s->updated = true;
   CK(cudaGetLastError());
@@ -561,6 +583,7 @@ emrt_status emrt_trace_backward(emrt_scene s, const emrt_trace_params *p, const 
   }
   CK(bvh_build_points(s->txb, s->tx_pos, s->n_tx, s->bbox, s->hist, st));
   gb.rxb = s->txb.view();
+  gb.mix = BVHView{};  // backward: the transmitters take the receivers' place
   gb.n_tx = n_src;
   gb.n_rx = s->n_tx;
   return run_trace(s, p, count, gb, n_src, jbits, true, rx_ids, out, st);

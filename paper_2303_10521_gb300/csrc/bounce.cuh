@@ -52,6 +52,47 @@ __device__ inline float escape_t(float3 o, float3 d, float3 rlo, float3 rhi) {
          fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
 }
 
+constexpr int kRxBuf = 4;  // receivers buffered per segment by the merged query
+
+// Vehicle boxes and reception spheres of one segment after its static
+// closest hit (tbest, face): one traversal of the merged vehicle + receiver
+// tree when the scene has one (collected receivers are tested exactly with
+// the final segment end; more than kRxBuf falls back to the receiver tree),
+// the two separate queries otherwise.  Same hits and detections either way.
+// Updates tbest/face; returns whether the segment hit something.
+template <typename F>
+__device__ inline bool veh_and_rx(const GeomView &g, const RayQ &q, float3 o, float3 d,
+                                  float3 rlo, float3 rhi, float Lacc, float kappa, uint32_t exv,
+                                  float &tbest, uint32_t &face, int *stk, float *stt,
+                                  TravStats &st, F &&emit) {
+  const uint32_t NO = EMRT_NO_FACE;
+  if (g.mix.n_prims) {
+    const float tq = fmaxf(face != NO ? tbest : escape_t(o, d, rlo, rhi), 0.f);
+    const float rq = kappa * (Lacc + tq) * 1.0001f + 1e-6f;
+    uint32_t rxb[kRxBuf];
+    int nrx = 0;
+    bool over = false;
+    trace_veh_rx<kRxBuf>(g.mix, q, tbest, face, g.n_static_faces, g.n_veh, exv, tq, rq, rxb, nrx,
+                         over, stk, stt, st);
+    const bool hit = face != NO;
+    const float t_end = fmaxf(hit ? tbest : escape_t(o, d, rlo, rhi), 0.f);
+    if (over) {
+      const float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
+      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, emit);
+    } else {
+      for (int k = 0; k < nrx; k++)
+        if (rx_hit(g.rx_pos[rxb[k]], q, t_end, Lacc, kappa)) emit(rxb[k]);
+    }
+    return hit;
+  }
+  trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
+  const bool hit = face != NO;
+  const float t_end = fmaxf(hit ? tbest : escape_t(o, d, rlo, rhi), 0.f);
+  const float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
+  query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, emit);
+  return hit;
+}
+
 // true when the first b reflections of a chain were all on static faces
 __device__ inline bool static_chain(const uint32_t *fc, uint32_t b, uint32_t fs) {
   bool ok = true;
@@ -161,14 +202,10 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
         if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
       }
       uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
-      trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
-      bool hit = face != NO;
-      float t_end = hit ? tbest : escape_t(o, d, rlo, rhi);
-      t_end = fmaxf(t_end, 0.f);
-      float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
       const uint32_t b = (uint32_t)L.b;
       const uint32_t w0 = BATCH ? (sc << 8 | tx) : tx;
-      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, [&](uint32_t rx) {
+      const bool hit = veh_and_rx(g, q, o, d, rlo, rhi, Lacc, kappa, exv, tbest, face, stk, stt, st,
+                                  [&](uint32_t rx) {
         uint32_t slot = warp_append(L.n_cand);
         if (slot < L.cand_cap) {
           const uint32_t jj = TABLE ? __float_as_uint(L.dirs[j].w) : j;
@@ -258,13 +295,9 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
       RayQ q;
       ray_setup(q, o, d);
       // the face just left is static, so no vehicle is excluded
-      trace_boxes<false>(L.g.dyn, q, 0.f, tbest, face, fs, NO, NO, stk, stt, st);
-      const bool hit = face != NO;
-      float t_end = hit ? tbest : escape_t(o, d, rlo, rhi);
-      t_end = fmaxf(t_end, 0.f);
-      const float rmax = L.kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
       const uint32_t bb = (uint32_t)b;
-      query_rx(L.g.rxb, q, t_end, Lacc, L.kappa, rmax, stk, stt, st, [&](uint32_t rx) {
+      const bool hit = veh_and_rx(L.g, q, o, d, rlo, rhi, Lacc, L.kappa, NO, tbest, face, stk, stt,
+                                  st, [&](uint32_t rx) {
         uint32_t slot = warp_append(L.n_cand);
         if (slot < L.cand_cap) {
           uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);

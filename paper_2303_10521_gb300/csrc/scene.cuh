@@ -16,6 +16,8 @@ struct emrt_scene_s {
   float4 *bbox = nullptr;  // [4]: lo, hi, scratch
   BVHBuf stat, dyn, rxb;
   BVHBuf txb;                     // transmitter points (backward tracing)
+  BVHBuf mix;                     // vehicles + receivers (merged per-frame tree)
+  float4 *mix_lo = nullptr, *mix_hi = nullptr;  // its primitive corners
   float4 *src_pos = nullptr;      // receiver points shot from (backward tracing)
   uint64_t src_cap = 0;
   float4 *veh_half = nullptr, *veh_lo = nullptr, *veh_hi = nullptr, *veh_vel = nullptr;
@@ -75,6 +77,7 @@ inline GeomView geom(const emrt_scene_s *s) {
   g.stat = s->stat.view();
   g.dyn = s->dyn.view();
   g.rxb = s->rxb.view();
+  g.mix = s->mix.view();
   g.face_plane = s->face_plane;
   g.face_info = s->face_info;
   g.face_vert = s->face_vert;

@@ -60,6 +60,22 @@ __device__ inline bool slab(const RayQ &r, float lx, float hx, float ly, float h
   return tn <= tf * 1.00000024f;
 }
 
+// Slab test of one child box with separate origin terms for the low and high
+// planes (t = p idir - ol for the low planes, p idir - oh for the high ones)
+// and tmin = 0.  ol = oh = o idir is slab() exactly; ol = (o + e) idir and
+// oh = (o - e) idir test the box grown by e on every side.
+__device__ inline bool slab_lh(const float3 &idir, const float3 &ol, const float3 &oh, float lx,
+                               float hx, float ly, float hy, float lz, float hz, float tmax,
+                               float &tnear) {
+  float t0x = fmaf(lx, idir.x, -ol.x), t1x = fmaf(hx, idir.x, -oh.x);
+  float t0y = fmaf(ly, idir.y, -ol.y), t1y = fmaf(hy, idir.y, -oh.y);
+  float t0z = fmaf(lz, idir.z, -ol.z), t1z = fmaf(hz, idir.z, -oh.z);
+  float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
+  float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+  tnear = tn;
+  return tn <= tf * 1.00000024f;
+}
+
 // Watertight ray/triangle test; on a hit with tmin < t < tmax returns t.
 __device__ inline bool tri_hit(const RayQ &r, float3 v0, float3 v1, float3 v2, float tmin,
                                float tmax, float &t) {
@@ -254,6 +270,29 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
   }
 }
 
+// One vehicle-box leaf: entry hit with t in (tmin, tmax) unless the box is
+// excluded (vehicle exv0 or exv1); face = fs + 6 v + entry face.  Returns
+// true when tmax/face changed.
+__device__ inline bool leaf_box(const BVHView &b, uint32_t g, const RayQ &r, float tmin,
+                                float &tmax, uint32_t &face, uint32_t fs, uint32_t exv0,
+                                uint32_t exv1) {
+  float4 lo = ldg4(b.prims + 2ull * g), hi = ldg4(b.prims + 2ull * g + 1);
+  uint32_t v = __float_as_uint(lo.w);
+  if (v == exv0 || v == exv1) return false;
+  float tx0 = (lo.x - r.o.x) * r.idir.x, tx1 = (hi.x - r.o.x) * r.idir.x;
+  float ty0 = (lo.y - r.o.y) * r.idir.y, ty1 = (hi.y - r.o.y) * r.idir.y;
+  float tz0 = (lo.z - r.o.z) * r.idir.z, tz1 = (hi.z - r.o.z) * r.idir.z;
+  float nx = fminf(tx0, tx1), ny = fminf(ty0, ty1), nz = fminf(tz0, tz1);
+  float tn = fmaxf(nx, fmaxf(ny, nz));
+  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+  if (!(tn <= tf && tn > tmin && tn < tmax)) return false;
+  int axis = (tn == nx) ? 0 : ((tn == ny) ? 1 : 2);
+  float dax = axis == 0 ? r.d.x : (axis == 1 ? r.d.y : r.d.z);
+  tmax = tn;
+  face = fs + 6u * v + 2u * axis + (dax > 0.f ? 0u : 1u);
+  return true;
+}
+
 // Vehicle boxes: closest (or any) entry hit with t in (tmin, tmax).  Box v is
 // skipped when exv0 or exv1 equals v.  face = F_s + 6 v + entry face.
 template <bool ANY>
@@ -287,25 +326,10 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
       if (h0) { node = c0; continue; }
       if (h1) { node = c1; continue; }
     } else {
-      uint32_t g = (uint32_t)(~node);
-      float4 lo = ldg4(b.prims + 2ull * g), hi = ldg4(b.prims + 2ull * g + 1);
       st.boxes++;
-      uint32_t v = __float_as_uint(lo.w);
-      if (v != exv0 && v != exv1) {
-        float tx0 = (lo.x - r.o.x) * r.idir.x, tx1 = (hi.x - r.o.x) * r.idir.x;
-        float ty0 = (lo.y - r.o.y) * r.idir.y, ty1 = (hi.y - r.o.y) * r.idir.y;
-        float tz0 = (lo.z - r.o.z) * r.idir.z, tz1 = (hi.z - r.o.z) * r.idir.z;
-        float nx = fminf(tx0, tx1), ny = fminf(ty0, ty1), nz = fminf(tz0, tz1);
-        float tn = fmaxf(nx, fmaxf(ny, nz));
-        float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
-        if (tn <= tf && tn > tmin && tn < tmax) {
-          int axis = (tn == nx) ? 0 : ((tn == ny) ? 1 : 2);
-          float dax = axis == 0 ? r.d.x : (axis == 1 ? r.d.y : r.d.z);
-          tmax = tn;
-          face = fs + 6u * v + 2u * axis + (dax > 0.f ? 0u : 1u);
-          hit = true;
-          if (ANY) return true;
-        }
+      if (leaf_box(b, (uint32_t)(~node), r, tmin, tmax, face, fs, exv0, exv1)) {
+        hit = true;
+        if (ANY) return true;
       }
     }
     for (;;) {
@@ -314,6 +338,88 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
       if (stt[sp] <= tmax) break;
     }
     node = stk[sp];
+  }
+}
+
+// Exact reception-sphere test of receiver position p against the segment
+// o + s d, s in [0, t_end], unfolded length L at o.
+__device__ inline bool rx_hit(float4 p, const RayQ &r, float t_end, float L, float kappa) {
+  float3 w = f3(p) - r.o;
+  float s = fminf(fmaxf(dot3(w, r.d), 0.f), t_end);
+  float3 q = w - r.d * s;
+  float rad = kappa * (L + s);
+  return dot3(q, q) <= rad * rad;
+}
+
+// Vehicle boxes and receivers in one traversal of the merged per-frame tree
+// (prims 0..n_veh-1 are vehicle boxes, the others receiver points, stored as
+// empty boxes with their receiver index + n_veh in lo.w).  Vehicles: closest
+// entry hit with t in (0, tmax), exactly as trace_boxes<false> (vehicle exv
+// skipped; tmax and face updated).  Receivers: collected into rx_buf (at most
+// RXB; more sets rx_over) when their box grown by rmax is entered within tq,
+// the bound of the segment end known before the call (the static hit or the
+// escape distance), which shrinks with every vehicle hit; rmax must bound
+// the reception radius at tq.  The caller tests the collected receivers
+// exactly (rx_hit) with the final segment end.  Boxes are grown by rmax for
+// the vehicles too, which only widens their pruning.
+template <int RXB>
+__device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax, uint32_t &face,
+                                    uint32_t fs, uint32_t n_veh, uint32_t exv, float tq,
+                                    float rmax, uint32_t *rx_buf, int &n_rx, bool &rx_over,
+                                    int *stk, float *stt, TravStats &st) {
+  if (b.n_prims == 0) return;
+  const float3 ol = make_float3(r.ood.x + rmax * r.idir.x, r.ood.y + rmax * r.idir.y,
+                                r.ood.z + rmax * r.idir.z);
+  const float3 oh = make_float3(r.ood.x - rmax * r.idir.x, r.ood.y - rmax * r.idir.y,
+                                r.ood.z - rmax * r.idir.z);
+  int sp = 0;
+  int node = b.root;
+  float tcur = 0.f;  // entry distance of the node being visited
+  uint32_t iter = 0;
+  for (;;) {
+    if (++iter > kMaxIter) {
+      st.overflow = true;
+      return;
+    }
+    if (node >= 0) {
+      const float4 *np = b.nodes + 4ll * node;
+      float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+      st.dnodes++;
+      float tn0, tn1;
+      bool h0 = slab_lh(r.idir, ol, oh, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax, tn0);
+      bool h1 = slab_lh(r.idir, ol, oh, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        int nearc = c0, farc = c1;
+        float tnear = tn0, tfar = tn1;
+        if (tn1 < tn0) { nearc = c1; farc = c0; tnear = tn1; tfar = tn0; }
+        if (sp < kStack) { stk[sp] = farc; stt[sp] = tfar; sp++; }
+        else st.overflow = true;
+        node = nearc;
+        tcur = tnear;
+        continue;
+      }
+      if (h0) { node = c0; tcur = tn0; continue; }
+      if (h1) { node = c1; tcur = tn1; continue; }
+    } else {
+      const uint32_t gi = (uint32_t)(~node);
+      const uint32_t s = __float_as_uint(ldg4(b.prims + 2ull * gi).w);
+      if (s < n_veh) {
+        st.boxes++;
+        if (leaf_box(b, gi, r, 0.f, tmax, face, fs, exv, EMRT_NO_FACE)) tq = fminf(tq, tmax);
+      } else if (tcur <= tq) {
+        st.rxs++;
+        if (n_rx < RXB) rx_buf[n_rx++] = s - n_veh;
+        else rx_over = true;
+      }
+    }
+    for (;;) {
+      if (sp == 0) return;
+      sp--;
+      if (stt[sp] <= tmax) break;
+    }
+    node = stk[sp];
+    tcur = stt[sp];
   }
 }
 
@@ -355,11 +461,7 @@ __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, fl
     } else {
       float4 p = ldg4(b.prims + (uint32_t)(~node));
       st.rxs++;
-      float3 w = f3(p) - r.o;
-      float s = fminf(fmaxf(dot3(w, r.d), 0.f), t_end);
-      float3 q = w - r.d * s;
-      float rad = kappa * (L + s);
-      if (dot3(q, q) <= rad * rad) emit(__float_as_uint(p.w));
+      if (rx_hit(p, r, t_end, L, kappa)) emit(__float_as_uint(p.w));
     }
     if (sp == 0) return;
     node = stk[--sp];
