@@ -333,8 +333,9 @@ typedef struct {
   uint32_t pad2;
   uint64_t static_reused;     /* segments whose static closest hit came from
                                  the static-hit cache (EMRT_TRACE_STATIC_CACHE) */
-  uint64_t deferred;          /* chain segments handed from the cache walker
-                                 to the per-bounce traversal                  */
+  uint64_t deferred;          /* chains the cache walker could not finish
+                                 from the cache (carried to their ends with
+                                 the full static traversal)                  */
 } emrt_stats;
 
 /* Waits for the stream, reads and clears the device error word, returns the

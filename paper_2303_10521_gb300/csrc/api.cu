@@ -274,7 +274,7 @@ void emrt_scene_destroy(emrt_scene s) {
     cudaFree(t.tx_ref);
     cudaFree(t.tx_epoch);
   }
-  for (auto &r : s->defer) cudaFree(r);
+  cudaFree(s->chain_q);
   cudaFree(s->dt_scratch);
   cudaFree(s->rays[0]); cudaFree(s->rays[1]);
   for (int k = 0; k < 2; k++) { cudaFree(s->rkeys[k]); cudaFree(s->rvals[k]); }
@@ -372,7 +372,10 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   }
   tab->last_use = ++s->dt_clock;
   uint64_t nrays = count * n_src;
-  if (p->max_depth > 0 && nrays > s->ray_cap) {
+  // the static-hit cache form runs in the chain walker alone: no per-bounce
+  // ray buffers or sorts
+  const bool cache = (p->flags & EMRT_TRACE_STATIC_CACHE) && !backward;
+  if (!cache && p->max_depth > 0 && nrays > s->ray_cap) {
     cudaFree(s->rays[0]);
     cudaFree(s->rays[1]);
     s->rays[0] = s->rays[1] = nullptr;
@@ -381,7 +384,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     CK(cudaMalloc(&s->rays[1], sizeof(Ray) * nrays));
     s->ray_cap = nrays;
   }
-  bool sort_rays = (p->flags & EMRT_TRACE_SORT_RAYS) && p->max_depth > 0;
+  bool sort_rays = (p->flags & EMRT_TRACE_SORT_RAYS) && p->max_depth > 0 && !cache;
   if (sort_rays && nrays > s->rsort_cap) {
     for (int k = 0; k < 2; k++) {
       cudaFree(s->rkeys[k]);
@@ -396,7 +399,6 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     }
     s->rsort_cap = nrays;
   }
-  const bool cache = (p->flags & EMRT_TRACE_STATIC_CACHE) && !backward;
   if (cache) {
     const uint32_t depth = p->max_depth + 1;
     if (tab->stab_slots != nrays || tab->stab_depth < depth || !tab->stab) {
@@ -418,15 +420,8 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
       tab->stab_slots = nrays;
       tab->stab_depth = depth;
     }
-    if (nrays > s->defer_cap) {
-      for (auto &r : s->defer) {
-        cudaFree(r);
-        r = nullptr;
-      }
-      s->defer_cap = 0;
-      for (uint32_t b = 0; b <= EMRT_MAX_DEPTH; b++)
-        CK(cudaMalloc(&s->defer[b], sizeof(Ray) * nrays));
-      s->defer_cap = nrays;
+    if (!s->chain_q) {
+      CK(cudaMalloc(&s->chain_q, sizeof(Ray) * chain_queue_entries()));
     }
   }
   uint64_t want = std::max<uint64_t>(s->want_cand,
@@ -444,7 +439,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   uint32_t nev = 0;  // traversal launches timed
   if (cache) {
     // static-hit cache: epochs of the transmitter positions, then the chain
-    // walker; what it cannot finish continues in the per-bounce traversal
+    // walker, which also carries the chains it defers to their ends
     launch_tx_epoch(s->tx_pos, tab->tx_ref, tab->tx_epoch, s->n_tx, st);
     BounceLaunch L{};
     L.g = gt;
@@ -462,24 +457,21 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.stab = tab->stab;
     L.tx_epoch = tab->tx_epoch;
     L.n_slots = (uint32_t)nrays;
-    ChainBufs D;
-    for (int b = 0; b <= EMRT_MAX_DEPTH; b++) D.rays[b] = s->defer[b];
+    ChainBufs D{s->chain_q};
     cudaEventRecord(s->evb[0], st);
     launch_chain(L, D, chain_grid(), st);
     cudaEventRecord(s->evb[1], st);
     nev = 1;
   }
   int key_buf = 0;  // sort buffer that receives the next bounce's keys
-  for (uint32_t b = 0; b <= p->max_depth; b++) {
+  for (uint32_t b = 0; !cache && b <= p->max_depth; b++) {
     BounceLaunch L{};
     L.g = gt;
-    L.rin = cache ? s->defer[b] : (b ? s->rays[(b - 1) & 1] : nullptr);
+    L.rin = b ? s->rays[(b - 1) & 1] : nullptr;
     L.order = nullptr;
     // reorder reflected rays for coherent traversal (keys written by the
-    // previous bounce into key_buf); the few segments the cache walker
-    // defers are not worth the sort's fixed cost (measured)
-    const bool sort_here = b > 0 && sort_rays && !cache;
-    if (sort_here) {
+    // previous bounce into key_buf)
+    if (b > 0 && sort_rays) {
       const int o = key_buf, q = 1 - key_buf;
       bool alt = radix_sort<1>(&c->n_ray[b], s->rkeys[o], s->rvals[o], s->rkeys[q], s->rvals[q],
                                24, s->hist, st, nrays);
@@ -491,7 +483,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.n_primary = (uint32_t)nrays;
     L.dirs = tab->dirs;
     L.count = (uint32_t)count;
-    L.rout = cache ? (b < p->max_depth ? s->defer[b + 1] : nullptr) : s->rays[b & 1];
+    L.rout = s->rays[b & 1];
     L.n_out = &c->n_ray[b + 1];
     L.cand = s->cand;
     L.cand_cap = s->cand_cap;
@@ -502,15 +494,10 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.b = (int)b;
     L.K = (int)p->max_depth;
     L.jbits = jbits;
-    if (sort_rays && !cache && b < p->max_depth) {
+    if (sort_rays && b < p->max_depth) {
       L.okeys = s->rkeys[key_buf];
       L.ovals = s->rvals[key_buf];
       L.bbox = s->bbox;
-    }
-    if (cache) {
-      L.stab = tab->stab;
-      L.tx_epoch = tab->tx_epoch;
-      L.n_slots = (uint32_t)nrays;
     }
     cudaEventRecord(s->evb[2 * nev], st);
     launch_bounce(L, grid, st, (p->flags & EMRT_TRACE_WIDE_BVH) != 0);

@@ -1,5 +1,6 @@
-// Closest-hit traversal kernels of one discovery bounce (k_bounce) and the
-// static-hit cache walker (k_chain), with their device helpers.  Included by
+// Closest-hit traversal kernels of one discovery bounce (k_bounce), the
+// static-hit cache walker (k_chain) and the continuation of the chains it
+// defers (k_continue), with their device helpers.  Included by
 // trace.cu only, inside its anonymous namespace.
 #pragma once
 
@@ -93,33 +94,21 @@ __device__ inline bool veh_and_rx(const GeomView &g, const RayQ &q, float3 o, fl
   return hit;
 }
 
-// true when the first b reflections of a chain were all on static faces
-__device__ inline bool static_chain(const uint32_t *fc, uint32_t b, uint32_t fs) {
-  bool ok = true;
-#pragma unroll
-  for (uint32_t k = 0; k < EMRT_MAX_DEPTH; k++)
-    if (k < b && fc[k] >= fs) ok = false;
-  return ok;
-}
-
 // Closest-hit traversal of one bounce for every ray (persistent threads: each
 // warp takes FETCH rays at a time from a global cursor).  BATCH: rays of many
 // scenes, each ray's scene read from the table; otherwise the single scene in
 // L.g.  Per ray: nearest hit over the static triangles and the vehicle
 // boxes, reception-sphere detections on the traced segment (appended as
 // candidates), and the specular continuation (appended to the next buffer).
-// TABLE: static-hit cache form (single scene): the static hit of a segment
-// whose chain is still static comes from L.stab when its entry is current,
-// and is stored there otherwise.
-template <bool BATCH, int BLOCK, int FETCH, bool WIDE, bool TABLE = false>
+template <bool BATCH, int BLOCK, int FETCH, bool WIDE>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
                                                   uint32_t n_scenes) {
   int stk[kStack];
   float stt[kStack];
   TravStats st;
-  uint32_t segs = 0, reused = 0;
+  uint32_t segs = 0;
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t n_items = (L.b == 0 && !TABLE) ? L.n_primary : *L.n_in;
+  const uint32_t n_items = L.b == 0 ? L.n_primary : *L.n_in;
   float3 rlo, rhi;
   if (!BATCH) rx_bounds(L.g.rxb, rlo, rhi);
   const uint32_t NO = EMRT_NO_FACE;
@@ -136,7 +125,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
       float Lacc;
       uint32_t tx, j, sc = 0;
       uint32_t fc[EMRT_MAX_DEPTH] = {NO, NO, NO, NO};
-      if (L.b == 0 && !TABLE) {
+      if (L.b == 0) {
         uint32_t local = i, count = L.count;
         const float4 *dirs = L.dirs;
         if (BATCH) {  // scene of a primary item: last scene whose range starts <= i
@@ -170,7 +159,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
           j = id & 0x3fffffu;
         } else {
           tx = id >> L.jbits;
-          j = id & ((1u << L.jbits) - 1u);  // TABLE: direction-table position
+          j = id & ((1u << L.jbits) - 1u);
         }
         fc[0] = R.faces.x; fc[1] = R.faces.y; fc[2] = R.faces.z; fc[3] = R.faces.w;
       }
@@ -183,24 +172,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
       ray_setup(q, o, d);
       float tbest = FLT_MAX;
       uint32_t face = NO;
-      bool have = false;
-      uint32_t slot = 0, ep = 0;
-      const bool keep = TABLE && static_chain(fc, (uint32_t)L.b, g.n_static_faces);
-      if (keep) {
-        slot = (uint32_t)L.b * L.n_slots + tx * L.count + j;
-        ep = L.tx_epoch[tx];
-        const uint4 e = L.stab[slot];
-        if (e.z == ep) {
-          tbest = __uint_as_float(e.x);
-          face = e.y;
-          have = true;
-          reused++;
-        }
-      }
-      if (!have) {
-        trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
-        if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
-      }
+      trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
       uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
       const uint32_t b = (uint32_t)L.b;
       const uint32_t w0 = BATCH ? (sc << 8 | tx) : tx;
@@ -208,10 +180,9 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
                                   [&](uint32_t rx) {
         uint32_t slot = warp_append(L.n_cand);
         if (slot < L.cand_cap) {
-          const uint32_t jj = TABLE ? __float_as_uint(L.dirs[j].w) : j;
           uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
           c[0] = make_uint4(w0, rx, b, fc[0]);
-          c[1] = make_uint4(fc[1], fc[2], fc[3], jj);
+          c[1] = make_uint4(fc[1], fc[2], fc[3], j);
         }
       });
       if (hit && L.b < K) {
@@ -240,18 +211,91 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
   add_u64(&L.ctr->box_tests, st.boxes);
   add_u64(&L.ctr->rx_node_visits, st.rnodes);
   add_u64(&L.ctr->rx_tests, st.rxs);
-  if (TABLE) add_u64(&L.ctr->static_reused, reused);
   if (st.overflow) atomicOr(&L.ctr->err, ERR_STACK);
 }
 
-// Chain walker of the static-hit cache: one thread follows the whole specular
-// chain of a primary ray (tx, direction-table position k) as long as its
-// segments have current cache entries and its reflections stay on static
-// faces: static hit from the cache, vehicle boxes and reception spheres of
-// this frame, reflection.  The first segment it cannot finish that way (no
-// current entry, or the chain reflected off a vehicle) goes to D.rays[b] for
-// the per-bounce traversal, which continues the chain.  Segments, candidates
-// and continuations are exactly those of k_bounce.
+// One chain from its first unfinished segment to its end: static hit from
+// the cache while the chain is still static and its entry is current, the
+// full static traversal otherwise (stored when the chain is static); vehicle
+// boxes and reception spheres of this frame; reflection.  The segment index
+// b of the chain's first segment is the number of faces already met.
+// Segments, candidates and cache entries are exactly those of k_bounce.
+__device__ __forceinline__ void carry_chain(const BounceLaunch &L, const Ray &R, float3 rlo,
+                                            float3 rhi, int *stk, float *stt, TravStats &st,
+                                            uint32_t (&segs)[EMRT_MAX_DEPTH + 1],
+                                            uint32_t &reused) {
+  const uint32_t fs = L.g.n_static_faces;
+  const uint32_t NO = EMRT_NO_FACE;
+  float3 o = f3(R.o_L), d = f3(R.d_id);
+  float Lacc = R.o_L.w;
+  const uint32_t id = __float_as_uint(R.d_id.w);
+  const uint32_t tx = id >> L.jbits, pos = id & ((1u << L.jbits) - 1u);
+  uint32_t f0 = R.faces.x, f1 = R.faces.y, f2 = R.faces.z, f3_ = R.faces.w;
+  uint32_t b = (f0 != NO) + (f1 != NO) + (f2 != NO) + (f3_ != NO);
+  for (;;) {
+    const uint32_t prev = b == 0 ? NO : b == 1 ? f0 : b == 2 ? f1 : b == 3 ? f2 : f3_;
+    RayQ q;
+    ray_setup(q, o, d);
+    float tbest = FLT_MAX;
+    uint32_t face = NO;
+    bool have = false;
+    uint32_t slot = 0, ep = 0;
+    const bool keep = (b < 1 || f0 < fs) && (b < 2 || f1 < fs) && (b < 3 || f2 < fs) &&
+                      (b < 4 || f3_ < fs);
+    if (keep) {
+      slot = b * L.n_slots + tx * L.count + pos;
+      ep = L.tx_epoch[tx];
+      const uint4 e = L.stab[slot];
+      if (e.z == ep) {
+        tbest = __uint_as_float(e.x);
+        face = e.y;
+        have = true;
+        reused++;
+      }
+    }
+    if (!have) {
+      trace_tris<false, false>(L.g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+      if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
+    }
+    const uint32_t exv = (prev != NO && prev >= fs) ? (prev - fs) / 6u : NO;
+    const uint32_t bb = b;
+    const bool hit = veh_and_rx(L.g, q, o, d, rlo, rhi, Lacc, L.kappa, exv, tbest, face, stk, stt,
+                                st, [&](uint32_t rx) {
+      uint32_t s = warp_append(L.n_cand);
+      if (s < L.cand_cap) {
+        uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * s);
+        c[0] = make_uint4(tx, rx, bb, f0);
+        c[1] = make_uint4(f1, f2, f3_, __float_as_uint(L.dirs[pos].w));
+      }
+    });
+#pragma unroll
+    for (uint32_t k = 0; k <= EMRT_MAX_DEPTH; k++)
+      if (k == b) segs[k]++;
+    if (!hit || (int)b >= L.K) break;
+    float3 p, r;
+    reflect_step(L.g, face, o, d, tbest, p, r);
+    f0 = b == 0 ? face : f0;
+    f1 = b == 1 ? face : f1;
+    f2 = b == 2 ? face : f2;
+    f3_ = b == 3 ? face : f3_;
+    Lacc = Lacc + tbest;
+    o = p;
+    d = r;
+    b++;
+  }
+}
+
+// Chain walker of the static-hit cache.  Walk tasks: one thread follows the
+// whole specular chain of a primary ray (tx, direction-table position k) as
+// long as its segments have current cache entries and its reflections stay on
+// static faces: static hit from the cache, vehicle boxes and reception
+// spheres of this frame, reflection.  A chain it cannot finish that way (no
+// current entry, or a reflection off a vehicle) goes to the warp's own queue
+// (kChainQueue entries of D.q, written and read by this warp alone); as soon
+// as it holds 32 chains the warp carries them to their ends together
+// (carry_chain), so that the costly deferred segments run while the walk
+// still fills the GPU, 32 to a warp, rather than in a sparse launch of their
+// own.  The queue's last chains are carried when the walk is handed out.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, ChainBufs D) {
   int stk[kStack];
@@ -263,6 +307,8 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
   const uint32_t n_items = L.n_primary;
   const uint32_t fs = L.g.n_static_faces;
   const uint32_t NO = EMRT_NO_FACE;
+  Ray *wq = D.q + (size_t)(blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5)) * kChainQueue;
+  uint32_t qn = 0;  // chains in the warp's queue (warp-uniform)
   float3 rlo, rhi;
   rx_bounds(L.g.rxb, rlo, rhi);
   for (;;) {
@@ -271,67 +317,81 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_items) break;
     const uint32_t i = base + lane;
-    if (i >= n_items) continue;
-    const uint32_t tx = i / L.count;
-    const uint32_t k = i - tx * L.count;
-    const float4 dj = L.dirs[k];
-    const uint32_t j = __float_as_uint(dj.w);
-    const uint32_t ep = L.tx_epoch[tx];
-    const uint32_t id = tx << L.jbits | k;
-    float3 o = f3(L.g.tx_pos[tx]), d = f3(dj);
+    bool defer = false;
+    float3 o, d;
     float Lacc = 0.f;
-    uint32_t f0 = NO, f1 = NO, f2 = NO, f3_ = NO;
-    int defer_b = -1;
-    for (int b = 0; b <= L.K; b++) {
-      const uint4 e = L.stab[(uint32_t)b * L.n_slots + i];
-      if (e.z != ep) {
-        defer_b = b;
-        break;
-      }
-      float tbest = __uint_as_float(e.x);
-      uint32_t face = e.y;
-      reused++;
-      segs[b]++;
-      RayQ q;
-      ray_setup(q, o, d);
-      // the face just left is static, so no vehicle is excluded
-      const uint32_t bb = (uint32_t)b;
-      const bool hit = veh_and_rx(L.g, q, o, d, rlo, rhi, Lacc, L.kappa, NO, tbest, face, stk, stt,
-                                  st, [&](uint32_t rx) {
-        uint32_t slot = warp_append(L.n_cand);
-        if (slot < L.cand_cap) {
-          uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
-          c[0] = make_uint4(tx, rx, bb, f0);
-          c[1] = make_uint4(f1, f2, f3_, j);
+    uint32_t id = 0, f0 = NO, f1 = NO, f2 = NO, f3_ = NO;
+    if (i < n_items) {
+      const uint32_t tx = i / L.count;
+      const uint32_t k = i - tx * L.count;
+      const float4 dj = L.dirs[k];
+      const uint32_t j = __float_as_uint(dj.w);
+      const uint32_t ep = L.tx_epoch[tx];
+      id = tx << L.jbits | k;
+      o = f3(L.g.tx_pos[tx]);
+      d = f3(dj);
+      for (int b = 0; b <= L.K; b++) {
+        const uint4 e = L.stab[(uint32_t)b * L.n_slots + i];
+        if (e.z != ep) {
+          defer = true;
+          break;
         }
-      });
-      if (!hit || b == L.K) break;
-      float3 p, r;
-      reflect_step(L.g, face, o, d, tbest, p, r);
-      f0 = b == 0 ? face : f0;
-      f1 = b == 1 ? face : f1;
-      f2 = b == 2 ? face : f2;
-      f3_ = b == 3 ? face : f3_;
-      Lacc = Lacc + tbest;
-      o = p;
-      d = r;
-      if (face >= fs) {  // off a vehicle: the rest of the chain is not cached
-        defer_b = b + 1;
-        break;
+        float tbest = __uint_as_float(e.x);
+        uint32_t face = e.y;
+        reused++;
+        segs[b]++;
+        RayQ q;
+        ray_setup(q, o, d);
+        // the face just left is static, so no vehicle is excluded
+        const uint32_t bb = (uint32_t)b;
+        const bool hit = veh_and_rx(L.g, q, o, d, rlo, rhi, Lacc, L.kappa, NO, tbest, face, stk,
+                                    stt, st, [&](uint32_t rx) {
+          uint32_t slot = warp_append(L.n_cand);
+          if (slot < L.cand_cap) {
+            uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
+            c[0] = make_uint4(tx, rx, bb, f0);
+            c[1] = make_uint4(f1, f2, f3_, j);
+          }
+        });
+        if (!hit || b == L.K) break;
+        float3 p, r;
+        reflect_step(L.g, face, o, d, tbest, p, r);
+        f0 = b == 0 ? face : f0;
+        f1 = b == 1 ? face : f1;
+        f2 = b == 2 ? face : f2;
+        f3_ = b == 3 ? face : f3_;
+        Lacc = Lacc + tbest;
+        o = p;
+        d = r;
+        if (face >= fs) {  // off a vehicle: the rest of the chain is not cached
+          defer = true;
+          break;
+        }
       }
     }
-    if (defer_b >= 0) {
-      uint32_t slot = warp_append_keyed(L.ctr->n_ray, (uint32_t)defer_b);
-      Ray R;
-      R.o_L = make_float4(o.x, o.y, o.z, Lacc);
-      R.d_id = make_float4(d.x, d.y, d.z, __uint_as_float(id));
-      R.faces = make_uint4(f0, f1, f2, f3_);
-      D.rays[defer_b][slot] = R;
+    const uint32_t m = __ballot_sync(0xffffffffu, defer);
+    if (defer) {
+      Ray *q = wq + qn + __popc(m & lanemask_lt());
+      q->o_L = make_float4(o.x, o.y, o.z, Lacc);
+      q->d_id = make_float4(d.x, d.y, d.z, __uint_as_float(id));
+      q->faces = make_uint4(f0, f1, f2, f3_);
       deferred++;
+    }
+    qn += __popc(m);
+    if (qn >= 32u) {  // carry the queue's last 32 chains
+      __syncwarp();
+      const Ray R = wq[qn - 32u + lane];
+      __syncwarp();
+      qn -= 32u;
+      carry_chain(L, R, rlo, rhi, stk, stt, st, segs, reused);
     }
   }
   __syncwarp();
+  if (lane < qn) carry_chain(L, wq[lane], rlo, rhi, stk, stt, st, segs, reused);
+  __syncwarp();
   for (int b = 0; b <= EMRT_MAX_DEPTH; b++) add_u64(&L.ctr->segments[b], segs[b]);
+  add_u64(&L.ctr->node_visits, st.nodes);
+  add_u64(&L.ctr->tri_tests, st.tris);
   add_u64(&L.ctr->dyn_node_visits, st.dnodes);
   add_u64(&L.ctr->box_tests, st.boxes);
   add_u64(&L.ctr->rx_node_visits, st.rnodes);

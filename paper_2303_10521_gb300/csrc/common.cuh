@@ -36,7 +36,7 @@ struct Counters {
   unsigned long long rx_tests;        // receivers tested against a sphere
   unsigned long long occl_rays;
   unsigned long long static_reused;   // static hits taken from the cache
-  unsigned long long deferred;        // chain segments handed to k_bounce
+  unsigned long long deferred;        // chains the cache walker queued
 };
 
 // ---------------------------------------------------------------------------

@@ -45,9 +45,8 @@ struct emrt_scene_s {
   // ray ping-pong buffers and the coherence-sort scratch
   Ray *rays[2] = {nullptr, nullptr};
   uint64_t ray_cap = 0;
-  // per-bounce ray buffers of the static-hit cache form
-  Ray *defer[EMRT_MAX_DEPTH + 1] = {};
-  uint64_t defer_cap = 0;
+  // per-warp deferred-chain queues of the static-hit cache walker
+  Ray *chain_q = nullptr;
   KeyW<1> *rkeys[2] = {nullptr, nullptr};
   uint32_t *rvals[2] = {nullptr, nullptr};
   uint64_t rsort_cap = 0;

@@ -475,6 +475,10 @@ int chain_grid() {
   return g_chain_grid;
 }
 
+uint64_t chain_queue_entries() {
+  return (uint64_t)chain_grid() * (kBounceBlock / 32) * kChainQueue;
+}
+
 void launch_chain(const BounceLaunch &L, const ChainBufs &D, int grid, cudaStream_t s) {
   emrt::note_launch(), k_chain<kBounceBlock><<<grid, kBounceBlock, 0, s>>>(L, D);
 }
@@ -569,9 +573,7 @@ void launch_ray_keys(const Ray *r, const uint32_t *n, const float4 *bbox, KeyW<1
 }
 
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s, bool wide) {
-  if (L.stab)
-    emrt::note_launch(), k_bounce<false, kBounceBlock, 32, false, true><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);
-  else if (wide)
+  if (wide)
     emrt::note_launch(), k_bounce<false, kBounceBlock, 32, true><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);
   else
     emrt::note_launch(), k_bounce<false, kBounceBlock, 32, false><<<grid, kBounceBlock, 0, s>>>(L, nullptr, 1);

@@ -36,11 +36,10 @@ struct BounceLaunch {
   float kappa;
   int b, K;
   int jbits;             // single-scene ray ids: source << jbits | ray index j
-  // static-hit cache (single scene, forward): entry (bounce b, item i) at
+  // static-hit cache (chain walker): entry (bounce b, item i) at
   // stab[b * n_slots + i], item i = tx * count + position in the direction
-  // table; uint4 (t bits, face, epoch of the tx position, 0).  With a cache
-  // the ray ids carry the direction-table position instead of j, and bounce
-  // 0 reads its rays from rin like the others.
+  // table; uint4 (t bits, face, epoch of the tx position, 0).  The walker's
+  // ray ids carry the direction-table position instead of j.
   uint4 *stab;
   const uint32_t *tx_epoch;
   uint32_t n_slots;
@@ -50,19 +49,21 @@ struct BounceLaunch {
   uint32_t *ovals;
   const float4 *bbox;
 };
-// Chain walker of the static-hit cache: rays[b] receives the segments that
-// the per-bounce traversal must trace at bounce b (count in ctr->n_ray[b]).
+// Per-warp queues of the static-hit cache walker: warp w of the launch owns
+// q[w * kChainQueue, (w + 1) * kChainQueue); chain_queue_entries() entries in
+// all for chain_grid() blocks.
+constexpr uint32_t kChainQueue = 64;
 struct ChainBufs {
-  Ray *rays[EMRT_MAX_DEPTH + 1];
+  Ray *q;
 };
+uint64_t chain_queue_entries();
 void launch_chain(const BounceLaunch &L, const ChainBufs &D, int grid, cudaStream_t s);
 int chain_grid();
 // epoch[t] += 1 and ref[t] = pos[t] for every transmitter whose position
 // differs (bitwise) from ref[t]
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,
                      cudaStream_t s);
-// wide: traverse the static BVH's 4-wide collapse; L.stab != null: static-hit
-// cache form (binary BVH)
+// wide: traverse the static BVH's 4-wide collapse
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s, bool wide = false);
 int bounce_grid();  // persistent grid size (SMs x resident blocks)
 
