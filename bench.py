@@ -31,13 +31,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s traversal and receiver-frames/s channel update (2x2km,10k Rx), cached vs plain"
 UNIT = "receiver-frames/s"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_bounce_city_traffic.txt")
-# sources of k_bounce and of the trees it traverses (the figures of the
-# committed ncu capture hold while these are unchanged)
-KERNEL_SOURCES = ["paper_2303_10521_gb300/csrc/bounce.cuh",
-                  "paper_2303_10521_gb300/csrc/traverse.cuh",
-                  "paper_2303_10521_gb300/csrc/common.cuh",
-                  "paper_2303_10521_gb300/csrc/bvh.cu"]
+# committed ncu figures of the plain traversal kernel, per traversal form,
+# and the sources of that kernel and of the trees it traverses (the figures
+# hold while these are unchanged)
+TRAFFIC_FILE = {"depth_first": os.path.join(ROOT, "profiles", "k_walk_city_traffic.txt"),
+                "breadth_first": os.path.join(ROOT, "profiles", "k_bounce_city_traffic.txt")}
+_TREE_SOURCES = ["paper_2303_10521_gb300/csrc/traverse.cuh",
+                 "paper_2303_10521_gb300/csrc/common.cuh",
+                 "paper_2303_10521_gb300/csrc/bvh.cu"]
+KERNEL_SOURCES = {"depth_first": ["paper_2303_10521_gb300/csrc/chain.cuh",
+                                  "paper_2303_10521_gb300/csrc/bounce.cuh"] + _TREE_SOURCES,
+                  "breadth_first": ["paper_2303_10521_gb300/csrc/bounce.cuh"] + _TREE_SOURCES}
 
 
 def parse():
@@ -54,8 +58,11 @@ def parse():
                     help="cached method: per-frame rediscovery with N_rays / this (0: none)")
     ap.add_argument("--ray-stride", type=int, default=1,
                     help="trace rays offset + stride*j only (profiling captures)")
+    ap.add_argument("--breadth-first", action="store_true",
+                    help="plain frames: trace bounce by bounce (k_bounce) instead of "
+                         "depth-first chains (k_walk)")
     ap.add_argument("--no-sort-rays", action="store_true",
-                    help="do not reorder reflected rays between bounces")
+                    help="breadth-first form: do not reorder reflected rays between bounces")
     ap.add_argument("--per-rx-frames", type=int, default=30,
                     help="per-receiver schedule leg: frames (0: skip)")
     ap.add_argument("--backward-rays", type=int, default=50_000,
@@ -105,9 +112,9 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
     return units_per_rank * world / (max_ms / 1e3)
 
 
-def kernel_hash():
+def kernel_hash(form="depth_first"):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[form]:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -120,18 +127,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_summary():
-    """Figures of the committed ncu capture of k_bounce (DRAM bytes per
-    closest-hit segment, memory-hierarchy and issue counters), if it was
-    taken on the current kernel source; else None."""
-    if not os.path.exists(TRAFFIC_FILE):
+def ncu_summary(form="depth_first"):
+    """Figures of the committed ncu capture of the plain traversal kernel of
+    this form (DRAM bytes per closest-hit segment, memory-hierarchy and issue
+    counters), if it was taken on the current kernel source; else None."""
+    path = TRAFFIC_FILE[form]
+    if not os.path.exists(path):
         return None
     kv = {}
-    for line in open(TRAFFIC_FILE):
+    for line in open(path):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.pop("kernel_hash", None) != kernel_hash():
+    if kv.pop("kernel_hash", None) != kernel_hash(form):
         return None
     try:
         return {k: float(v) for k, v in kv.items()}
@@ -262,7 +270,9 @@ def arm_config(ws):
     return {"workload": "city 2x2 km, 6400 buildings (~293k triangles), 5000 vehicles, "
                         "10k Rx, 4 Tx, 1e7 rays/Tx, K=4, fields at 3.5 and 28 GHz",
             "method": "plain per-frame retrace", "parallelism": f"replicas x{ws}",
-            "l2": "inputs larger than L2 (3.8 GB ray buffers per bounce)"}
+            "l2": "inputs larger than L2: the 160 MB primary direction table is streamed "
+                  "once per Tx per frame (the breadth-first form also streams 1.9 GB ray "
+                  "buffers per bounce)"}
 
 
 def run_reference(args):
@@ -329,16 +339,18 @@ def main():
     g = engine.Scene(sc, device=dev)
     g.update(frames[0])
     rs = args.ray_stride
-    paths = g.trace(stride=rs)                     # sizes scratch buffers
+    paths = g.trace(stride=rs, breadth_first=args.breadth_first)  # sizes scratch buffers
     cap = paths.capacity
     out = engine.Paths(cap * 2, dev)
     chs = [None, None]
 
     sort_rays = not args.no_sort_rays
+    bf = args.breadth_first
+    form = "breadth_first" if bf else "depth_first"
 
     def step(k, stats):
         g.update(frames[k])
-        g.trace_async(out, stride=rs, sort_rays=sort_rays)
+        g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(out, f, out=chs[i])
         st = g.sync()
@@ -376,19 +388,23 @@ def main():
         sg = s["segments"]
         byt += 64 * (s["node_visits"] + s["dyn_node_visits"] + s["rx_node_visits"])
         byt += 48 * s["tri_tests"] + 32 * s["box_tests"] + 16 * s["rx_tests"]
-        byt += 16 * sg[0] + 48 * sum(sg[1:])          # ray reads
-        byt += (48 + 8) * sum(sg[1:])                  # reflected rays written, with key
+        if bf:
+            byt += 16 * sg[0] + 48 * sum(sg[1:])      # ray reads
+            byt += (48 + 8) * sum(sg[1:])              # reflected rays written, with key
+        else:
+            byt += 32 * sg[0]                          # Tx point + direction per chain
         byt += 32 * s["candidates"]
-    launches_trav = (K + 1) * len(stats)
+    launches_trav = ((K + 1) if bf else 1) * len(stats)
     peak, peak_kind = measured_peaks()
     achieved = (byt / launches_trav) / (trav_ms / launches_trav / 1e3) / 1e9
-    ncu = ncu_summary()
+    ncu = ncu_summary(form)
     tps = ncu.pop("dram_bytes_per_segment", None) if ncu else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": (tps * seg / launches_trav) if tps else None,
                 "ncu": ncu,
-                "kernel": "k_bounce (closest-hit traversal + reception spheres)",
+                "kernel": ("k_bounce (one bounce: closest hit + reception spheres)" if bf else
+                           "k_walk (depth-first chains: closest hit + reception spheres)"),
                 "algorithmic_bytes_per_launch": byt / launches_trav,
                 "launch_ms": trav_ms / launches_trav}
     mrays = seg / (trav_ms / 1e3) / 1e6
@@ -417,7 +433,7 @@ def main():
     torch.cuda.synchronize()
     sc_ms = max_over_ranks(e6.elapsed_time(e7), dev)
     rec_c = out.records()
-    g.trace_async(out, stride=rs, sort_rays=sort_rays)      # plain, same last frame
+    g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf)  # plain, same last frame
     g.sync()
     static_cache = {
         "receiver_frames_per_s": job_throughput(n_rx * args.steps, ws, sc_ms),
@@ -465,7 +481,7 @@ def main():
     for k in range(args.steps):
         d = F({f: t.to(dev, non_blocking=True) for f, t in pinned[k].items()})
         g.update(d)
-        g.trace_async(out, sort_rays=sort_rays)
+        g.trace_async(out, sort_rays=sort_rays, breadth_first=bf)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(out, f, out=chs[i])
             rx_host[i].copy_(chs[i].rx, non_blocking=True)
@@ -490,9 +506,9 @@ def main():
     fresh = engine.Paths(cap * 2, dev)
     for k in (nc - 2, nc - 1):  # untimed warm-up of the cached pipeline (sizes scratch)
         g.update(cframes[k])
-        g.trace_async(cache, sort_rays=sort_rays, static_cache=use_sc)
+        g.trace_async(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
         g.revalidate(cache)
-        g.trace_async(fresh, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays,
+        g.trace_async(fresh, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays, breadth_first=bf,
                       static_cache=use_sc)
         g.merge(cache, fresh)
         for i, f in enumerate(sc.freqs):
@@ -500,7 +516,7 @@ def main():
         chs[0].rx[:, 0].clone()  # the accuracy record below; loads its copy kernel
         g.sync()
     g.update(cframes[0])
-    g.trace_async(cache, sort_rays=sort_rays, static_cache=use_sc)
+    g.trace_async(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
     g.sync()
     cached_rx = []
     torch.cuda.synchronize()
@@ -512,10 +528,10 @@ def main():
         g.update(cframes[k])
         g.revalidate(cache)
         if REFRESH and k % REFRESH == 0:
-            g.trace_async(fresh, sort_rays=sort_rays, static_cache=use_sc)
+            g.trace_async(fresh, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
             g.merge(cache, fresh)
         elif R_LOW:
-            g.trace_async(fresh, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays,
+            g.trace_async(fresh, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays, breadth_first=bf,
                           static_cache=use_sc)
             g.merge(cache, fresh)
         for i, f in enumerate(sc.freqs):
@@ -541,9 +557,9 @@ def main():
     plain_ref = {}
     for k in range(4, nc, 8):  # plain references, untimed
         g.update(cframes[k])
-        g.trace_async(fresh, sort_rays=sort_rays)
+        g.trace_async(fresh, sort_rays=sort_rays, breadth_first=bf)
         pp = g.channel(fresh, sc.freqs[0]).rx[:, 0].cpu().numpy()
-        g.trace_async(fresh, n_rays=int(sc.n_rays * 0.9), sort_rays=sort_rays)
+        g.trace_async(fresh, n_rays=int(sc.n_rays * 0.9), sort_rays=sort_rays, breadth_first=bf)
         pq = g.channel(fresh, sc.freqs[0]).rx[:, 0].cpu().numpy()
         g.sync()
         plain_ref[k] = pp
@@ -565,10 +581,10 @@ def main():
         fresh2 = engine.Paths(cap * 2, dev)
         warm_ids = torch.arange(min(n_rx, 2000), dtype=torch.int32, device=dev)
         g.update(cframes[0])                  # untimed: sizes backward scratch
-        g.trace_backward_async(fresh2, warm_ids, n_rays=NB, sort_rays=sort_rays)
+        g.trace_backward_async(fresh2, warm_ids, n_rays=NB, sort_rays=sort_rays, breadth_first=bf)
         g.merge(cache2, fresh2)
         g.sync()
-        g.trace_async(cache2, sort_rays=sort_rays, static_cache=use_sc)  # frame 0: full
+        g.trace_async(cache2, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)  # frame 0: full
         g.refresh_schedule(sched)
         g.sync()
         tc = g.coherence_time(sc.freqs[0]).min(dim=0).values
@@ -584,7 +600,7 @@ def main():
             ids = sched.due()
             n_due.append(len(ids))
             if len(ids):
-                g.trace_backward_async(fresh2, ids, n_rays=NB, sort_rays=sort_rays)
+                g.trace_backward_async(fresh2, ids, n_rays=NB, sort_rays=sort_rays, breadth_first=bf)
                 g.merge(cache2, fresh2)
             for i, f in enumerate(sc.freqs):
                 chs[i] = g.channel(cache2, f, out=chs[i])

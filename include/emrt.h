@@ -55,15 +55,23 @@ extern "C" {
 /* emrt_trace_params.flags */
 #define EMRT_TRACE_KEEP_REJECTED 0x1u  /* output every unique candidate, with
                                           EMRT_PATH_VALID set on accepted ones */
-#define EMRT_TRACE_SORT_RAYS 0x2u      /* reorder rays between bounces by
-                                          origin cell and direction bin       */
-#define EMRT_TRACE_WIDE_BVH 0x4u       /* traverse the static geometry through
-                                          its 4-wide BVH (same results; on
-                                          GB300 the binary BVH is faster for
-                                          the city scenes measured)           */
+#define EMRT_TRACE_SORT_RAYS 0x2u      /* breadth-first form: reorder rays
+                                          between bounces by origin cell and
+                                          direction bin                       */
+#define EMRT_TRACE_WIDE_BVH 0x4u       /* breadth-first form through the 4-wide
+                                          BVH of the static geometry (same
+                                          results; on GB300 the binary BVH is
+                                          faster for the city scenes measured) */
 #define EMRT_TRACE_STATIC_CACHE 0x8u   /* keep the static-geometry closest hit of
                                           every ray segment between calls (see
                                           emrt_trace); same results bit for bit */
+#define EMRT_TRACE_BREADTH_FIRST 0x10u /* trace bounce by bounce over all rays
+                                          (one launch per bounce, rays kept in
+                                          buffers between bounces) instead of
+                                          the default depth-first chains (32
+                                          neighbouring primary rays per warp,
+                                          each carried to its end); same
+                                          results bit for bit                 */
 /* emrt_revalidate flags */
 #define EMRT_REVALIDATE_KEEP 0x1u      /* do not compact: flag only          */
 

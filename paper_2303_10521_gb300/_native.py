@@ -20,6 +20,7 @@ TRACE_KEEP_REJECTED = 0x1
 TRACE_SORT_RAYS = 0x2
 TRACE_WIDE_BVH = 0x4
 TRACE_STATIC_CACHE = 0x8
+TRACE_BREADTH_FIRST = 0x10
 REVALIDATE_KEEP = 0x1
 NOALLOC_MAX_PATHS = 65536
 BATCH_AUTOTUNE = 0x1

@@ -375,7 +375,10 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   // the static-hit cache form runs in the chain walker alone: no per-bounce
   // ray buffers or sorts
   const bool cache = (p->flags & EMRT_TRACE_STATIC_CACHE) && !backward;
-  if (!cache && p->max_depth > 0 && nrays > s->ray_cap) {
+  // depth-first chains unless the breadth-first form is asked for (the
+  // 4-wide BVH is traversed by the breadth-first kernel only)
+  const bool walk = !cache && !(p->flags & (EMRT_TRACE_BREADTH_FIRST | EMRT_TRACE_WIDE_BVH));
+  if (!cache && !walk && p->max_depth > 0 && nrays > s->ray_cap) {
     cudaFree(s->rays[0]);
     cudaFree(s->rays[1]);
     s->rays[0] = s->rays[1] = nullptr;
@@ -384,7 +387,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     CK(cudaMalloc(&s->rays[1], sizeof(Ray) * nrays));
     s->ray_cap = nrays;
   }
-  bool sort_rays = (p->flags & EMRT_TRACE_SORT_RAYS) && p->max_depth > 0 && !cache;
+  bool sort_rays = (p->flags & EMRT_TRACE_SORT_RAYS) && p->max_depth > 0 && !cache && !walk;
   if (sort_rays && nrays > s->rsort_cap) {
     for (int k = 0; k < 2; k++) {
       cudaFree(s->rkeys[k]);
@@ -463,8 +466,27 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     cudaEventRecord(s->evb[1], st);
     nev = 1;
   }
+  if (walk) {
+    BounceLaunch L{};
+    L.g = gt;
+    L.n_primary = (uint32_t)nrays;
+    L.dirs = tab->dirs;
+    L.count = (uint32_t)count;
+    L.cand = s->cand;
+    L.cand_cap = s->cand_cap;
+    L.n_cand = &c->n_cand;
+    L.work = &c->chain_work;
+    L.ctr = c;
+    L.kappa = kappa;
+    L.K = (int)p->max_depth;
+    L.jbits = jbits;
+    cudaEventRecord(s->evb[0], st);
+    launch_walk(L, st);
+    cudaEventRecord(s->evb[1], st);
+    nev = 1;
+  }
   int key_buf = 0;  // sort buffer that receives the next bounce's keys
-  for (uint32_t b = 0; !cache && b <= p->max_depth; b++) {
+  for (uint32_t b = 0; !cache && !walk && b <= p->max_depth; b++) {
     BounceLaunch L{};
     L.g = gt;
     L.rin = b ? s->rays[(b - 1) & 1] : nullptr;

@@ -95,6 +95,7 @@ __device__ inline uint32_t ray_key(float3 o, float3 d, float4 lo, float4 hi) {
 
 // ----------------------------------------------------------------------------
 #include "bounce.cuh"
+#include "chain.cuh"
 
 // ----------------------------------------------------------------------------
 // canonical key: tx | rx | depth | f0 | .. | f_{K-1}, most significant first
@@ -481,6 +482,22 @@ uint64_t chain_queue_entries() {
 
 void launch_chain(const BounceLaunch &L, const ChainBufs &D, int grid, cudaStream_t s) {
   emrt::note_launch(), k_chain<kBounceBlock><<<grid, kBounceBlock, 0, s>>>(L, D);
+}
+
+int g_walk_grid = 0;
+int walk_grid() {
+  if (!g_walk_grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<kBounceBlock>, kBounceBlock, 0);
+    g_walk_grid = sms * (per > 0 ? per : 1);
+  }
+  return g_walk_grid;
+}
+
+void launch_walk(const BounceLaunch &L, cudaStream_t s) {
+  emrt::note_launch(), k_walk<kBounceBlock><<<walk_grid(), kBounceBlock, 0, s>>>(L);
 }
 
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,

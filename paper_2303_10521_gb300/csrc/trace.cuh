@@ -59,6 +59,9 @@ struct ChainBufs {
 uint64_t chain_queue_entries();
 void launch_chain(const BounceLaunch &L, const ChainBufs &D, int grid, cudaStream_t s);
 int chain_grid();
+// Depth-first discovery of L.n_primary primary rays without the cache
+// (persistent grid; cursor L.work).
+void launch_walk(const BounceLaunch &L, cudaStream_t s);
 // epoch[t] += 1 and ref[t] = pos[t] for every transmitter whose position
 // differs (bitwise) from ref[t]
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,

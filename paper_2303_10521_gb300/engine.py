@@ -162,39 +162,45 @@ class Scene:
 
     def trace_async(self, out: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
                     keep_rejected=False, sort_rays=True, stream=None, wide_bvh=False,
-                    static_cache=False):
+                    static_cache=False, breadth_first=False):
         """Plain discovery into out (no sync).  static_cache: reuse the static
-        closest hits of earlier calls with this ray set (identical output)."""
+        closest hits of earlier calls with this ray set; breadth_first: trace
+        bounce by bounce (sort_rays and wide_bvh apply to that form) instead
+        of depth-first chains.  Identical output either way."""
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
                           (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
                           (N.TRACE_SORT_RAYS if sort_rays else 0) |
                           (N.TRACE_WIDE_BVH if wide_bvh else 0) |
-                          (N.TRACE_STATIC_CACHE if static_cache else 0))
+                          (N.TRACE_STATIC_CACHE if static_cache else 0) |
+                          (N.TRACE_BREADTH_FIRST if breadth_first else 0))
         pc = out.c()
         N.check(self.lib.emrt_trace(self.h, C.byref(p), C.byref(pc), _stream(stream)),
                 "emrt_trace")
 
     def trace(self, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
               keep_rejected=False, capacity=None, stream=None, retries=3,
-              sort_rays=True, wide_bvh=False, static_cache=False) -> Paths:
+              sort_rays=True, wide_bvh=False, static_cache=False,
+              breadth_first=False) -> Paths:
         """Plain discovery; grows scratch and output on capacity errors."""
         return self._retry(lambda out: self.trace_async(
             out, n_rays, max_depth, offset, stride, count, keep_rejected, sort_rays=sort_rays,
-            stream=stream, wide_bvh=wide_bvh, static_cache=static_cache), capacity, stream,
-            retries, "emrt_trace")
+            stream=stream, wide_bvh=wide_bvh, static_cache=static_cache,
+            breadth_first=breadth_first), capacity, stream, retries, "emrt_trace")
 
     def trace_backward_async(self, out: Paths, rx_ids: Optional[torch.Tensor] = None,
                              n_rays=None, max_depth=None, offset=0, stride=1, count=0,
-                             keep_rejected=False, sort_rays=True, stream=None):
+                             keep_rejected=False, sort_rays=True, stream=None,
+                             breadth_first=False):
         """Backward discovery from the receivers rx_ids (device int tensor;
         None = every receiver); paths come out in forward orientation."""
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
                           (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
-                          (N.TRACE_SORT_RAYS if sort_rays else 0))
+                          (N.TRACE_SORT_RAYS if sort_rays else 0) |
+                          (N.TRACE_BREADTH_FIRST if breadth_first else 0))
         ids, n_ids = None, 0
         if rx_ids is not None:
             ids = rx_ids.to(device=self.device, dtype=torch.int32).contiguous()
@@ -209,12 +215,13 @@ class Scene:
 
     def trace_backward(self, rx_ids: Optional[torch.Tensor] = None, n_rays=None, max_depth=None,
                        offset=0, stride=1, count=0, keep_rejected=False, capacity=None,
-                       stream=None, retries=3, sort_rays=True) -> Paths:
+                       stream=None, retries=3, sort_rays=True,
+                       breadth_first=False) -> Paths:
         """Backward discovery; grows scratch and output on capacity errors."""
         return self._retry(lambda out: self.trace_backward_async(
             out, rx_ids, n_rays, max_depth, offset, stride, count, keep_rejected,
-            sort_rays=sort_rays, stream=stream), capacity, stream, retries,
-            "emrt_trace_backward")
+            sort_rays=sort_rays, stream=stream, breadth_first=breadth_first), capacity, stream,
+            retries, "emrt_trace_backward")
 
     def _retry(self, launch, capacity, stream, retries, name) -> Paths:
         cap = capacity or max(4096, 8 * self.n_tx * self.n_rx)

@@ -34,9 +34,17 @@ def city():
     fr = sc.frame(0)
     g = engine.Scene(sc)
     g.update(fr)
-    allc = g.trace(keep_rejected=True, sort_rays=True)
-    acc = g.trace(sort_rays=True)
+    allc = g.trace(keep_rejected=True)
+    acc = g.trace()
     return sc, fr, g, allc, acc, oracle.OracleScene(sc, fr)
+
+
+def test_city_depth_first_equals_breadth_first(city):
+    """Full-size city frame: the default depth-first chains and the
+    breadth-first form with the coherence sort give the same records."""
+    sc, fr, g, allc, acc, o = city
+    b = g.trace(keep_rejected=True, breadth_first=True, sort_rays=True).records()
+    assert np.array_equal(b, allc.records())
 
 
 def test_city_acceptance_every_candidate(city):

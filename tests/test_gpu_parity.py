@@ -142,6 +142,29 @@ def test_district_subsample_parity(engine, stride, offset):
     assert rf["ok"], rf
 
 
+def test_district_traversal_forms_identical(engine):
+    """The depth-first chains (default), the breadth-first form with and
+    without the ray sort and through the 4-wide BVH, forward and backward:
+    the same records bit for bit and the same segments per bounce."""
+    sc = S.district_scene(seed=0)
+    g = _gpu(engine, sc)
+    forms = [dict(), dict(breadth_first=True), dict(breadth_first=True, sort_rays=False),
+             dict(wide_bvh=True)]
+    ref, ref_segs = None, None
+    for kw in forms:
+        rec = g.trace(stride=13, offset=7, keep_rejected=True, **kw).records()
+        segs = g.last_stats["segments"]
+        if ref is None:
+            ref, ref_segs = rec, segs
+            assert len(rec) > 100
+        assert np.array_equal(rec, ref), kw
+        assert segs == ref_segs, kw
+    ids = torch.arange(0, g.n_rx, 7, dtype=torch.int32, device="cuda")
+    b0 = g.trace_backward(ids, n_rays=20_000, keep_rejected=True).records()
+    b1 = g.trace_backward(ids, n_rays=20_000, keep_rejected=True, breadth_first=True).records()
+    assert len(b0) > 10 and np.array_equal(b0, b1)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_tiny_scenes(engine, seed):
     """Property test on random tiny scenes (<= 25 static faces, 0-2 vehicles,
