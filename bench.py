@@ -198,9 +198,10 @@ class Clocks:
 def run_batched(engine, scenes, dev, reps=5):
     """Batched form: 64 seeded scenes of uneven size (50-2000 buildings,
     0-500 vehicles, 16-4000 receivers, 1-4 Tx, K 2-4, 1e5-4e6 rays) traced by
-    one persistent launch per bounce replayed from a CUDA graph (autotuned
-    variant), against the same 64 traces issued one after another; best of
-    `reps`, CUDA events; records compared scene by scene."""
+    persistent launches over all scenes (autotuned variant: depth-first, one
+    launch, or breadth-first, one per bounce) replayed from a CUDA graph,
+    against the same 64 traces issued one after another; best of `reps`,
+    CUDA events; records compared scene by scene."""
     import torch
     descs = scenes.batched_scenes(seed=0, n=64)
     scs = []

@@ -352,17 +352,21 @@ emrt_status emrt_sync(emrt_scene sc, emrt_stream s, emrt_stats *st);
 
 /* ---------------------------------------------------------------------
  * Batched discovery over many scenes of uneven size (the paper runs one
- * scene at a time).  One persistent traversal launch per
- * bounce serves the rays of every scene of the batch; deduplication,
- * acceptance and the scatter to each scene's output follow once.  The launch
+ * scene at a time).  Persistent traversal launches serve the rays of every
+ * scene of the batch (depth-first: one launch carrying every chain to its
+ * end, the untuned default; breadth-first: one launch per bounce);
+ * deduplication, acceptance and the scatter to each scene's output follow
+ * once.  The launch
  * sequence is captured into a CUDA graph on the first emrt_batch_trace and
  * replayed afterwards.  Limits: <= 64 scenes, <= 16 transmitters per scene,
  * <= 2^22 rays per transmitter. */
 typedef struct emrt_batch_s *emrt_batch;
 
-#define EMRT_BATCH_AUTOTUNE 0x1u /* time every traversal variant (block size x
-                                    rays fetched per warp, coherence sort on or
-                                    off) on this batch and keep the fastest;
+#define EMRT_BATCH_AUTOTUNE 0x1u /* time every traversal variant (form and
+                                    block size; rays fetched per warp and
+                                    coherence sort on or off for the
+                                    breadth-first form) on this batch and keep
+                                    the fastest;
                                     the choice is cached in the JSON file
                                     $EMRT_AUTOTUNE_CACHE (default
                                     $HOME/.emrt_autotune.json) and reused */

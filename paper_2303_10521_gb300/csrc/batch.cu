@@ -1,10 +1,12 @@
-// Batched discovery over many scenes (C-ABI emrt_batch_*): one persistent
-// traversal launch per bounce serves the rays of every scene, followed by one
-// deduplication, one acceptance and a per-scene scatter.  The launch sequence
-// has fixed grids and device-resident counts; it is captured once into a
-// CUDA graph and replayed.  The traversal variant (block size x rays fetched
-// per warp) and the ray coherence sort are chosen by an autotuner that times
-// every candidate on the batch and keeps its choice in a JSON cache file.
+// Batched discovery over many scenes (C-ABI emrt_batch_*): persistent
+// traversal launches serve the rays of every scene -- depth-first (one launch
+// carrying every chain to its end, the default) or breadth-first (one launch
+// per bounce) -- followed by one deduplication, one acceptance and a
+// per-scene scatter.  The launch sequence has fixed grids and device-resident
+// counts; it is captured once into a CUDA graph and replayed.  The traversal
+// variant (form and block size; rays fetched per warp and the ray coherence
+// sort for the breadth-first form) is chosen by an autotuner that times every
+// candidate on the batch and keeps its choice in a JSON cache file.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -40,8 +42,8 @@ struct emrt_batch_s {
   Counters *ctr = nullptr;
   uint32_t *hist = nullptr, *partial = nullptr;
   KeyLayout kl{};
-  int variant = 1;
-  bool sort_rays = true;
+  int variant = default_bounce_variant();
+  bool sort_rays = false;
   uint32_t largest = 0;  // scene whose box quantises the ray sort keys
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -122,11 +124,12 @@ void enqueue(emrt_batch_s *b, int variant, bool sort_rays, cudaStream_t st) {
   Counters *c = b->ctr;
   cudaMemsetAsync(reinterpret_cast<char *>(c) + sizeof(uint32_t), 0,
                   sizeof(Counters) - sizeof(uint32_t), st);
-  for (uint32_t bb = 0; bb <= b->Kmax; bb++) {
+  const bool walk = bounce_variant_depth_first(variant);
+  for (uint32_t bb = 0; bb <= (walk ? 0u : b->Kmax); bb++) {
     BounceLaunch L{};
     L.rin = bb ? b->rays[(bb - 1) & 1] : nullptr;
     L.order = nullptr;
-    if (bb > 0 && sort_rays) {
+    if (bb > 0 && sort_rays && !walk) {
       launch_ray_keys(L.rin, &c->n_ray[bb], b->scenes[b->largest]->bbox, b->rkeys[0], b->rvals[0],
                       st, true);
       bool alt = radix_sort<1>(&c->n_ray[bb], b->rkeys[0], b->rvals[0], b->rkeys[1], b->rvals[1], 24,
@@ -330,6 +333,7 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n, const emrt_t
     float best = 1e30f;
     for (int so = 0; so < 2; so++) {
       for (int v = 0; v < n_bounce_variants(); v++) {
+        if (so && bounce_variant_depth_first(v)) continue;  // no ray sort to switch
         for (int rep = 0; rep < 2; rep++) {  // first run warms caches, second is timed
           cudaEventRecord(e0, st);
           enqueue(b, v, so != 0, st);

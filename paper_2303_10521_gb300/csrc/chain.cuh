@@ -4,25 +4,27 @@
 // its anonymous namespace.
 #pragma once
 
-// One chain from its first unfinished segment to its end.  CACHE: static
-// hit from the cache while the chain is still static and its entry is
-// current, the full static traversal otherwise (stored when the chain is
-// static); without: the full static traversal.  Then the vehicle boxes and
-// reception spheres of this frame, and the reflection.  R.d_id.w holds
-// tx << L.jbits | direction-table position; the segment index b of the
-// chain's first segment is the number of faces already met.  Segments,
-// candidates and cache entries are exactly those of k_bounce.
+// One chain from its first unfinished segment to its end, in scene g (kappa:
+// reception radius factor, K: reflections).  CACHE (single scene): static
+// hit from the cache L.stab while the chain is still static and its entry
+// (tx, item = tx * count + direction-table position) is current, the full
+// static traversal otherwise (stored when the chain is static); without: the
+// full static traversal.  Then the vehicle boxes and reception spheres of
+// this frame, and the reflection.  R holds the origin, L travelled, direction
+// and faces met; the segment index b of its first segment is the number of
+// faces met.  Candidates carry w0 in word 0 and jj (the ray index) in word 7.
+// Segments, candidates and cache entries are exactly those of k_bounce.
 template <bool CACHE>
-__device__ __forceinline__ void carry_chain(const BounceLaunch &L, const Ray &R, float3 rlo,
-                                            float3 rhi, int *stk, float *stt, TravStats &st,
+__device__ __forceinline__ void carry_chain(const BounceLaunch &L, const GeomView &g, float kappa,
+                                            int K, uint32_t w0, uint32_t tx, uint32_t item,
+                                            uint32_t jj, const Ray &R, float3 rlo, float3 rhi,
+                                            int *stk, float *stt, TravStats &st,
                                             uint32_t (&segs)[EMRT_MAX_DEPTH + 1],
                                             uint32_t &reused) {
-  const uint32_t fs = L.g.n_static_faces;
+  const uint32_t fs = g.n_static_faces;
   const uint32_t NO = EMRT_NO_FACE;
   float3 o = f3(R.o_L), d = f3(R.d_id);
   float Lacc = R.o_L.w;
-  const uint32_t id = __float_as_uint(R.d_id.w);
-  const uint32_t tx = id >> L.jbits, pos = id & ((1u << L.jbits) - 1u);
   uint32_t f0 = R.faces.x, f1 = R.faces.y, f2 = R.faces.z, f3_ = R.faces.w;
   uint32_t b = (f0 != NO) + (f1 != NO) + (f2 != NO) + (f3_ != NO);
   for (;;) {
@@ -36,7 +38,7 @@ __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const Ray &R,
     const bool keep = CACHE && (b < 1 || f0 < fs) && (b < 2 || f1 < fs) && (b < 3 || f2 < fs) &&
                       (b < 4 || f3_ < fs);
     if (keep) {
-      slot = b * L.n_slots + tx * L.count + pos;
+      slot = b * L.n_slots + item;
       ep = L.tx_epoch[tx];
       const uint4 e = L.stab[slot];
       if (e.z == ep) {
@@ -47,26 +49,26 @@ __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const Ray &R,
       }
     }
     if (!have) {
-      trace_tris<false, false>(L.g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+      trace_tris<false, false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
       if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
     }
     const uint32_t exv = (prev != NO && prev >= fs) ? (prev - fs) / 6u : NO;
     const uint32_t bb = b;
-    const bool hit = veh_and_rx(L.g, q, o, d, rlo, rhi, Lacc, L.kappa, exv, tbest, face, stk, stt,
-                                st, [&](uint32_t rx) {
+    const bool hit = veh_and_rx(g, q, o, d, rlo, rhi, Lacc, kappa, exv, tbest, face, stk, stt, st,
+                                [&](uint32_t rx) {
       uint32_t s = warp_append(L.n_cand);
       if (s < L.cand_cap) {
         uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * s);
-        c[0] = make_uint4(tx, rx, bb, f0);
-        c[1] = make_uint4(f1, f2, f3_, __float_as_uint(L.dirs[pos].w));
+        c[0] = make_uint4(w0, rx, bb, f0);
+        c[1] = make_uint4(f1, f2, f3_, jj);
       }
     });
 #pragma unroll
     for (uint32_t k = 0; k <= EMRT_MAX_DEPTH; k++)
       if (k == b) segs[k]++;
-    if (!hit || (int)b >= L.K) break;
+    if (!hit || (int)b >= K) break;
     float3 p, r;
-    reflect_step(L.g, face, o, d, tbest, p, r);
+    reflect_step(g, face, o, d, tbest, p, r);
     f0 = b == 0 ? face : f0;
     f1 = b == 1 ? face : f1;
     f2 = b == 2 ? face : f2;
@@ -76,6 +78,18 @@ __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const Ray &R,
     d = r;
     b++;
   }
+}
+
+// A chain of the walker's queue: R.d_id.w holds tx << L.jbits | position in
+// the direction table.
+__device__ __forceinline__ void carry_queued(const BounceLaunch &L, const Ray &R, float3 rlo,
+                                             float3 rhi, int *stk, float *stt, TravStats &st,
+                                             uint32_t (&segs)[EMRT_MAX_DEPTH + 1],
+                                             uint32_t &reused) {
+  const uint32_t id = __float_as_uint(R.d_id.w);
+  const uint32_t tx = id >> L.jbits, pos = id & ((1u << L.jbits) - 1u);
+  carry_chain<true>(L, L.g, L.kappa, L.K, tx, tx, tx * L.count + pos,
+                    __float_as_uint(L.dirs[pos].w), R, rlo, rhi, stk, stt, st, segs, reused);
 }
 
 // Chain walker of the static-hit cache.  Walk tasks: one thread follows the
@@ -176,11 +190,11 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
       const Ray R = wq[qn - 32u + lane];
       __syncwarp();
       qn -= 32u;
-      carry_chain<true>(L, R, rlo, rhi, stk, stt, st, segs, reused);
+      carry_queued(L, R, rlo, rhi, stk, stt, st, segs, reused);
     }
   }
   __syncwarp();
-  if (lane < qn) carry_chain<true>(L, wq[lane], rlo, rhi, stk, stt, st, segs, reused);
+  if (lane < qn) carry_queued(L, wq[lane], rlo, rhi, stk, stt, st, segs, reused);
   __syncwarp();
   for (int b = 0; b <= EMRT_MAX_DEPTH; b++) add_u64(&L.ctr->segments[b], segs[b]);
   add_u64(&L.ctr->node_visits, st.nodes);
@@ -202,9 +216,14 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
 // chains of neighbouring directions stay coherent through their bounces, and
 // there are no ray buffers, sorts or per-bounce launches.  Handing a lane
 // whose chain ended a new primary ray at once was slower: it mixes depths in
-// a warp.  Segments and candidates are exactly those of k_bounce.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L) {
+// a warp.  BATCH: primary items of many scenes (table tab, each item's scene
+// the last whose range starts at or before it; candidates carry
+// scene << 8 | tx); otherwise the single scene in L.g.  Segments and
+// candidates are exactly those of k_bounce.
+template <int BLOCK, bool BATCH>
+__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L,
+                                                             const BatchScene *__restrict__ tab,
+                                                             uint32_t n_scenes) {
   int stk[kStack];
   float stt[kStack];
   TravStats st;
@@ -214,7 +233,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L) {
   const uint32_t n_items = L.n_primary;
   const uint32_t NO = EMRT_NO_FACE;
   float3 rlo, rhi;
-  rx_bounds(L.g.rxb, rlo, rhi);
+  if (!BATCH) rx_bounds(L.g.rxb, rlo, rhi);
   for (;;) {
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(L.work, 32u);
@@ -222,14 +241,32 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L) {
     if (base >= n_items) break;
     const uint32_t i = base + lane;
     if (i < n_items) {
-      const uint32_t tx = i / L.count;
-      const uint32_t k = i - tx * L.count;
-      const float4 p = L.g.tx_pos[tx], dj = L.dirs[k];
+      uint32_t sc = 0, local = i, count = L.count;
+      const float4 *dirs = L.dirs;
+      if (BATCH) {
+        uint32_t lo = 0, hi = n_scenes;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (tab[mid].prim_begin <= i) lo = mid;
+          else hi = mid;
+        }
+        sc = lo;
+        local = i - tab[sc].prim_begin;
+        count = tab[sc].count;
+        dirs = tab[sc].dirs;
+      }
+      const GeomView &g = BATCH ? tab[sc].g : L.g;
+      if (BATCH) rx_bounds(g.rxb, rlo, rhi);
+      const uint32_t tx = local / count;
+      const uint32_t k = local - tx * count;
+      const float4 p = g.tx_pos[tx], dj = dirs[k];
       Ray R;
       R.o_L = make_float4(p.x, p.y, p.z, 0.f);
-      R.d_id = make_float4(dj.x, dj.y, dj.z, __uint_as_float(tx << L.jbits | k));
+      R.d_id = dj;
       R.faces = make_uint4(NO, NO, NO, NO);
-      carry_chain<false>(L, R, rlo, rhi, stk, stt, st, segs, unused);
+      carry_chain<false>(L, g, BATCH ? tab[sc].kappa : L.kappa, BATCH ? (int)tab[sc].K : L.K,
+                         BATCH ? (sc << 8 | tx) : tx, tx, local, __float_as_uint(dj.w), R, rlo,
+                         rhi, stk, stt, st, segs, unused);
     }
     __syncwarp();
   }

@@ -2,6 +2,8 @@
 // acceptance kernels.
 #include <cfloat>
 
+#include <cstring>
+
 #include "trace.cuh"
 #include "traverse.cuh"
 
@@ -490,14 +492,14 @@ int walk_grid() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<kBounceBlock>, kBounceBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<kBounceBlock, false>, kBounceBlock, 0);
     g_walk_grid = sms * (per > 0 ? per : 1);
   }
   return g_walk_grid;
 }
 
 void launch_walk(const BounceLaunch &L, cudaStream_t s) {
-  emrt::note_launch(), k_walk<kBounceBlock><<<walk_grid(), kBounceBlock, 0, s>>>(L);
+  emrt::note_launch(), k_walk<kBounceBlock, false><<<walk_grid(), kBounceBlock, 0, s>>>(L, nullptr, 1);
 }
 
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,
@@ -522,23 +524,33 @@ struct Variant {
   const char *name;
   int block;
   void (*kern)(BounceLaunch, const BatchScene *, uint32_t);
+  bool walk;  // depth-first: one launch for all bounces
   int grid;
 };
 Variant g_variants[] = {
-    {"block64_fetch32", 64, k_bounce<true, 64, 32, false>, 0},
-    {"block128_fetch32", 128, k_bounce<true, 128, 32, false>, 0},
-    {"block256_fetch32", 256, k_bounce<true, 256, 32, false>, 0},
-    {"block128_fetch128", 128, k_bounce<true, 128, 128, false>, 0},
-    {"block256_fetch64", 256, k_bounce<true, 256, 64, false>, 0},
-    {"block64_fetch128", 64, k_bounce<true, 64, 128, false>, 0},
-    {"block128_fetch32_bvh4", 128, k_bounce<true, 128, 32, true>, 0},
-    {"block64_fetch32_bvh4", 64, k_bounce<true, 64, 32, true>, 0},
+    {"block64_fetch32", 64, k_bounce<true, 64, 32, false>, false, 0},
+    {"block128_fetch32", 128, k_bounce<true, 128, 32, false>, false, 0},
+    {"block256_fetch32", 256, k_bounce<true, 256, 32, false>, false, 0},
+    {"block128_fetch128", 128, k_bounce<true, 128, 128, false>, false, 0},
+    {"block256_fetch64", 256, k_bounce<true, 256, 64, false>, false, 0},
+    {"block64_fetch128", 64, k_bounce<true, 64, 128, false>, false, 0},
+    {"block128_fetch32_bvh4", 128, k_bounce<true, 128, 32, true>, false, 0},
+    {"block64_fetch32_bvh4", 64, k_bounce<true, 64, 32, true>, false, 0},
+    {"depth_first_block128", 128, k_walk<128, true>, true, 0},
+    {"depth_first_block64", 64, k_walk<64, true>, true, 0},
+    {"depth_first_block256", 256, k_walk<256, true>, true, 0},
 };
 constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 }  // namespace
 
 int n_bounce_variants() { return kNumVariants; }
 const char *bounce_variant_name(int v) { return g_variants[v].name; }
+bool bounce_variant_depth_first(int v) { return g_variants[v].walk; }
+int default_bounce_variant() {  // fastest on the 64-scene batch measured
+  for (int v = 0; v < kNumVariants; v++)
+    if (!strcmp(g_variants[v].name, "depth_first_block128")) return v;
+  return 0;
+}
 int bounce_variant_grid(int v) {
   Variant &V = g_variants[v];
   if (!V.grid) {

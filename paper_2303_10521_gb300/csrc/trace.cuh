@@ -88,10 +88,13 @@ struct BatchScene {
 };
 constexpr uint32_t kBatchMaxScenes = 64, kBatchMaxTx = 16, kBatchMaxCount = 1u << 22;
 
-// Batched traversal variants (block size x rays fetched per warp); the
-// autotuner picks one.  variant in [0, n_bounce_variants()).
+// Batched traversal variants: breadth-first (block size x rays fetched per
+// warp, one launch per bounce) and depth-first (block size, one launch for
+// all bounces); the autotuner picks one.  variant in [0, n_bounce_variants()).
 int n_bounce_variants();
 const char *bounce_variant_name(int v);
+bool bounce_variant_depth_first(int v);
+int default_bounce_variant();  // the variant used without autotuning
 int bounce_variant_grid(int v);
 void launch_bounce_batched(int variant, const BounceLaunch &L, const BatchScene *tab,
                            uint32_t n_scenes, cudaStream_t s);

@@ -234,8 +234,10 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
   int node = b.root;
   uint32_t iter = 0;
   for (;;) {
-    EMRT_ITER_GUARD(st)
-    if (node >= 0) {
+    // descend through inner nodes until this lane reaches a leaf, so that
+    // the lanes of a warp test their leaves together
+    while (node >= 0) {
+      EMRT_ITER_GUARD(st)
       const float4 *np = b.nodes + 4ll * node;
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
       st.nodes++;
@@ -254,13 +256,19 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
       }
       if (h0) { node = c0; continue; }
       if (h1) { node = c1; continue; }
-    } else {
-      if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
-        hit = true;
-        if (ANY) return true;
+      // pop the next subtree that can still hold a closer hit
+      for (;;) {
+        if (sp == 0) return hit;
+        sp--;
+        if (stt[sp] <= tmax) break;
       }
+      node = stk[sp];
     }
-    // pop the next subtree that can still hold a closer hit
+    EMRT_ITER_GUARD(st)
+    if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
+      hit = true;
+      if (ANY) return true;
+    }
     for (;;) {
       if (sp == 0) return hit;
       sp--;
