@@ -219,6 +219,12 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
                                                           s->face_vert);
   if ((e = grow(&s->ctr, c, 1))) return fail(e); c = 0;
   if ((e = grow(&s->hist, c, 256 * kPrimGrid + 1))) return fail(e); c = 0;
+  for (int k = 0; k < 2; k++) {
+    if ((e = grow(&s->hist_side[k], c, 256 * kPrimGrid + 1))) return fail(e); c = 0;
+    if ((e = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking))) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&s->ev_side[k], cudaEventDisableTiming))) return fail(e);
+  }
+  if ((e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming))) return fail(e);
   if ((e = grow(&s->partial, c, kPrimGrid + 1))) return fail(e); c = 0;
   cudaMemsetAsync(s->ctr, 0, sizeof(Counters), st);
   bbox_of_tris(d->tri_xyz, s->T, s->bbox, st);
@@ -268,6 +274,12 @@ void emrt_scene_destroy(emrt_scene s) {
   cudaFree(s->veh_half); cudaFree(s->veh_lo); cudaFree(s->veh_hi); cudaFree(s->veh_vel);
   cudaFree(s->rx_pos); cudaFree(s->rx_vel); cudaFree(s->tx_pos); cudaFree(s->tx_vel);
   cudaFree(s->ctr); cudaFree(s->hist); cudaFree(s->partial);
+  for (int k = 0; k < 2; k++) {
+    cudaFree(s->hist_side[k]);
+    if (s->side[k]) cudaStreamDestroy(s->side[k]);
+    if (s->ev_side[k]) cudaEventDestroy(s->ev_side[k]);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   for (auto &t : s->dt) {
     cudaFree(t.dirs);
     cudaFree(t.stab);
@@ -304,19 +316,28 @@ emrt_status emrt_scene_update_dynamic(emrt_scene s, const float *veh_pos, const 
                                              s->veh_hi, s->veh_vel, rx_pos, rx_vel, n_rx,
                                              s->rx_pos, s->rx_vel, tx_pos, tx_vel, n_tx, s->tx_pos,
                                              s->tx_vel);
+  // the three per-frame trees are independent small builds (a few tens of
+  // blocks per launch): vehicles and receivers on side streams, the merged
+  // tree on the caller's stream, joined before the update returns
+  CK(cudaEventRecord(s->ev_fork, st));
+  for (int k = 0; k < 2; k++) CK(cudaStreamWaitEvent(s->side[k], s->ev_fork, 0));
   if (s->V) {
     if (s->n_updates % s->rebuild_every == 0)
-      CK(bvh_build_boxes(s->dyn, s->veh_lo, s->veh_hi, s->V, s->bbox, s->hist, st));
+      CK(bvh_build_boxes(s->dyn, s->veh_lo, s->veh_hi, s->V, s->bbox, s->hist_side[0], s->side[0]));
     else
-      CK(bvh_refit_boxes(s->dyn, s->veh_lo, s->veh_hi, st));
+      CK(bvh_refit_boxes(s->dyn, s->veh_lo, s->veh_hi, s->side[0]));
   }
-  CK(bvh_build_points(s->rxb, s->rx_pos, n_rx, s->bbox, s->hist, st));
+  CK(bvh_build_points(s->rxb, s->rx_pos, n_rx, s->bbox, s->hist_side[1], s->side[1]));
   // vehicles and receivers in one tree for discovery's per-segment query
   const uint32_t nm = s->V + n_rx;
   emrt::note_launch(), k_mix_prims<<<ceil_div(nm, 256), 256, 0, st>>>(s->veh_lo, s->veh_hi, s->V,
                                                                      s->rx_pos, n_rx, s->mix_lo,
                                                                      s->mix_hi);
   CK(bvh_build_boxes(s->mix, s->mix_lo, s->mix_hi, nm, s->bbox, s->hist, st));
+  for (int k = 0; k < 2; k++) {
+    CK(cudaEventRecord(s->ev_side[k], s->side[k]));
+    CK(cudaStreamWaitEvent(st, s->ev_side[k], 0));
+  }
   s->n_updates++;
   s->updated = true;
   CK(cudaGetLastError());

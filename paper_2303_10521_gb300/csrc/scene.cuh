@@ -61,6 +61,11 @@ struct emrt_scene_s {
   uint64_t contrib_cap = 0;
   emrt_status sticky = EMRT_OK;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // side streams of the per-frame tree builds (vehicles, receivers), their
+  // fork/join events and histogram scratch
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_side[2] = {nullptr, nullptr};
+  uint32_t *hist_side[2] = {nullptr, nullptr};
   cudaEvent_t evb[2 * (EMRT_MAX_DEPTH + 2)] = {};  // around each traversal launch
   uint32_t ev_bounces = 0;
   bool ev_recorded = false;
