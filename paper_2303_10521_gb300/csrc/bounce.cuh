@@ -63,7 +63,7 @@ constexpr int kRxBuf = 4;  // receivers buffered per segment by the merged query
 template <typename F>
 __device__ inline bool veh_and_rx(const GeomView &g, const RayQ &q, float3 o, float3 d,
                                   float3 rlo, float3 rhi, float Lacc, float kappa, uint32_t exv,
-                                  float &tbest, uint32_t &face, int *stk, float *stt,
+                                  float &tbest, uint32_t &face, StackSlot *stk,
                                   TravStats &st, F &&emit) {
   const uint32_t NO = EMRT_NO_FACE;
   if (g.mix.n_prims) {
@@ -73,23 +73,23 @@ __device__ inline bool veh_and_rx(const GeomView &g, const RayQ &q, float3 o, fl
     int nrx = 0;
     bool over = false;
     trace_veh_rx<kRxBuf>(g.mix, q, tbest, face, g.n_static_faces, g.n_veh, exv, tq, rq, rxb, nrx,
-                         over, stk, stt, st);
+                         over, stk, st);
     const bool hit = face != NO;
     const float t_end = fmaxf(hit ? tbest : escape_t(o, d, rlo, rhi), 0.f);
     if (over) {
       const float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
-      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, emit);
+      query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, st, emit);
     } else {
       for (int k = 0; k < nrx; k++)
         if (rx_hit(g.rx_pos[rxb[k]], q, t_end, Lacc, kappa)) emit(rxb[k]);
     }
     return hit;
   }
-  trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, stt, st);
+  trace_boxes<false>(g.dyn, q, 0.f, tbest, face, g.n_static_faces, exv, NO, stk, st);
   const bool hit = face != NO;
   const float t_end = fmaxf(hit ? tbest : escape_t(o, d, rlo, rhi), 0.f);
   const float rmax = kappa * (Lacc + t_end) * 1.0001f + 1e-6f;
-  query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, stt, st, emit);
+  query_rx(g.rxb, q, t_end, Lacc, kappa, rmax, stk, st, emit);
   return hit;
 }
 
@@ -102,8 +102,7 @@ __device__ inline bool veh_and_rx(const GeomView &g, const RayQ &q, float3 o, fl
 template <bool BATCH, int BLOCK, int FETCH, bool WIDE>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, const BatchScene *__restrict__ tab,
                                                   uint32_t n_scenes) {
-  int stk[kStack];
-  float stt[kStack];
+  StackSlot stk[kStack];
   TravStats st;
   uint32_t segs = 0;
   const uint32_t lane = threadIdx.x & 31;
@@ -171,11 +170,11 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_bounce(BounceLaunch L, 
       ray_setup(q, o, d);
       float tbest = FLT_MAX;
       uint32_t face = NO;
-      trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+      trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, st);
       uint32_t exv = (prev != NO && prev >= g.n_static_faces) ? (prev - g.n_static_faces) / 6u : NO;
       const uint32_t b = (uint32_t)L.b;
       const uint32_t w0 = BATCH ? (sc << 8 | tx) : tx;
-      const bool hit = veh_and_rx(g, q, o, d, rlo, rhi, Lacc, kappa, exv, tbest, face, stk, stt, st,
+      const bool hit = veh_and_rx(g, q, o, d, rlo, rhi, Lacc, kappa, exv, tbest, face, stk, st,
                                   [&](uint32_t rx) {
         uint32_t slot = warp_append(L.n_cand);
         if (slot < L.cand_cap) {

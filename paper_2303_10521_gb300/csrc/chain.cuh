@@ -18,7 +18,7 @@ template <bool CACHE>
 __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const GeomView &g, float kappa,
                                             int K, uint32_t w0, uint32_t tx, uint32_t item,
                                             uint32_t jj, const Ray &R, float3 rlo, float3 rhi,
-                                            int *stk, float *stt, TravStats &st,
+                                            StackSlot *stk, TravStats &st,
                                             uint32_t (&segs)[EMRT_MAX_DEPTH + 1],
                                             uint32_t &reused) {
   const uint32_t fs = g.n_static_faces;
@@ -49,12 +49,12 @@ __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const GeomVie
       }
     }
     if (!have) {
-      trace_tris<false, false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, stt, st);
+      trace_tris<false, false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, st);
       if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
     }
     const uint32_t exv = (prev != NO && prev >= fs) ? (prev - fs) / 6u : NO;
     const uint32_t bb = b;
-    const bool hit = veh_and_rx(g, q, o, d, rlo, rhi, Lacc, kappa, exv, tbest, face, stk, stt, st,
+    const bool hit = veh_and_rx(g, q, o, d, rlo, rhi, Lacc, kappa, exv, tbest, face, stk, st,
                                 [&](uint32_t rx) {
       uint32_t s = warp_append(L.n_cand);
       if (s < L.cand_cap) {
@@ -83,13 +83,13 @@ __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const GeomVie
 // A chain of the walker's queue: R.d_id.w holds tx << L.jbits | position in
 // the direction table.
 __device__ __forceinline__ void carry_queued(const BounceLaunch &L, const Ray &R, float3 rlo,
-                                             float3 rhi, int *stk, float *stt, TravStats &st,
+                                             float3 rhi, StackSlot *stk, TravStats &st,
                                              uint32_t (&segs)[EMRT_MAX_DEPTH + 1],
                                              uint32_t &reused) {
   const uint32_t id = __float_as_uint(R.d_id.w);
   const uint32_t tx = id >> L.jbits, pos = id & ((1u << L.jbits) - 1u);
   carry_chain<true>(L, L.g, L.kappa, L.K, tx, tx, tx * L.count + pos,
-                    __float_as_uint(L.dirs[pos].w), R, rlo, rhi, stk, stt, st, segs, reused);
+                    __float_as_uint(L.dirs[pos].w), R, rlo, rhi, stk, st, segs, reused);
 }
 
 // Chain walker of the static-hit cache.  Walk tasks: one thread follows the
@@ -105,8 +105,7 @@ __device__ __forceinline__ void carry_queued(const BounceLaunch &L, const Ray &R
 // own.  The queue's last chains are carried when the walk is handed out.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, ChainBufs D) {
-  int stk[kStack];
-  float stt[kStack];
+  StackSlot stk[kStack];
   TravStats st;
   uint32_t segs[EMRT_MAX_DEPTH + 1] = {0, 0, 0, 0, 0};
   uint32_t reused = 0, deferred = 0;
@@ -152,7 +151,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
         // the face just left is static, so no vehicle is excluded
         const uint32_t bb = (uint32_t)b;
         const bool hit = veh_and_rx(L.g, q, o, d, rlo, rhi, Lacc, L.kappa, NO, tbest, face, stk,
-                                    stt, st, [&](uint32_t rx) {
+                                    st, [&](uint32_t rx) {
           uint32_t slot = warp_append(L.n_cand);
           if (slot < L.cand_cap) {
             uint4 *c = reinterpret_cast<uint4 *>(L.cand + 8ull * slot);
@@ -190,11 +189,11 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
       const Ray R = wq[qn - 32u + lane];
       __syncwarp();
       qn -= 32u;
-      carry_queued(L, R, rlo, rhi, stk, stt, st, segs, reused);
+      carry_queued(L, R, rlo, rhi, stk, st, segs, reused);
     }
   }
   __syncwarp();
-  if (lane < qn) carry_queued(L, wq[lane], rlo, rhi, stk, stt, st, segs, reused);
+  if (lane < qn) carry_queued(L, wq[lane], rlo, rhi, stk, st, segs, reused);
   __syncwarp();
   for (int b = 0; b <= EMRT_MAX_DEPTH; b++) add_u64(&L.ctr->segments[b], segs[b]);
   add_u64(&L.ctr->node_visits, st.nodes);
@@ -224,8 +223,7 @@ template <int BLOCK, bool BATCH>
 __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L,
                                                              const BatchScene *__restrict__ tab,
                                                              uint32_t n_scenes) {
-  int stk[kStack];
-  float stt[kStack];
+  StackSlot stk[kStack];
   TravStats st;
   uint32_t segs[EMRT_MAX_DEPTH + 1] = {0, 0, 0, 0, 0};
   uint32_t unused = 0;
@@ -266,7 +264,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L,
       R.faces = make_uint4(NO, NO, NO, NO);
       carry_chain<false>(L, g, BATCH ? tab[sc].kappa : L.kappa, BATCH ? (int)tab[sc].K : L.K,
                          BATCH ? (sc << 8 | tx) : tx, tx, local, __float_as_uint(dj.w), R, rlo,
-                         rhi, stk, stt, st, segs, unused);
+                         rhi, stk, st, segs, unused);
     }
     __syncwarp();
   }

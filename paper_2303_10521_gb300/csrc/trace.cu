@@ -277,8 +277,7 @@ __global__ void __launch_bounds__(kBounceBlock) k_accept_occl(GeomView G, const 
                                                               uint32_t *rec, const uint32_t *n,
                                                               const float4 *pts, uint32_t cap,
                                                               Counters *ctr) {
-  int stk[kStack];
-  float stt[kStack];
+  StackSlot stk[kStack];
   TravStats st;
   const uint32_t cnt = min(*n, cap);
   const uint32_t NO = EMRT_NO_FACE;
@@ -304,9 +303,9 @@ __global__ void __launch_bounds__(kBounceBlock) k_accept_occl(GeomView G, const 
     float tmax = 1.f;
     uint32_t hf = NO;
     occl++;
-    bool hit = trace_tris<true>(g.stat, rq, 0.f, tmax, hf, e0, e1, stk, stt, st);
+    bool hit = trace_tris<true>(g.stat, rq, 0.f, tmax, hf, e0, e1, stk, st);
     tmax = 1.f;
-    if (!hit) hit = trace_boxes<true>(g.dyn, rq, 0.f, tmax, hf, g.n_static_faces, v0, v1, stk, stt, st);
+    if (!hit) hit = trace_boxes<true>(g.dyn, rq, 0.f, tmax, hf, g.n_static_faces, v0, v1, stk, st);
     if (hit) atomicAnd(&rec[8ull * i + 2], ~EMRT_PATH_VALID);
   }
   add_u64(&ctr->occl_rays, occl);

@@ -14,6 +14,11 @@
 namespace emrt {
 
 constexpr int kStack = 64;
+// traversal stack entry: node code and entry distance, one 8-byte access
+struct __align__(8) StackSlot {
+  int node;
+  float t;
+};
 // hard bound on loop iterations per query (a safety net: a well-formed tree
 // never comes close); exceeding it records a device error and stops
 constexpr uint32_t kMaxIter = 1u << 22;
@@ -152,7 +157,7 @@ __device__ inline bool leaf_tri(const BVHView &b, uint32_t code, const RayQ &r, 
 // nearest hit child is entered, the others are pushed far-to-near.
 template <bool ANY>
 __device__ inline bool trace_tris4(const BVHView &b, const RayQ &r, float tmin, float &tmax,
-                                   uint32_t &face, uint32_t ex0, uint32_t ex1, int *stk, float *stt,
+                                   uint32_t &face, uint32_t ex0, uint32_t ex1, StackSlot *stk,
                                    TravStats &st) {
   bool hit = false;
   int sp = 0;
@@ -192,13 +197,11 @@ __device__ inline bool trace_tris4(const BVHView &b, const RayQ &r, float tmin, 
             continue;
           }
           int q = sp++;
-          while (q > g0 && stt[q - 1] < tn[k]) {
+          while (q > g0 && stk[q - 1].t < tn[k]) {
             stk[q] = stk[q - 1];
-            stt[q] = stt[q - 1];
             q--;
           }
-          stk[q] = code[k];
-          stt[q] = tn[k];
+          stk[q] = StackSlot{code[k], tn[k]};
         }
         node = code[best];
         continue;
@@ -212,9 +215,9 @@ __device__ inline bool trace_tris4(const BVHView &b, const RayQ &r, float tmin, 
     for (;;) {
       if (sp == 0) return hit;
       sp--;
-      if (stt[sp] <= tmax) break;
+      if (stk[sp].t <= tmax) break;
     }
-    node = stk[sp];
+    node = stk[sp].node;
   }
 }
 
@@ -224,11 +227,11 @@ __device__ inline bool trace_tris4(const BVHView &b, const RayQ &r, float tmin, 
 // WIDE: use the 4-wide collapse when the BVH has one.
 template <bool ANY, bool WIDE = false>
 __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, float &tmax,
-                                  uint32_t &face, uint32_t ex0, uint32_t ex1, int *stk, float *stt,
+                                  uint32_t &face, uint32_t ex0, uint32_t ex1, StackSlot *stk,
                                   TravStats &st) {
   if (b.n_prims == 0) return false;
   if (WIDE && b.nodes4 && b.n_prims >= 2)
-    return trace_tris4<ANY>(b, r, tmin, tmax, face, ex0, ex1, stk, stt, st);
+    return trace_tris4<ANY>(b, r, tmin, tmax, face, ex0, ex1, stk, st);
   bool hit = false;
   int sp = 0;
   int node = b.root;
@@ -249,7 +252,7 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
         int nearc = c0, farc = c1;
         float tfar = tn1;
         if (tn1 < tn0) { nearc = c1; farc = c0; tfar = tn0; }
-        if (sp < kStack) { stk[sp] = farc; stt[sp] = tfar; sp++; }
+        if (sp < kStack) { stk[sp] = StackSlot{farc, tfar}; sp++; }
         else st.overflow = true;
         node = nearc;
         continue;
@@ -260,9 +263,9 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
       for (;;) {
         if (sp == 0) return hit;
         sp--;
-        if (stt[sp] <= tmax) break;
+        if (stk[sp].t <= tmax) break;
       }
-      node = stk[sp];
+      node = stk[sp].node;
     }
     EMRT_ITER_GUARD(st)
     if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
@@ -272,9 +275,9 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
     for (;;) {
       if (sp == 0) return hit;
       sp--;
-      if (stt[sp] <= tmax) break;
+      if (stk[sp].t <= tmax) break;
     }
-    node = stk[sp];
+    node = stk[sp].node;
   }
 }
 
@@ -306,7 +309,7 @@ __device__ inline bool leaf_box(const BVHView &b, uint32_t g, const RayQ &r, flo
 template <bool ANY>
 __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, float &tmax,
                                    uint32_t &face, uint32_t fs, uint32_t exv0, uint32_t exv1,
-                                   int *stk, float *stt, TravStats &st) {
+                                   StackSlot *stk, TravStats &st) {
   if (b.n_prims == 0) return false;
   bool hit = false;
   int sp = 0;
@@ -326,7 +329,7 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
         int nearc = c0, farc = c1;
         float tfar = tn1;
         if (tn1 < tn0) { nearc = c1; farc = c0; tfar = tn0; }
-        if (sp < kStack) { stk[sp] = farc; stt[sp] = tfar; sp++; }
+        if (sp < kStack) { stk[sp] = StackSlot{farc, tfar}; sp++; }
         else st.overflow = true;
         node = nearc;
         continue;
@@ -343,9 +346,9 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
     for (;;) {
       if (sp == 0) return hit;
       sp--;
-      if (stt[sp] <= tmax) break;
+      if (stk[sp].t <= tmax) break;
     }
-    node = stk[sp];
+    node = stk[sp].node;
   }
 }
 
@@ -374,7 +377,7 @@ template <int RXB>
 __device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax, uint32_t &face,
                                     uint32_t fs, uint32_t n_veh, uint32_t exv, float tq,
                                     float rmax, uint32_t *rx_buf, int &n_rx, bool &rx_over,
-                                    int *stk, float *stt, TravStats &st) {
+                                    StackSlot *stk, TravStats &st) {
   if (b.n_prims == 0) return;
   const float3 ol = make_float3(r.ood.x + rmax * r.idir.x, r.ood.y + rmax * r.idir.y,
                                 r.ood.z + rmax * r.idir.z);
@@ -401,7 +404,7 @@ __device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax
         int nearc = c0, farc = c1;
         float tnear = tn0, tfar = tn1;
         if (tn1 < tn0) { nearc = c1; farc = c0; tnear = tn1; tfar = tn0; }
-        if (sp < kStack) { stk[sp] = farc; stt[sp] = tfar; sp++; }
+        if (sp < kStack) { stk[sp] = StackSlot{farc, tfar}; sp++; }
         else st.overflow = true;
         node = nearc;
         tcur = tnear;
@@ -424,10 +427,10 @@ __device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax
     for (;;) {
       if (sp == 0) return;
       sp--;
-      if (stt[sp] <= tmax) break;
+      if (stk[sp].t <= tmax) break;
     }
-    node = stk[sp];
-    tcur = stt[sp];
+    node = stk[sp].node;
+    tcur = stk[sp].t;
   }
 }
 
@@ -436,7 +439,7 @@ __device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax
 // to p, calls emit(receiver id).  rmax bounds kappa (L + t_end).
 template <typename F>
 __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, float L, float kappa,
-                                float rmax, int *stk, float *stt, TravStats &st, F &&emit) {
+                                float rmax, StackSlot *stk, TravStats &st, F &&emit) {
   if (b.n_prims == 0) return;
   int sp = 0;
   int node = b.root;
@@ -459,7 +462,7 @@ __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, fl
                      n2.w + rmax, 0.f, t_end, tn1);
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
-        if (sp < kStack) { stk[sp] = c1; sp++; }
+        if (sp < kStack) { stk[sp] = StackSlot{c1, 0.f}; sp++; }
         else st.overflow = true;
         node = c0;
         continue;
@@ -472,7 +475,7 @@ __device__ inline void query_rx(const BVHView &b, const RayQ &r, float t_end, fl
       if (rx_hit(p, r, t_end, L, kappa)) emit(__float_as_uint(p.w));
     }
     if (sp == 0) return;
-    node = stk[--sp];
+    node = stk[--sp].node;
   }
 }
 
