@@ -201,7 +201,11 @@ emrt_status emrt_revalidate_cache(emrt_scene sc, emrt_paths *cache, uint32_t *n_
 emrt_status emrt_revalidate(emrt_scene sc, emrt_paths *cache, uint32_t flags,
                             emrt_stream s);
 
-/* cache <- sorted union of cache and fresh (both canonical). */
+/* cache <- sorted union of cache and fresh, both in canonical order (as
+ * emrt_trace, emrt_trace_backward, emrt_revalidate and emrt_cache_merge
+ * write them): the two runs are merged, not re-sorted; an input out of order
+ * makes the next emrt_sync return EMRT_ERR_INVALID_ARG.  Equal paths keep
+ * the cache's record with the smaller ray index of the two. */
 emrt_status emrt_cache_merge(emrt_scene sc, emrt_paths *cache,
                              const emrt_paths *fresh, emrt_stream s);
 

@@ -663,7 +663,14 @@ emrt_status emrt_cache_merge(emrt_scene s, emrt_paths *cache, const emrt_paths *
   if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
   launch_concat(cache->rec, cache->count, cache->capacity, fresh->rec, fresh->count,
                 fresh->capacity, s->cand, s->cand_cap, &c->tmp, c, st);
-  dedup(s, s->cand, &c->tmp, s->cand_cap, kl, st);
+  // both inputs are in canonical order: merge their keys along the merge
+  // path instead of sorting the concatenation, then merge equal runs
+  launch_path_keys(s->cand, &c->tmp, s->cand_cap, kl, s->keys[0], s->vals[0], &c->n_eff, st);
+  launch_merge_path(s->keys[0], s->vals[0], cache->count, cache->capacity, &c->n_eff, s->keys[1],
+                    s->vals[1], c, st);
+  launch_heads(s->keys[1], &c->n_eff, s->head, st);
+  exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_unique, s->partial, st);
+  launch_unique(s->cand, s->keys[1], s->vals[1], s->head, s->pos, &c->n_eff, s->uniq, st);
   launch_keep_flags(s->uniq, &c->n_unique, 1, s->head, st);
   exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_accepted, s->partial, st);
   launch_scatter(s->uniq, &c->n_unique, s->head, s->pos, cache->rec, cache->capacity,
@@ -867,6 +874,7 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
   s->sticky = EMRT_OK;
   if (r != EMRT_OK) return r;
   if (h.err & ERR_STACK) return EMRT_ERR_DEVICE;
+  if (h.err & ERR_UNSORTED) return EMRT_ERR_INVALID_ARG;
   if (h.err & (ERR_CAND_OVERFLOW | ERR_PATH_OVERFLOW | ERR_RAY_OVERFLOW)) return EMRT_ERR_CAPACITY;
   return EMRT_OK;
 }

@@ -14,6 +14,7 @@ enum : uint32_t {
   ERR_PATH_OVERFLOW = 2u,   // caller's path buffer too small
   ERR_STACK = 4u,           // traversal stack overflow
   ERR_RAY_OVERFLOW = 8u,    // ray scratch too small (internal bug)
+  ERR_UNSORTED = 16u,       // a merge input is not in canonical order
 };
 
 // per-call counters kept in device memory (one struct per scene)

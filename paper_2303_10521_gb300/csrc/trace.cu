@@ -138,6 +138,40 @@ __device__ inline bool key_eq(const KeyW<4> &a, const KeyW<4> &b) {
   return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2] && a.w[3] == b.w[3];
 }
 
+__device__ inline bool key_lt(const KeyW<4> &a, const KeyW<4> &b) {
+  for (int q = 3; q >= 0; q--)
+    if (a.w[q] != b.w[q]) return a.w[q] < b.w[q];
+  return false;
+}
+
+// Stable merge of two runs of canonical keys, A = keys[0, na) and
+// B = keys[na, n) with na = min(*na_p, cap_a, n), A first among equal keys.
+// Output position k takes the element chosen after the binary search for the
+// number of A keys among the first k outputs (the merge path).  A pair of
+// neighbours out of order in A or in B raises ERR_UNSORTED.
+__global__ void k_merge_path(const KeyW<4> *keys, const uint32_t *vals, const uint32_t *na_p,
+                             uint32_t cap_a, const uint32_t *n_p, KeyW<4> *kout, uint32_t *vout,
+                             Counters *ctr) {
+  const uint32_t n = *n_p;
+  const uint32_t na = min(min(*na_p, cap_a), n), nb = n - na;
+  const KeyW<4> *A = keys, *B = keys + na;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    if (k < na ? (k > 0 && key_lt(A[k], A[k - 1]))
+               : (k > na && key_lt(B[k - na], B[k - na - 1])))
+      atomicOr(&ctr->err, ERR_UNSORTED);
+    uint32_t lo = k > nb ? k - nb : 0, hi = min(k, na);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (!key_lt(B[k - 1 - mid], A[mid])) lo = mid + 1;  // A[mid] precedes B[k-1-mid]
+      else hi = mid;
+    }
+    const uint32_t i = lo, j = k - lo;
+    const bool take_a = i < na && (j >= nb || !key_lt(B[j], A[i]));
+    kout[k] = take_a ? A[i] : B[j];
+    vout[k] = take_a ? vals[i] : vals[na + j];
+  }
+}
+
 __global__ void k_heads(const KeyW<4> *keys, const uint32_t *n, uint32_t *head) {
   uint32_t cnt = *n;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
@@ -641,6 +675,11 @@ void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const 
                    const uint32_t *nb, uint32_t cap_b, uint32_t *dst, uint32_t dst_cap,
                    uint32_t *n_dst, Counters *ctr, cudaStream_t s) {
   emrt::note_launch(), k_concat<<<kPrimGrid * 4, 256, 0, s>>>(a, na, cap_a, b, nb, cap_b, dst, dst_cap, n_dst, ctr);
+}
+void launch_merge_path(const KeyW<4> *keys, const uint32_t *vals, const uint32_t *na, uint32_t cap_a,
+                       const uint32_t *n, KeyW<4> *kout, uint32_t *vout, Counters *ctr,
+                       cudaStream_t s) {
+  emrt::note_launch(), k_merge_path<<<kPrimGrid * 4, 256, 0, s>>>(keys, vals, na, cap_a, n, kout, vout, ctr);
 }
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s) { emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(p, v); }
 

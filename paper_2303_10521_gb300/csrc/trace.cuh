@@ -145,6 +145,12 @@ void launch_copy_records(const uint32_t *in, const uint32_t *n, uint32_t *out, u
 void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const uint32_t *b,
                    const uint32_t *nb, uint32_t cap_b, uint32_t *dst, uint32_t dst_cap,
                    uint32_t *n_dst, Counters *ctr, cudaStream_t s);
+// Stable merge of the canonical key runs keys[0, na) and keys[na, *n)
+// (na = min(*na, cap_a, *n); the first run first among equal keys) into
+// (kout, vout); ERR_UNSORTED when a run is out of order.
+void launch_merge_path(const KeyW<4> *keys, const uint32_t *vals, const uint32_t *na, uint32_t cap_a,
+                       const uint32_t *n, KeyW<4> *kout, uint32_t *vout, Counters *ctr,
+                       cudaStream_t s);
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
 
 // Backward tracing.  out[i] = pos[ids[i]] for i < n (source points of the

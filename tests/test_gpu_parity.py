@@ -238,6 +238,21 @@ def test_revalidation_and_merge(engine):
     merged = rec_to_paths(cache.records())
     want = sorted(set(map(tuple, oracle.key_fields(kept))) | set(map(tuple, oracle.key_fields(fk))))
     assert [tuple(r) for r in oracle.key_fields(merged)] == want
+    # merging the union into itself changes nothing; an input out of
+    # canonical order is reported at the next sync
+    again = engine.Paths(cache.capacity, g.device)
+    again.rec[:cache.n()] = cache.rec[:cache.n()]
+    again.count.fill_(cache.n())
+    g.merge(again, cache)
+    g.sync()
+    assert np.array_equal(again.records(), cache.records())
+    bad = engine.Paths(cache.capacity, g.device)
+    bad.rec[:len(kept)] = torch.flip(p0.rec[:len(kept)], dims=[0])
+    bad.count.fill_(len(kept))
+    g.merge(bad, fresh)
+    from paper_2303_10521_gb300 import _native
+    with pytest.raises(_native.EmrtError):
+        g.sync()
 
 
 def test_dynamic_frames_vehicle_paths(engine):
