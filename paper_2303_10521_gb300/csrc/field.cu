@@ -579,7 +579,10 @@ void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, u
 
 void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                   uint32_t cap, double freq, double *path_out, cudaStream_t s) {
-  emrt::note_launch(), k_field<<<152 * 8, 128, 0, s>>>(g, m, rec, n, cap, freq, path_out);
+  // one warp per block: the ~1e4 paths of a frame spread over every SM's
+  // FP64 units (128-thread blocks left half the SMs idle; measured 4 % of
+  // the channel stage)
+  emrt::note_launch(), k_field<<<152 * 16, 32, 0, s>>>(g, m, rec, n, cap, freq, path_out);
 }
 
 void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
