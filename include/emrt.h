@@ -374,6 +374,10 @@ typedef struct emrt_batch_s *emrt_batch;
                                     the choice is cached in the JSON file
                                     $EMRT_AUTOTUNE_CACHE (default
                                     $HOME/.emrt_autotune.json) and reused */
+#define EMRT_BATCH_BREADTH_FIRST 0x2u /* without autotuning: the breadth-first
+                                         form (one launch per bounce, ray
+                                         sort) instead of the depth-first one;
+                                         same records */
 
 /* scenes[i] must have been updated (emrt_scene_update_dynamic) and keeps its
  * transmitter count for the life of the batch; params[i] and outs[i] are the

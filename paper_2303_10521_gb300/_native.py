@@ -24,6 +24,7 @@ TRACE_BREADTH_FIRST = 0x10
 REVALIDATE_KEEP = 0x1
 NOALLOC_MAX_PATHS = 65536
 BATCH_AUTOTUNE = 0x1
+BATCH_BREADTH_FIRST = 0x2
 
 vp, u32, u64, dbl = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
 

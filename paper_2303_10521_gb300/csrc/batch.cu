@@ -91,6 +91,30 @@ cudaError_t alloc_cand(emrt_batch_s *b, uint64_t cap) {
   return cudaSuccess;
 }
 
+// ray buffers and sort scratch of the breadth-first variants (the
+// depth-first ones keep their rays in registers)
+void free_rays(emrt_batch_s *b) {
+  for (int k = 0; k < 2; k++) {
+    cudaFree(b->rays[k]);
+    cudaFree(b->rkeys[k]);
+    cudaFree(b->rvals[k]);
+    b->rays[k] = nullptr;
+    b->rkeys[k] = nullptr;
+    b->rvals[k] = nullptr;
+  }
+}
+
+cudaError_t alloc_rays(emrt_batch_s *b) {
+  if (b->Kmax == 0 || b->rays[0]) return cudaSuccess;
+  cudaError_t e;
+  for (int k = 0; k < 2; k++) {
+    if ((e = cudaMalloc(&b->rays[k], sizeof(Ray) * b->total))) return e;
+    if ((e = cudaMalloc(&b->rkeys[k], sizeof(KeyW<1>) * b->total))) return e;
+    if ((e = cudaMalloc(&b->rvals[k], sizeof(uint32_t) * b->total))) return e;
+  }
+  return cudaSuccess;
+}
+
 void drop_graph(emrt_batch_s *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -291,13 +315,6 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n, const emrt_t
   cudaStreamSynchronize(st);
   cudaFree(k0);
   cudaFree(v0);
-  if (b->Kmax > 0) {
-    for (int k = 0; k < 2; k++) {
-      BCK(cudaMalloc(&b->rays[k], sizeof(Ray) * b->total));
-      BCK(cudaMalloc(&b->rkeys[k], sizeof(KeyW<1>) * b->total));
-      BCK(cudaMalloc(&b->rvals[k], sizeof(uint32_t) * b->total));
-    }
-  }
   uint64_t want = 0;
   for (uint32_t i = 0; i < n; i++)
     want += 4ull * b->scenes[i]->n_tx * b->scenes[i]->n_rx * (b->params[i].max_depth + 1);
@@ -327,6 +344,7 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n, const emrt_t
       b->sort_rays = so != 0;
     }
   } else if (flags & EMRT_BATCH_AUTOTUNE) {
+    BCK(alloc_rays(b));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -365,6 +383,15 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n, const emrt_t
     snprintf(val, sizeof(val), "%d,%d", b->variant, b->sort_rays ? 1 : 0);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_store(b->tune_key, val);
+  } else if (flags & EMRT_BATCH_BREADTH_FIRST) {
+    b->variant = default_breadth_first_variant();
+    b->sort_rays = true;
+  }
+  if (bounce_variant_depth_first(b->variant)) {
+    cudaStreamSynchronize(st);
+    free_rays(b);
+  } else {
+    BCK(alloc_rays(b));
   }
   cudaError_t e = cudaStreamSynchronize(st);
   if (!e) e = cudaGetLastError();
@@ -444,7 +471,7 @@ void emrt_batch_destroy(emrt_batch b) {
   drop_graph(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   free_scratch(b);
-  for (int k = 0; k < 2; k++) { cudaFree(b->rays[k]); cudaFree(b->rkeys[k]); cudaFree(b->rvals[k]); }
+  free_rays(b);
   for (auto p : b->owned_dirs) cudaFree(p);
   cudaFree(b->d_tab); cudaFree(b->ctr); cudaFree(b->hist); cudaFree(b->partial);
   cudaFree(b->first); cudaFree(b->cnt);

@@ -579,11 +579,14 @@ constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 int n_bounce_variants() { return kNumVariants; }
 const char *bounce_variant_name(int v) { return g_variants[v].name; }
 bool bounce_variant_depth_first(int v) { return g_variants[v].walk; }
-int default_bounce_variant() {  // fastest on the 64-scene batch measured
+int variant_named(const char *name) {
   for (int v = 0; v < kNumVariants; v++)
-    if (!strcmp(g_variants[v].name, "depth_first_block128")) return v;
+    if (!strcmp(g_variants[v].name, name)) return v;
   return 0;
 }
+// fastest on the 64-scene batch measured, of either form
+int default_bounce_variant() { return variant_named("depth_first_block128"); }
+int default_breadth_first_variant() { return variant_named("block128_fetch32"); }
 int bounce_variant_grid(int v) {
   Variant &V = g_variants[v];
   if (!V.grid) {

@@ -95,6 +95,7 @@ int n_bounce_variants();
 const char *bounce_variant_name(int v);
 bool bounce_variant_depth_first(int v);
 int default_bounce_variant();  // the variant used without autotuning
+int default_breadth_first_variant();  // ... with EMRT_BATCH_BREADTH_FIRST
 int bounce_variant_grid(int v);
 void launch_bounce_batched(int variant, const BounceLaunch &L, const BatchScene *tab,
                            uint32_t n_scenes, cudaStream_t s);

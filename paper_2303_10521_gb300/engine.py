@@ -345,10 +345,12 @@ class RefreshSchedule:
 
 
 class Batch:
-    """Batched discovery over several Scenes (wraps ``emrt_batch``): one
-    traversal launch per bounce for all scenes, replayed from a CUDA graph."""
+    """Batched discovery over several Scenes (wraps ``emrt_batch``):
+    traversal launches over all scenes (depth-first by default, one launch per
+    bounce with breadth_first), replayed from a CUDA graph."""
 
-    def __init__(self, scenes, params=None, capacity=None, autotune=False, stream=None):
+    def __init__(self, scenes, params=None, capacity=None, autotune=False, stream=None,
+                 breadth_first=False):
         self.lib = N.load()
         self.scenes = list(scenes)
         n = len(self.scenes)
@@ -370,7 +372,9 @@ class Batch:
         self._scenes = (C.c_void_p * n)(*[sc.h.value for sc in self.scenes])
         h = C.c_void_p()
         N.check(self.lib.emrt_batch_create(self._scenes, n, self._params, self._outs,
-                                           N.BATCH_AUTOTUNE if autotune else 0, _stream(stream),
+                                           (N.BATCH_AUTOTUNE if autotune else 0) |
+                                           (N.BATCH_BREADTH_FIRST if breadth_first else 0),
+                                           _stream(stream),
                                            C.byref(h)), "emrt_batch_create")
         self.h = h
 

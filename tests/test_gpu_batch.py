@@ -1,6 +1,6 @@
-"""Batched discovery (one traversal launch per bounce over many uneven
-scenes, replayed from a CUDA graph) gives, scene by scene, exactly the path
-set of the per-scene plain trace, before and after a frame update."""
+"""Batched discovery (traversal launches over many uneven scenes, replayed
+from a CUDA graph) gives, scene by scene, exactly the path set of the
+per-scene plain trace, before and after a frame update."""
 import numpy as np
 import pytest
 
@@ -47,6 +47,30 @@ def test_batched_equals_sequential(tmp_path, monkeypatch):
                 assert got.shape == ref.shape, (d.name, got.shape, ref.shape)
                 assert np.array_equal(got, ref), d.name
     assert "block" in b.config()
+
+
+@pytest.mark.parametrize("breadth_first", [False, True])
+def test_batch_forms_equal_sequential(breadth_first):
+    """Untuned batches of either traversal form (depth-first: one launch for
+    all bounces; breadth-first: one launch per bounce with the ray sort)
+    give the per-scene traces' records, and say which form they run."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_10521_gb300 import engine
+    descs = _small_batch(n=6, seed=11)
+    scs = []
+    for d in descs:
+        g = engine.Scene(d)
+        g.update(d.frame(0))
+        scs.append(g)
+    caps = [max(4096, 8 * g.n_tx * g.n_rx) for g in scs]
+    b = engine.Batch(scs, capacity=caps, breadth_first=breadth_first)
+    assert ("depth_first" in b.config()) != breadth_first, b.config()
+    b.trace_async()
+    assert b.sync()["error_bits"] == 0
+    for d, g, o in zip(descs, scs, b.outs):
+        ref = g.trace(capacity=o.capacity).records()
+        assert np.array_equal(o.records(), ref), d.name
 
 
 def test_trace_batched_one_call():
