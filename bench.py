@@ -497,8 +497,9 @@ def main():
     # ---------------- cached frames: the path cache is revalidated every frame
     # (image method + occlusion rays on the cached face sequences), new paths
     # come from a low-density rediscovery (N / R_LOW rays, reception radius
-    # for that density) merged into the cache, and a full-density
-    # rediscovery replaces it every REFRESH frames.
+    # for that density) merged into the cache -- the candidates the cache
+    # already holds are not validated again -- and a full-density rediscovery
+    # is merged every REFRESH frames.
     nc = args.cached_frames
     use_sc = not args.no_static_cache
     REFRESH, R_LOW = args.refresh, args.rediscovery_fraction
@@ -509,9 +510,8 @@ def main():
         g.update(cframes[k])
         g.trace_async(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
         g.revalidate(cache)
-        g.trace_async(fresh, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays, breadth_first=bf,
-                      static_cache=use_sc)
-        g.merge(cache, fresh)
+        g.rediscover(cache, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays,
+                     breadth_first=bf, static_cache=use_sc)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
         chs[0].rx[:, 0].clone()  # the accuracy record below; loads its copy kernel
@@ -529,12 +529,10 @@ def main():
         g.update(cframes[k])
         g.revalidate(cache)
         if REFRESH and k % REFRESH == 0:
-            g.trace_async(fresh, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
-            g.merge(cache, fresh)
+            g.rediscover(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
         elif R_LOW:
-            g.trace_async(fresh, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays, breadth_first=bf,
-                          static_cache=use_sc)
-            g.merge(cache, fresh)
+            g.rediscover(cache, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays,
+                         breadth_first=bf, static_cache=use_sc)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
         cached_rx.append(chs[0].rx[:, 0].clone())

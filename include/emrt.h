@@ -171,6 +171,23 @@ emrt_status emrt_trace(emrt_scene sc, const emrt_trace_params *p,
  * the output of the same call without the flag, bit for bit.  Forward
  * emrt_trace only (ignored by emrt_trace_backward and the batched form). */
 
+/* Rediscovery into a path cache (Sec. II-A path caching, Sec. III-B): the
+ * discovery and deduplication of emrt_trace with the ray set p, then
+ * cache <- cache U (accepted candidates), where the candidates the cache
+ * already holds are not validated again -- the cache must have been
+ * revalidated (emrt_revalidate, compacting) with the current poses, so that
+ * their acceptance is already known.  The result equals emrt_trace into a
+ * separate output followed by emrt_cache_merge, bit for bit (a candidate
+ * held as a valid path lowers that record's smallest ray index, as the merge
+ * would).  cache: canonical records (as the calls of this library write
+ * them); it must have room for the union, else emrt_sync returns
+ * EMRT_ERR_CAPACITY and the cache holds only its first capacity records.
+ * EMRT_TRACE_KEEP_REJECTED is not accepted (EMRT_ERR_INVALID_ARG); the other
+ * trace flags apply.  emrt_stats.accepted is the cache count after the
+ * call. */
+emrt_status emrt_rediscover(emrt_scene sc, const emrt_trace_params *p, emrt_paths *cache,
+                            emrt_stream s);
+
 /* Backward discovery (Sec. II-A: ray tracing from the receiver in the
  * visibility step): shoot-and-bounce from receivers, with the same Fibonacci
  * ray set p (per receiver instead of per Tx) and reception spheres of the

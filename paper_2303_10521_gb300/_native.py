@@ -82,6 +82,7 @@ SIGNATURES = {
     "emrt_trace_batched": (C.c_int, [C.POINTER(vp), u32, C.POINTER(TraceParams),
                                      C.POINTER(PathsC), vp]),
     "emrt_cache_merge": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(PathsC), vp]),
+    "emrt_rediscover": (C.c_int, [vp, C.POINTER(TraceParams), C.POINTER(PathsC), vp]),
     "emrt_channel": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, dbl,
                                C.POINTER(ChannelOut), vp]),
     "emrt_channel_backward": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, vp,

@@ -362,9 +362,33 @@ int id_bits(uint64_t v) {
 // canonical dedup, image-method acceptance in the scene's forward geometry
 // and compaction into out.  count: rays per source; jbits: ray-index bits of
 // the ray ids.
+// Tail of a rediscovery: the unique candidates in s->uniq (count n_unique,
+// canonical) that the cache does not hold are accepted, and the accepted
+// ones merged into the cache (both canonical and disjoint: a merge-path
+// gather, no duplicate runs).
+void rediscover_tail(emrt_scene_s *s, const GeomView &g, emrt_paths *cache, cudaStream_t st) {
+  Counters *c = s->ctr;
+  const KeyLayout kl = key_layout(s->n_tx, s->n_rx, s->Fs + 6 * s->V + 1, EMRT_MAX_DEPTH);
+  launch_known(s->uniq, &c->n_unique, cache->rec, cache->count, cache->capacity, kl, s->head, st);
+  exclusive_scan(&c->n_unique, s->head, s->pos, &c->n_eff, s->partial, st);
+  launch_scatter(s->uniq, &c->n_unique, s->head, s->pos, s->cand, s->cand_cap, &c->n_eff, c, st);
+  launch_accept(g, s->cand, &c->n_eff, c, s->apts, s->cand_cap, st);
+  launch_keep_flags(s->cand, &c->n_eff, 0, s->head, st);
+  exclusive_scan(&c->n_eff, s->head, s->pos, &c->tmp, s->partial, st);
+  launch_scatter(s->cand, &c->n_eff, s->head, s->pos, s->uniq, s->cand_cap, &c->tmp, c, st);
+  launch_concat(cache->rec, cache->count, cache->capacity, s->uniq, &c->tmp, s->cand_cap, s->cand,
+                s->cand_cap, &c->n_accepted, c, st);
+  launch_path_keys(s->cand, &c->n_accepted, s->cand_cap, kl, s->keys[0], s->vals[0], &c->n_eff, st);
+  launch_merge_path(s->keys[0], s->vals[0], cache->count, cache->capacity, &c->n_eff, s->keys[1],
+                    s->vals[1], c, st);
+  launch_gather_records(s->cand, s->vals[1], &c->n_eff, cache->rec, cache->capacity, c, st);
+  emrt::note_launch(), k_clamp_count<<<1, 1, 0, st>>>(&c->n_eff, 0xffffffffu, cache->count);
+}
+
 emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t count,
                       const GeomView &gt, uint32_t n_src, int jbits, bool backward,
-                      const uint32_t *rx_ids, emrt_paths *out, cudaStream_t st) {
+                      const uint32_t *rx_ids, emrt_paths *out, cudaStream_t st,
+                      emrt_paths *merge_cache = nullptr) {
   uint32_t nf = s->Fs + 6 * s->V;
   KeyLayout kl = key_layout(s->n_tx, s->n_rx, nf + 1, (int)p->max_depth);
   if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
@@ -450,7 +474,9 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   }
   uint64_t want = std::max<uint64_t>(s->want_cand,
                                      std::max<uint64_t>(1u << 16, 4ull * s->n_tx * s->n_rx * (p->max_depth + 1)));
-  want = std::max<uint64_t>(want, out->capacity);
+  // a rediscovery also concatenates the cache with the new paths in the
+  // candidate scratch
+  want = merge_cache ? want + out->capacity : std::max<uint64_t>(want, out->capacity);
   CK(ensure_cand(s, want));
   // counters: keep the error word, clear the rest
   cudaMemsetAsync(reinterpret_cast<char *>(c) + sizeof(uint32_t), 0,
@@ -553,6 +579,13 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   if (backward) launch_reverse_candidates(s->cand, &c->n_cand, s->cand_cap, rx_ids, st);
   dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
   cudaEventRecord(s->ev[2], st);
+  if (merge_cache) {
+    rediscover_tail(s, g, merge_cache, st);
+    cudaEventRecord(s->ev[3], st);
+    s->ev_recorded = true;
+    CK(cudaGetLastError());
+    return EMRT_OK;
+  }
   launch_accept(g, s->uniq, &c->n_unique, c, s->apts, s->cand_cap, st);
   launch_keep_flags(s->uniq, &c->n_unique, (p->flags & EMRT_TRACE_KEEP_REJECTED) ? 1 : 0, s->head,
                     st);
@@ -590,6 +623,20 @@ emrt_status emrt_trace(emrt_scene s, const emrt_trace_params *p, emrt_paths *out
     return EMRT_ERR_INVALID_ARG;
   return run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, out,
                    (cudaStream_t)stream);
+}
+
+emrt_status emrt_rediscover(emrt_scene s, const emrt_trace_params *p, emrt_paths *cache,
+                            emrt_stream stream) {
+  if (!s || !p || check_paths(cache) != EMRT_OK) return EMRT_ERR_INVALID_ARG;
+  if (p->flags & EMRT_TRACE_KEEP_REJECTED) return EMRT_ERR_INVALID_ARG;
+  if (!s->updated) return EMRT_ERR_STATE;
+  uint64_t count = ray_count(p);
+  if (count == 0 || count > (1u << 24) || count * s->n_tx >= (1ull << 32))
+    return EMRT_ERR_INVALID_ARG;
+  const uint32_t nf = s->Fs + 6 * s->V;
+  if (key_layout(s->n_tx, s->n_rx, nf + 1, EMRT_MAX_DEPTH).total > 128) return EMRT_ERR_INVALID_ARG;
+  return run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, cache,
+                   (cudaStream_t)stream, cache);
 }
 
 emrt_status emrt_trace_backward(emrt_scene s, const emrt_trace_params *p, const uint32_t *rx_ids,

@@ -108,28 +108,33 @@ __device__ inline void push_bits(U128 &k, uint64_t v, int nb) {
   k.lo = (nb < 64) ? ((k.lo << nb) | v) : v;
 }
 
+// canonical key of the record at r
+__device__ inline KeyW<4> record_key(const uint32_t *r, const KeyLayout &kl) {
+  const uint4 *q4 = reinterpret_cast<const uint4 *>(r);
+  uint4 a = q4[0], b = q4[1];
+  uint32_t depth = a.z & 15u;
+  uint32_t f[4] = {a.w, b.x, b.y, b.z};
+  U128 k = {0ull, 0ull};
+  push_bits(k, a.x >> 8, kl.bs);   // scene (batched records; 0 bits otherwise)
+  push_bits(k, a.x & 255u, kl.bt);
+  push_bits(k, a.y, kl.br);
+  push_bits(k, depth, 3);
+  for (int q = 0; q < kl.K; q++) push_bits(k, q < (int)depth ? f[q] : 0u, kl.bf);
+  KeyW<4> kk;
+  kk.w[0] = (uint32_t)k.lo;
+  kk.w[1] = (uint32_t)(k.lo >> 32);
+  kk.w[2] = (uint32_t)k.hi;
+  kk.w[3] = (uint32_t)(k.hi >> 32);
+  return kk;
+}
+
 __global__ void k_path_keys(const uint32_t *rec, const uint32_t *n, uint32_t cap, KeyLayout kl,
                             KeyW<4> *keys, uint32_t *vals, uint32_t *n_eff) {
   uint32_t cnt = min(*n, cap);
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *n_eff = cnt;
   for (; i < cnt; i += gridDim.x * blockDim.x) {
-    const uint4 *r = reinterpret_cast<const uint4 *>(rec + 8ull * i);
-    uint4 a = r[0], b = r[1];
-    uint32_t depth = a.z & 15u;
-    uint32_t f[4] = {a.w, b.x, b.y, b.z};
-    U128 k = {0ull, 0ull};
-    push_bits(k, a.x >> 8, kl.bs);   // scene (batched records; 0 bits otherwise)
-    push_bits(k, a.x & 255u, kl.bt);
-    push_bits(k, a.y, kl.br);
-    push_bits(k, depth, 3);
-    for (int q = 0; q < kl.K; q++) push_bits(k, q < (int)depth ? f[q] : 0u, kl.bf);
-    KeyW<4> kk;
-    kk.w[0] = (uint32_t)k.lo;
-    kk.w[1] = (uint32_t)(k.lo >> 32);
-    kk.w[2] = (uint32_t)k.hi;
-    kk.w[3] = (uint32_t)(k.hi >> 32);
-    keys[i] = kk;
+    keys[i] = record_key(rec + 8ull * i, kl);
     vals[i] = i;
   }
 }
@@ -169,6 +174,45 @@ __global__ void k_merge_path(const KeyW<4> *keys, const uint32_t *vals, const ui
     const bool take_a = i < na && (j >= nb || !key_lt(B[j], A[i]));
     kout[k] = take_a ? A[i] : B[j];
     vout[k] = take_a ? vals[i] : vals[na + j];
+  }
+}
+
+// Candidates already in the cache: for each of the *n unique candidates (in
+// canonical order) a binary search of the cache's canonical records;
+// flag[i] = 1 for a candidate the cache does not hold.  A candidate the
+// cache holds as a valid path lowers that record's smallest ray index to its
+// own (what merging the accepted candidate would have done; one candidate per
+// record, so no two threads write the same word).
+__global__ void k_known(const uint32_t *cand, const uint32_t *n, uint32_t *cache,
+                        const uint32_t *cache_n, uint32_t cache_cap, KeyLayout kl,
+                        uint32_t *flag) {
+  const uint32_t cnt = *n, nc = min(*cache_n, cache_cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const KeyW<4> k = record_key(cand + 8ull * i, kl);
+    uint32_t lo = 0, hi = nc;
+    while (lo < hi) {  // first cache record whose key is not below k
+      const uint32_t mid = (lo + hi) >> 1;
+      if (key_lt(record_key(cache + 8ull * mid, kl), k)) lo = mid + 1;
+      else hi = mid;
+    }
+    const bool found = lo < nc && key_eq(record_key(cache + 8ull * lo, kl), k);
+    flag[i] = found ? 0u : 1u;
+    if (found && (cache[8ull * lo + 2] & EMRT_PATH_VALID))
+      cache[8ull * lo + 7] = min(cache[8ull * lo + 7], cand[8ull * i + 7]);
+  }
+}
+
+// out[k] = rec[vals[k]] for k < min(*n, cap); ERR_PATH_OVERFLOW when *n > cap.
+__global__ void k_gather_records(const uint32_t *rec, const uint32_t *vals, const uint32_t *n,
+                                 uint32_t *out, uint32_t cap, Counters *ctr) {
+  const uint32_t cnt = *n;
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && cnt > cap) atomicOr(&ctr->err, ERR_PATH_OVERFLOW);
+  for (; i < min(cnt, cap); i += gridDim.x * blockDim.x) {
+    const uint4 *r = reinterpret_cast<const uint4 *>(rec + 8ull * vals[i]);
+    uint4 *o = reinterpret_cast<uint4 *>(out + 8ull * i);
+    o[0] = r[0];
+    o[1] = r[1];
   }
 }
 
@@ -683,6 +727,14 @@ void launch_merge_path(const KeyW<4> *keys, const uint32_t *vals, const uint32_t
                        const uint32_t *n, KeyW<4> *kout, uint32_t *vout, Counters *ctr,
                        cudaStream_t s) {
   emrt::note_launch(), k_merge_path<<<kPrimGrid * 4, 256, 0, s>>>(keys, vals, na, cap_a, n, kout, vout, ctr);
+}
+void launch_known(const uint32_t *cand, const uint32_t *n, uint32_t *cache, const uint32_t *cache_n,
+                  uint32_t cache_cap, KeyLayout kl, uint32_t *flag, cudaStream_t s) {
+  emrt::note_launch(), k_known<<<kPrimGrid * 4, 256, 0, s>>>(cand, n, cache, cache_n, cache_cap, kl, flag);
+}
+void launch_gather_records(const uint32_t *rec, const uint32_t *vals, const uint32_t *n,
+                           uint32_t *out, uint32_t cap, Counters *ctr, cudaStream_t s) {
+  emrt::note_launch(), k_gather_records<<<kPrimGrid * 4, 256, 0, s>>>(rec, vals, n, out, cap, ctr);
 }
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s) { emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(p, v); }
 

@@ -152,6 +152,14 @@ void launch_concat(const uint32_t *a, const uint32_t *na, uint32_t cap_a, const 
 void launch_merge_path(const KeyW<4> *keys, const uint32_t *vals, const uint32_t *na, uint32_t cap_a,
                        const uint32_t *n, KeyW<4> *kout, uint32_t *vout, Counters *ctr,
                        cudaStream_t s);
+// flag[i] = 1 for each of the *n canonical candidate records the canonical
+// cache (min(*cache_n, cache_cap) records) does not hold; a candidate it holds
+// as a valid path lowers that record's smallest ray index (word 7).
+void launch_known(const uint32_t *cand, const uint32_t *n, uint32_t *cache, const uint32_t *cache_n,
+                  uint32_t cache_cap, KeyLayout kl, uint32_t *flag, cudaStream_t s);
+// out[k] = rec[vals[k]] for k < min(*n, cap); ERR_PATH_OVERFLOW when *n > cap.
+void launch_gather_records(const uint32_t *rec, const uint32_t *vals, const uint32_t *n,
+                           uint32_t *out, uint32_t cap, Counters *ctr, cudaStream_t s);
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
 
 // Backward tracing.  out[i] = pos[ids[i]] for i < n (source points of the

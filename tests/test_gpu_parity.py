@@ -255,6 +255,35 @@ def test_revalidation_and_merge(engine):
         g.sync()
 
 
+@pytest.mark.parametrize("static_cache", [False, True])
+def test_rediscover_equals_trace_and_merge(engine, static_cache):
+    """Cached frames of the district: revalidation then rediscovery into the
+    cache (candidates the cache holds are not validated again) give the
+    records of revalidation, a separate trace and a merge, bit for bit."""
+    sc = S.district_scene(seed=4)
+    g = _gpu(engine, sc)
+    first = g.trace(stride=29)
+    a = engine.Paths(first.capacity * 4, g.device)
+    b = engine.Paths(first.capacity * 4, g.device)
+    for p in (a, b):
+        p.rec[:first.n()] = first.rec[:first.n()]
+        p.count.fill_(first.n())
+    fresh = engine.Paths(first.capacity * 2, g.device)
+    for k in (1, 2, 3):
+        g.update(sc.frame(k))
+        g.revalidate(a)
+        g.trace_async(fresh, stride=97, offset=k, static_cache=static_cache)
+        g.merge(a, fresh)
+        st_a = g.sync()
+        g.revalidate(b)
+        g.rediscover(b, stride=97, offset=k, static_cache=static_cache)
+        st_b = g.sync()
+        assert st_b["accepted"] == b.n()
+        assert st_a["segments"] == st_b["segments"]
+        assert b.n() > first.n() // 2
+        assert np.array_equal(a.records(), b.records()), k
+
+
 def test_dynamic_frames_vehicle_paths(engine):
     """Several frames of the district: vehicle faces appear in paths, the
     vehicle BVH is refitted and rebuilt, and Doppler matches the oracle."""
