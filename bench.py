@@ -148,32 +148,62 @@ def ncu_summary(form="depth_first"):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 25 ms) around the timed region: started
+    before the warm-up, the region marked with host times, and the samples
+    whose timestamps fall inside it kept (the nearest one when the region is
+    shorter than the interval)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, dev_index):
         self.proc = None
+        self.t0 = self.t1 = None
         self.path = os.path.join("/tmp", f"emrt_clocks_{os.getpid()}.csv")
         try:
+            import torch
             sel = []
-            bus = getattr(__import__("torch").cuda.get_device_properties(dev_index), "pci_bus_id", None)
+            prop = torch.cuda.get_device_properties(dev_index)
+            bus = getattr(prop, "pci_bus_id", None)
             if bus is not None:
-                dom = getattr(__import__("torch").cuda.get_device_properties(dev_index), "pci_domain_id", 0)
-                dv = getattr(__import__("torch").cuda.get_device_properties(dev_index), "pci_device_id", 0)
+                dom = getattr(prop, "pci_domain_id", 0)
+                dv = getattr(prop, "pci_device_id", 0)
                 sel = ["-i", f"{dom:08x}:{bus:02x}:{dv:02x}.0"]
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"] + sel,
+                                          "--format=csv,noheader,nounits", "-lms", "25"] + sel,
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
+    def ready(self, timeout=5.0):
+        """Wait until the sampler has written its first line."""
+        end = time.time() + timeout
+        while self.proc is not None and time.time() < end:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
+
+    def start(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _when(ts):
+        import datetime
+        try:
+            return datetime.datetime.strptime(ts.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.05)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -182,16 +212,23 @@ class Clocks:
         self.f.close()
         rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
         os.unlink(self.path)
-        rows = [r for r in rows if len(r) >= 9]
+        rows = [r for r in rows if len(r) >= 10]
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        when = [self._when(r[0]) for r in rows]
+        keep = rows
+        if self.t0 is not None and self.t1 is not None and all(w is not None for w in when):
+            inside = [r for r, w in zip(rows, when) if self.t0 <= w <= self.t1]
+            mid = 0.5 * (self.t0 + self.t1)
+            keep = inside or [min(zip(rows, when), key=lambda rw: abs(rw[1] - mid))[0]]
+        sm = [float(r[2]) for r in keep if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in keep if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" == v.strip()})
+        reasons = sorted({n for r in keep for n, v in zip(names, r[6:10]) if "Active" == v.strip()})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(keep), "interval_ms": 25,
+                "region_s": round(self.t1 - self.t0, 3) if self.t0 and self.t1 else None}
 
 
 # ---------------------------------------------------------------------------
@@ -357,13 +394,15 @@ def main():
         st = g.sync()
         stats.append(st)
 
+    clocks = Clocks(local)
     warm = []
     for k in range(args.warmup):
         step(k, warm)
     torch.cuda.synchronize()
+    clocks.ready()
     if ws > 1:
         torch.distributed.barrier()
-    clocks = Clocks(local)
+    clocks.start()
     l0 = lib.emrt_kernel_launches()
     stats = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -373,6 +412,7 @@ def main():
         step(k, stats)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     launches = lib.emrt_kernel_launches() - l0
     clk = clocks.stop()
     t_ms = max_over_ranks(e0.elapsed_time(e1), dev)

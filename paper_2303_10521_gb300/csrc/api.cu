@@ -22,8 +22,6 @@ unsigned long long launch_count() { return g_launches.load(); }
 
 namespace {
 
-constexpr uint32_t kNO = EMRT_NO_FACE;
-
 emrt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return EMRT_OK;
   if (e == cudaErrorMemoryAllocation) return EMRT_ERR_OOM;
@@ -48,7 +46,7 @@ cudaError_t grow(T **p, uint64_t &cap, uint64_t need) {
 }
 
 __global__ void k_faces(const uint32_t *off, const float *xyz, const uint32_t *mat, uint32_t F,
-                        double4 *plane, uint4 *info, float4 *vert) {
+                        double4_32a *plane, uint4 *info, float4 *vert) {
   uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   uint32_t a = off[f], nv = off[f + 1] - off[f];
@@ -66,7 +64,7 @@ __global__ void k_faces(const uint32_t *off, const float *xyz, const uint32_t *m
   }
   double l = sqrt(nx * nx + ny * ny + nz * nz);
   nx /= l; ny /= l; nz /= l;
-  plane[f] = make_double4(nx, ny, nz, (nx * cx + ny * cy + nz * cz) / nv);
+  plane[f] = make_double4_32a(nx, ny, nz, (nx * cx + ny * cy + nz * cz) / nv);
   info[f] = make_uint4(a, nv, mat[f], 0u);
 }
 

@@ -324,8 +324,8 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n, const emrt_t
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  char key[256];
-  snprintf(key, sizeof(key), "%s|scenes=%u|rays=%llu|tris=%llu|K=%u", prop.name, n,
+  char key[512];
+  snprintf(key, sizeof(key), "%.256s|scenes=%u|rays=%llu|tris=%llu|K=%u", prop.name, n,
            (unsigned long long)b->total, (unsigned long long)tris, b->Kmax);
   b->tune_key = key;
   fill_table(b);

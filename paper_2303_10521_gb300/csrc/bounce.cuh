@@ -5,7 +5,7 @@
 
 __device__ inline float3 face_normal_f(const GeomView &g, uint32_t f) {
   if (f < g.n_static_faces) {
-    double4 p = g.face_plane[f];
+    double4_32a p = g.face_plane[f];
     return make_float3((float)p.x, (float)p.y, (float)p.z);
   }
   uint32_t j = (f - g.n_static_faces) % 6u;

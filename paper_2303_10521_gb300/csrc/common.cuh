@@ -128,7 +128,7 @@ struct GeomView {
   BVHView rxb;             // receiver points
   BVHView mix;             // vehicles and receivers in one tree (or empty):
                            // prims 0..n_veh-1 boxes, then receiver points
-  const double4 *face_plane;  // [F_s] unit normal, offset
+  const double4_32a *face_plane;  // [F_s] unit normal, offset
   const uint4 *face_info;     // [F_s] vertex offset, vertex count, material, 0
   const float4 *face_vert;    // [NV] polygon vertices
   const float4 *veh_lo;       // [V] box corners (w unused)

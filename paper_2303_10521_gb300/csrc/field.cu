@@ -180,7 +180,7 @@ __device__ inline void load_geom(const GeomView &g, const uint32_t *rec, PathGeo
   for (uint32_t q = 0; q < P.k; q++) {
     P.f[q] = f[q];
     if (f[q] < g.n_static_faces) {
-      double4 p = g.face_plane[f[q]];
+      double4_32a p = g.face_plane[f[q]];
       P.n[q][0] = p.x; P.n[q][1] = p.y; P.n[q][2] = p.z; P.d[q] = p.w;
       P.mat[q] = g.face_info[f[q]].z;
       P.vel[q] = make_float3(0.f, 0.f, 0.f);
@@ -280,7 +280,7 @@ __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32
     const uint32_t *r = rec + 8ull * i;
     uint32_t tx = r[0], rx = r[1];
     if (!record_ok(g, r)) {  // malformed record: no field
-      reinterpret_cast<double4 *>(out)[i] = make_double4(0.0, 0.0, 0.0, 0.0);
+      reinterpret_cast<double4_32a *>(out)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
       continue;
     }
     load_geom(g, r, P);
@@ -305,12 +305,12 @@ __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32
       float3 v = P.vel[q - 1];
       dL += v.x * (kh[q - 1].x - kh[q].x) + v.y * (kh[q - 1].y - kh[q].y) + v.z * (kh[q - 1].z - kh[q].z);
     }
-    double4 o;
+    double4_32a o;
     o.x = a.re;
     o.y = a.im;
     o.z = L / kC;
     o.w = -(freq / kC) * dL;
-    reinterpret_cast<double4 *>(out)[i] = o;
+    reinterpret_cast<double4_32a *>(out)[i] = o;
   }
 }
 
@@ -328,7 +328,7 @@ __global__ void k_pair_seq(const uint32_t *rec, const uint32_t *n, uint32_t cap,
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
     uint32_t e = i;
     for (; e < cnt && rec[8ull * e] == tx && rec[8ull * e + 1] == rx; e++) {
-      double4 o = reinterpret_cast<const double4 *>(path_out)[e];
+      double4_32a o = reinterpret_cast<const double4_32a *>(path_out)[e];
       double w = o.x * o.x + o.y * o.y;
       s[0] += o.x; s[1] += o.y; s[2] += w;
       s[3] += w * o.w; s[4] += w * o.w * o.w;

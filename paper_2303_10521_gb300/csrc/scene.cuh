@@ -10,7 +10,7 @@ struct emrt_scene_s {
   int device = 0;
   uint32_t Fs = 0, T = 0, V = 0, NV = 0, max_rx = 0, max_tx = 0, veh_mat = 0;
   uint32_t rebuild_every = 1, n_updates = 0;
-  double4 *face_plane = nullptr;
+  double4_32a *face_plane = nullptr;
   uint4 *face_info = nullptr;
   float4 *face_vert = nullptr;
   float4 *bbox = nullptr;  // [4]: lo, hi, scratch

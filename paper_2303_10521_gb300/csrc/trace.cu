@@ -246,7 +246,7 @@ __global__ void k_unique(const uint32_t *rec, const KeyW<4> *keys, const uint32_
 // image method in double precision
 __device__ inline void plane_of(const GeomView &g, uint32_t f, D3 &n, double &d) {
   if (f < g.n_static_faces) {
-    double4 p = g.face_plane[f];
+    double4_32a p = g.face_plane[f];
     n = mkd(p.x, p.y, p.z);
     d = p.w;
     return;
