@@ -535,11 +535,12 @@ def main():
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---------------- cached frames: the path cache is revalidated every frame
-    # (image method + occlusion rays on the cached face sequences), new paths
-    # come from a low-density rediscovery (N / R_LOW rays, reception radius
-    # for that density) merged into the cache -- the candidates the cache
-    # already holds are not validated again -- and a full-density rediscovery
-    # is merged every REFRESH frames.
+    # (image method + occlusion rays on the cached face sequences, on a side
+    # stream during the discovery), new paths come from a low-density
+    # rediscovery (N / R_LOW rays, reception radius for that density) merged
+    # into the cache -- the candidates the cache already holds are not
+    # validated again -- and a full-density rediscovery is merged every
+    # REFRESH frames.
     nc = args.cached_frames
     use_sc = not args.no_static_cache
     REFRESH, R_LOW = args.refresh, args.rediscovery_fraction
@@ -549,9 +550,8 @@ def main():
     for k in (nc - 2, nc - 1):  # untimed warm-up of the cached pipeline (sizes scratch)
         g.update(cframes[k])
         g.trace_async(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
-        g.revalidate(cache)
         g.rediscover(cache, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays,
-                     breadth_first=bf, static_cache=use_sc)
+                     breadth_first=bf, static_cache=use_sc, revalidate=True)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
         chs[0].rx[:, 0].clone()  # the accuracy record below; loads its copy kernel
@@ -567,12 +567,14 @@ def main():
     for k in range(1, nc):
         fev[k - 1].record(stream)
         g.update(cframes[k])
-        g.revalidate(cache)
         if REFRESH and k % REFRESH == 0:
-            g.rediscover(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
+            g.rediscover(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc,
+                         revalidate=True)
         elif R_LOW:
             g.rediscover(cache, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays,
-                         breadth_first=bf, static_cache=use_sc)
+                         breadth_first=bf, static_cache=use_sc, revalidate=True)
+        else:
+            g.revalidate(cache)
         for i, f in enumerate(sc.freqs):
             chs[i] = g.channel(cache, f, out=chs[i])
         cached_rx.append(chs[0].rx[:, 0].clone())

@@ -65,6 +65,10 @@ extern "C" {
 #define EMRT_TRACE_STATIC_CACHE 0x8u   /* keep the static-geometry closest hit of
                                           every ray segment between calls (see
                                           emrt_trace); same results bit for bit */
+#define EMRT_TRACE_REVALIDATE_FIRST 0x20u /* emrt_rediscover only: revalidate
+                                          the cache first (as emrt_revalidate,
+                                          compacting), on a side stream while
+                                          the discovery runs              */
 #define EMRT_TRACE_BREADTH_FIRST 0x10u /* trace bounce by bounce over all rays
                                           (one launch per bounce, rays kept in
                                           buffers between bounces) instead of
@@ -176,7 +180,10 @@ emrt_status emrt_trace(emrt_scene sc, const emrt_trace_params *p,
  * cache <- cache U (accepted candidates), where the candidates the cache
  * already holds are not validated again -- the cache must have been
  * revalidated (emrt_revalidate, compacting) with the current poses, so that
- * their acceptance is already known.  The result equals emrt_trace into a
+ * their acceptance is already known.  With EMRT_TRACE_REVALIDATE_FIRST the
+ * call does that revalidation itself, on a side stream overlapping the
+ * discovery (its own scratch, sized for the cache's capacity, allocated on
+ * first use); the result is that of emrt_revalidate followed by this call.  The result equals emrt_trace into a
  * separate output followed by emrt_cache_merge, bit for bit (a candidate
  * held as a valid path lowers that record's smallest ray index, as the merge
  * would).  cache: canonical records (as the calls of this library write

@@ -21,6 +21,7 @@ TRACE_SORT_RAYS = 0x2
 TRACE_WIDE_BVH = 0x4
 TRACE_STATIC_CACHE = 0x8
 TRACE_BREADTH_FIRST = 0x10
+TRACE_REVALIDATE_FIRST = 0x20
 REVALIDATE_KEEP = 0x1
 NOALLOC_MAX_PATHS = 65536
 BATCH_AUTOTUNE = 0x1

@@ -278,6 +278,8 @@ void emrt_scene_destroy(emrt_scene s) {
     if (s->ev_side[k]) cudaEventDestroy(s->ev_side[k]);
   }
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  cudaFree(s->rv_rec); cudaFree(s->rv_head); cudaFree(s->rv_pos); cudaFree(s->rv_partial);
+  cudaFree(s->rv_apts); cudaFree(s->rv_ctr);
   for (auto &t : s->dt) {
     cudaFree(t.dirs);
     cudaFree(t.stab);
@@ -360,6 +362,48 @@ int id_bits(uint64_t v) {
 // canonical dedup, image-method acceptance in the scene's forward geometry
 // and compaction into out.  count: rays per source; jbits: ray-index bits of
 // the ray ids.
+// Revalidation of cache on stream st with the scratch (rec, head, pos,
+// partial, apts; capacity cap >= cache->capacity) and counters c.
+void revalidate_with(emrt_scene_s *s, emrt_paths *cache, uint32_t flags, cudaStream_t st,
+                     uint32_t *rec, uint32_t *head, uint32_t *pos, uint32_t *partial,
+                     float4 *apts, uint32_t cap, Counters *c) {
+  GeomView g = geom(s);
+  // clamp the count to the capacity before acceptance
+  emrt::note_launch(), k_clamp_count<<<1, 1, 0, st>>>(cache->count, cache->capacity, &c->n_eff);
+  launch_copy_records(cache->rec, &c->n_eff, rec, cache->capacity, st);
+  launch_accept(g, rec, &c->n_eff, c, apts, cap, st);
+  int keep_all = (flags & EMRT_REVALIDATE_KEEP) ? 1 : 0;
+  launch_keep_flags(rec, &c->n_eff, keep_all, head, st);
+  exclusive_scan(&c->n_eff, head, pos, &c->n_accepted, partial, st);
+  launch_scatter(rec, &c->n_eff, head, pos, cache->rec, cache->capacity, &c->n_accepted, c, st);
+  emrt::note_launch(), k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+}
+
+// The side-stream revalidation scratch, sized for cap records.
+cudaError_t ensure_rv(emrt_scene_s *s, uint64_t cap) {
+  if (cap <= s->rv_cap && s->rv_rec) return cudaSuccess;
+  cudaFree(s->rv_rec); cudaFree(s->rv_head); cudaFree(s->rv_pos); cudaFree(s->rv_partial);
+  cudaFree(s->rv_apts);
+  s->rv_rec = s->rv_head = s->rv_pos = s->rv_partial = nullptr;
+  s->rv_apts = nullptr;
+  s->rv_cap = 0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->rv_rec, sizeof(uint32_t) * 8 * cap))) return e;
+  if ((e = cudaMalloc(&s->rv_head, sizeof(uint32_t) * cap))) return e;
+  if ((e = cudaMalloc(&s->rv_pos, sizeof(uint32_t) * cap))) return e;
+  if ((e = cudaMalloc(&s->rv_partial, sizeof(uint32_t) * (kPrimGrid + 1)))) return e;
+  if ((e = cudaMalloc(&s->rv_apts, sizeof(float4) * (EMRT_MAX_DEPTH + 2) * cap))) return e;
+  if (!s->rv_ctr && (e = cudaMalloc(&s->rv_ctr, sizeof(Counters)))) return e;
+  s->rv_cap = cap;
+  return cudaSuccess;
+}
+
+// main counters <- error bits and occlusion rays of the side revalidation
+__global__ void k_fold_counters(const Counters *side, Counters *c) {
+  atomicOr(&c->err, side->err);
+  c->occl_rays += side->occl_rays;
+}
+
 // Tail of a rediscovery: the unique candidates in s->uniq (count n_unique,
 // canonical) that the cache does not hold are accepted, and the accepted
 // ones merged into the cache (both canonical and disjoint: a merge-path
@@ -386,7 +430,7 @@ void rediscover_tail(emrt_scene_s *s, const GeomView &g, emrt_paths *cache, cuda
 emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t count,
                       const GeomView &gt, uint32_t n_src, int jbits, bool backward,
                       const uint32_t *rx_ids, emrt_paths *out, cudaStream_t st,
-                      emrt_paths *merge_cache = nullptr) {
+                      emrt_paths *merge_cache = nullptr, cudaEvent_t merge_after = nullptr) {
   uint32_t nf = s->Fs + 6 * s->V;
   KeyLayout kl = key_layout(s->n_tx, s->n_rx, nf + 1, (int)p->max_depth);
   if (kl.total > 128) return EMRT_ERR_INVALID_ARG;
@@ -578,6 +622,10 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   dedup(s, s->cand, &c->n_cand, s->cand_cap, kl, st);
   cudaEventRecord(s->ev[2], st);
   if (merge_cache) {
+    if (merge_after) {  // the cache's revalidation on the side stream
+      CK(cudaStreamWaitEvent(st, merge_after, 0));
+      emrt::note_launch(), k_fold_counters<<<1, 1, 0, st>>>(s->rv_ctr, c);
+    }
     rediscover_tail(s, g, merge_cache, st);
     cudaEventRecord(s->ev[3], st);
     s->ev_recorded = true;
@@ -633,8 +681,21 @@ emrt_status emrt_rediscover(emrt_scene s, const emrt_trace_params *p, emrt_paths
     return EMRT_ERR_INVALID_ARG;
   const uint32_t nf = s->Fs + 6 * s->V;
   if (key_layout(s->n_tx, s->n_rx, nf + 1, EMRT_MAX_DEPTH).total > 128) return EMRT_ERR_INVALID_ARG;
-  return run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, cache,
-                   (cudaStream_t)stream, cache);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t after = nullptr;
+  if (p->flags & EMRT_TRACE_REVALIDATE_FIRST) {
+    // revalidate the cache on a side stream while the discovery runs; the
+    // merge waits for it
+    CK(ensure_rv(s, cache->capacity));
+    CK(cudaEventRecord(s->ev_fork, st));
+    CK(cudaStreamWaitEvent(s->side[0], s->ev_fork, 0));
+    cudaMemsetAsync(s->rv_ctr, 0, sizeof(Counters), s->side[0]);
+    revalidate_with(s, cache, 0u, s->side[0], s->rv_rec, s->rv_head, s->rv_pos, s->rv_partial,
+                    s->rv_apts, (uint32_t)s->rv_cap, s->rv_ctr);
+    CK(cudaEventRecord(s->ev_side[0], s->side[0]));
+    after = s->ev_side[0];
+  }
+  return run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, cache, st, cache, after);
 }
 
 emrt_status emrt_trace_backward(emrt_scene s, const emrt_trace_params *p, const uint32_t *rx_ids,
@@ -669,18 +730,8 @@ emrt_status emrt_revalidate(emrt_scene s, emrt_paths *cache, uint32_t flags, emr
   if (!s->updated) return EMRT_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
   CK(ensure_cand(s, std::max<uint64_t>(s->want_cand, cache->capacity)));
-  Counters *c = s->ctr;
-  GeomView g = geom(s);
-  // clamp the count to the capacity before acceptance
-  emrt::note_launch(), k_clamp_count<<<1, 1, 0, st>>>(cache->count, cache->capacity, &c->n_eff);
-  launch_copy_records(cache->rec, &c->n_eff, s->uniq, cache->capacity, st);
-  launch_accept(g, s->uniq, &c->n_eff, c, s->apts, s->cand_cap, st);
-  int keep_all = (flags & EMRT_REVALIDATE_KEEP) ? 1 : 0;
-  launch_keep_flags(s->uniq, &c->n_eff, keep_all, s->head, st);
-  exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_accepted, s->partial, st);
-  launch_scatter(s->uniq, &c->n_eff, s->head, s->pos, cache->rec, cache->capacity, &c->n_accepted,
-                 c, st);
-  emrt::note_launch(), k_publish_count<<<1, 1, 0, st>>>(c, cache->count);
+  revalidate_with(s, cache, flags, st, s->uniq, s->head, s->pos, s->partial, s->apts, s->cand_cap,
+                  s->ctr);
   CK(cudaGetLastError());
   return EMRT_OK;
 }

@@ -61,6 +61,13 @@ struct emrt_scene_s {
   uint64_t contrib_cap = 0;
   emrt_status sticky = EMRT_OK;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // revalidation scratch of a rediscovery that revalidates its cache on a
+  // side stream while the discovery runs: records, flags, positions, scan
+  // partials, reflection points (capacity rv_cap) and its own counters
+  uint32_t *rv_rec = nullptr, *rv_head = nullptr, *rv_pos = nullptr, *rv_partial = nullptr;
+  float4 *rv_apts = nullptr;
+  Counters *rv_ctr = nullptr;
+  uint64_t rv_cap = 0;
   // side streams of the per-frame tree builds (vehicles, receivers), their
   // fork/join events and histogram scratch
   cudaStream_t side[2] = {nullptr, nullptr};

@@ -238,17 +238,21 @@ class Scene:
         raise N.EmrtError(4, name + " (after retries)")
 
     def rediscover(self, cache: Paths, n_rays=None, max_depth=None, offset=0, stride=1, count=0,
-                   sort_rays=True, stream=None, static_cache=False, breadth_first=False):
+                   sort_rays=True, stream=None, static_cache=False, breadth_first=False,
+                   revalidate=False):
         """cache <- cache | accepted paths of a discovery with this ray set
         (no sync).  The cache must have been revalidated with the current
-        poses: the candidates it holds are not validated again.  Same records
-        as trace_async into a separate output followed by merge."""
+        poses (revalidate=True: done by this call, on a side stream during
+        the discovery): the candidates it holds are not validated again.
+        Same records as revalidate, trace_async into a separate output and
+        merge."""
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
                           (N.TRACE_SORT_RAYS if sort_rays else 0) |
                           (N.TRACE_STATIC_CACHE if static_cache else 0) |
-                          (N.TRACE_BREADTH_FIRST if breadth_first else 0))
+                          (N.TRACE_BREADTH_FIRST if breadth_first else 0) |
+                          (N.TRACE_REVALIDATE_FIRST if revalidate else 0))
         pc = cache.c()
         N.check(self.lib.emrt_rediscover(self.h, C.byref(p), C.byref(pc), _stream(stream)),
                 "emrt_rediscover")

@@ -258,14 +258,16 @@ def test_revalidation_and_merge(engine):
 @pytest.mark.parametrize("static_cache", [False, True])
 def test_rediscover_equals_trace_and_merge(engine, static_cache):
     """Cached frames of the district: revalidation then rediscovery into the
-    cache (candidates the cache holds are not validated again) give the
-    records of revalidation, a separate trace and a merge, bit for bit."""
+    cache (candidates the cache holds are not validated again), and the
+    rediscovery that revalidates on a side stream itself, give the records of
+    revalidation, a separate trace and a merge, bit for bit."""
     sc = S.district_scene(seed=4)
     g = _gpu(engine, sc)
     first = g.trace(stride=29)
     a = engine.Paths(first.capacity * 4, g.device)
     b = engine.Paths(first.capacity * 4, g.device)
-    for p in (a, b):
+    c = engine.Paths(first.capacity * 4, g.device)
+    for p in (a, b, c):
         p.rec[:first.n()] = first.rec[:first.n()]
         p.count.fill_(first.n())
     fresh = engine.Paths(first.capacity * 2, g.device)
@@ -282,6 +284,11 @@ def test_rediscover_equals_trace_and_merge(engine, static_cache):
         assert st_a["segments"] == st_b["segments"]
         assert b.n() > first.n() // 2
         assert np.array_equal(a.records(), b.records()), k
+        # the same with the revalidation inside the call (side stream)
+        g.rediscover(c, stride=97, offset=k, static_cache=static_cache, revalidate=True)
+        st_c = g.sync()
+        assert st_c["error_bits"] == 0
+        assert np.array_equal(a.records(), c.records()), k
 
 
 def test_dynamic_frames_vehicle_paths(engine):
