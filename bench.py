@@ -389,8 +389,7 @@ def main():
     def step(k, stats):
         g.update(frames[k])
         g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf)
-        for i, f in enumerate(sc.freqs):
-            chs[i] = g.channel(out, f, out=chs[i])
+        chs[:] = g.channels(out, sc.freqs, outs=chs)
         st = g.sync()
         stats.append(st)
 
@@ -456,8 +455,7 @@ def main():
     def step_c(k, st_list):
         g.update(frames[k])
         g.trace_async(out, stride=rs, sort_rays=sort_rays, static_cache=True)
-        for i, f in enumerate(sc.freqs):
-            chs[i] = g.channel(out, f, out=chs[i])
+        chs[:] = g.channels(out, sc.freqs, outs=chs)
         st_list.append(g.sync())
 
     for k in range(args.warmup):                    # first call fills the cache
@@ -523,8 +521,8 @@ def main():
         d = F({f: t.to(dev, non_blocking=True) for f, t in pinned[k].items()})
         g.update(d)
         g.trace_async(out, sort_rays=sort_rays, breadth_first=bf)
-        for i, f in enumerate(sc.freqs):
-            chs[i] = g.channel(out, f, out=chs[i])
+        chs[:] = g.channels(out, sc.freqs, outs=chs)
+        for i in range(len(sc.freqs)):
             rx_host[i].copy_(chs[i].rx, non_blocking=True)
         cnt_host.copy_(out.count, non_blocking=True)
         g.sync()
@@ -552,8 +550,7 @@ def main():
         g.trace_async(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
         g.rediscover(cache, n_rays=sc.n_rays // max(R_LOW, 1), sort_rays=sort_rays,
                      breadth_first=bf, static_cache=use_sc, revalidate=True)
-        for i, f in enumerate(sc.freqs):
-            chs[i] = g.channel(cache, f, out=chs[i])
+        chs[:] = g.channels(cache, sc.freqs, outs=chs)
         chs[0].rx[:, 0].clone()  # the accuracy record below; loads its copy kernel
         g.sync()
     g.update(cframes[0])
@@ -575,8 +572,7 @@ def main():
                          breadth_first=bf, static_cache=use_sc, revalidate=True)
         else:
             g.revalidate(cache)
-        for i, f in enumerate(sc.freqs):
-            chs[i] = g.channel(cache, f, out=chs[i])
+        chs[:] = g.channels(cache, sc.freqs, outs=chs)
         cached_rx.append(chs[0].rx[:, 0].clone())
         g.sync()
     e5.record(stream)
@@ -643,8 +639,7 @@ def main():
             if len(ids):
                 g.trace_backward_async(fresh2, ids, n_rays=NB, sort_rays=sort_rays, breadth_first=bf)
                 g.merge(cache2, fresh2)
-            for i, f in enumerate(sc.freqs):
-                chs[i] = g.channel(cache2, f, out=chs[i])
+            chs[:] = g.channels(cache2, sc.freqs, outs=chs)
             rx_rec.append(chs[0].rx[:, 0].clone())
             g.sync()
         fe[nr - 1].record(stream)

@@ -259,6 +259,14 @@ emrt_status emrt_channel(emrt_scene sc, const emrt_paths *paths,
                          double tx_power_w, emrt_channel_out *out,
                          emrt_stream s);
 
+/* emrt_channel at n_freq frequencies (1..8) in one pass: outs[q] receives
+ * the results at freq_hz[q] (host array), exactly as emrt_channel would (the
+ * frequencies share each launch, one grid row per frequency).
+ * outs[q].rx_out may be NULL. */
+emrt_status emrt_channel_multi(emrt_scene sc, const emrt_paths *paths, const emrt_materials *m,
+                               const double *freq_hz, uint32_t n_freq, double tx_power_w,
+                               emrt_channel_out *outs, emrt_stream s);
+
 /* Adjoint of emrt_channel's coherent sums over a frozen path topology:
  * given dloss_dh [n_tx][n_rx][2] (d loss / d Re h, d loss / d Im h),
  * accumulates (overwrites) grad_eps [n_mat], grad_sigma [n_mat] and

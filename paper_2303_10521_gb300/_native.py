@@ -86,6 +86,9 @@ SIGNATURES = {
     "emrt_rediscover": (C.c_int, [vp, C.POINTER(TraceParams), C.POINTER(PathsC), vp]),
     "emrt_channel": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, dbl,
                                C.POINTER(ChannelOut), vp]),
+    "emrt_channel_multi": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials),
+                                     C.POINTER(dbl), C.c_uint32, dbl, C.POINTER(ChannelOut),
+                                     vp]),
     "emrt_channel_backward": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials), dbl, vp,
                                         vp, vp, vp, vp]),
     "emrt_channel_backward_noalloc": (C.c_int, [vp, C.POINTER(PathsC), C.POINTER(Materials),

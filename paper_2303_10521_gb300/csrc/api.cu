@@ -795,16 +795,28 @@ static MatView matview(const emrt_materials *m) {
 emrt_status emrt_channel(emrt_scene s, const emrt_paths *paths, const emrt_materials *m,
                          double freq_hz, double tx_power_w, emrt_channel_out *out,
                          emrt_stream stream) {
-  if (!s || check_paths(paths) != EMRT_OK || check_mat(m) != EMRT_OK || !out || !out->path_out ||
-      !out->pair_out || !(freq_hz > 0))
+  if (!out) return EMRT_ERR_INVALID_ARG;
+  return emrt_channel_multi(s, paths, m, &freq_hz, 1, tx_power_w, out, stream);
+}
+
+emrt_status emrt_channel_multi(emrt_scene s, const emrt_paths *paths, const emrt_materials *m,
+                               const double *freq_hz, uint32_t n_freq, double tx_power_w,
+                               emrt_channel_out *outs, emrt_stream stream) {
+  if (!s || check_paths(paths) != EMRT_OK || check_mat(m) != EMRT_OK || !freq_hz || !outs ||
+      n_freq == 0 || n_freq > kMaxFreq)
     return EMRT_ERR_INVALID_ARG;
+  FreqSet fs{};
+  fs.n = n_freq;
+  for (uint32_t q = 0; q < n_freq; q++) {
+    if (!outs[q].path_out || !outs[q].pair_out || !(freq_hz[q] > 0)) return EMRT_ERR_INVALID_ARG;
+    fs.f[q] = freq_hz[q];
+    fs.path_out[q] = outs[q].path_out;
+    fs.pair_out[q] = outs[q].pair_out;
+    fs.rx_out[q] = outs[q].rx_out;
+  }
   if (!s->updated) return EMRT_ERR_STATE;
-  cudaStream_t st = (cudaStream_t)stream;
-  GeomView g = geom(s);
-  launch_field(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, out->path_out,
-               st);
-  launch_reduce(paths->rec, paths->count, paths->capacity, out->path_out, s->n_tx, s->n_rx,
-                tx_power_w, out->pair_out, out->rx_out, st);
+  launch_channel(geom(s), matview(m), paths->rec, paths->count, paths->capacity, fs, s->n_tx,
+                 s->n_rx, tx_power_w, (cudaStream_t)stream);
   CK(cudaGetLastError());
   return EMRT_OK;
 }

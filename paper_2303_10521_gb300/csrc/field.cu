@@ -272,8 +272,25 @@ __device__ inline void path_field(const PathGeom &P, V3<T> tx, V3<double> rx, co
   Lout = L;
 }
 
+// frequency blockIdx.y of a set (kernel parameters; no dynamic indexing)
+__device__ inline void pick_freq(const FreqSet &fs, double &freq, double *&out) {
+  freq = fs.f[0];
+  out = fs.path_out[0];
+#pragma unroll
+  for (uint32_t q = 1; q < kMaxFreq; q++)
+    if (blockIdx.y == q) {
+      freq = fs.f[q];
+      out = fs.path_out[q];
+    }
+}
+
+// Field of every path at the frequency blockIdx.y of fs (frequencies share
+// the launch, so a frame's ~1e4 paths at two frequencies fill twice the warps).
 __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32_t *n, uint32_t cap,
-                        double freq, double *out) {
+                        FreqSet fs) {
+  double freq;
+  double *out;
+  pick_freq(fs, freq, out);
   uint32_t cnt = min(*n, cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
     PathGeom P;
@@ -319,7 +336,15 @@ __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32
 // equal (tx, rx) in the canonical order sums the run sequentially (fixed
 // order, deterministic); pairs without paths keep the zeros written before.
 __global__ void k_pair_seq(const uint32_t *rec, const uint32_t *n, uint32_t cap, uint32_t n_tx,
-                           uint32_t n_rx, const double *path_out, double *pair_out) {
+                           uint32_t n_rx, FreqSet fs) {
+  const double *path_out = fs.path_out[0];
+  double *pair_out = fs.pair_out[0];
+#pragma unroll
+  for (uint32_t q = 1; q < kMaxFreq; q++)
+    if (blockIdx.y == q) {
+      path_out = fs.path_out[q];
+      pair_out = fs.pair_out[q];
+    }
   uint32_t cnt = min(*n, cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
     uint32_t tx = rec[8ull * i], rx = rec[8ull * i + 1];
@@ -345,10 +370,17 @@ __global__ void k_pair_seq(const uint32_t *rec, const uint32_t *n, uint32_t cap,
   }
 }
 
-__global__ void k_rx_power(const double *pair_out, uint32_t n_tx, uint32_t n_rx, double pt,
-                           double *rx_out) {
+__global__ void k_rx_power(uint32_t n_tx, uint32_t n_rx, double pt, FreqSet fs) {
+  const double *pair_out = fs.pair_out[0];
+  double *rx_out = fs.rx_out[0];
+#pragma unroll
+  for (uint32_t q = 1; q < kMaxFreq; q++)
+    if (blockIdx.y == q) {
+      pair_out = fs.pair_out[q];
+      rx_out = fs.rx_out[q];
+    }
   uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_rx) return;
+  if (r >= n_rx || !rx_out) return;
   double coh = 0.0, inc = 0.0;
   for (uint32_t t = 0; t < n_tx; t++) {
     const double *o = pair_out + 8ull * (t * n_rx + r);
@@ -577,22 +609,20 @@ void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, u
   emrt::note_launch(), k_compact_ids<<<ceil_div(n, 256), 256, 0, s>>>(flag, pos, n, ids);
 }
 
-void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
-                  uint32_t cap, double freq, double *path_out, cudaStream_t s) {
+void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
+                    uint32_t cap, const FreqSet &fs, uint32_t n_tx, uint32_t n_rx,
+                    double tx_power_w, cudaStream_t s) {
   // one warp per block: the ~1e4 paths of a frame spread over every SM's
   // FP64 units (128-thread blocks left half the SMs idle; measured 4 % of
-  // the channel stage)
-  emrt::note_launch(), k_field<<<152 * 16, 32, 0, s>>>(g, m, rec, n, cap, freq, path_out);
-}
-
-void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
-                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, double *pair_out,
-                   double *rx_out, cudaStream_t s) {
+  // the channel stage); one grid row per frequency
+  emrt::note_launch(), k_field<<<dim3(152 * 16, fs.n), 32, 0, s>>>(g, m, rec, n, cap, fs);
   uint32_t np = n_tx * n_rx;
-  cudaMemsetAsync(pair_out, 0, sizeof(double) * 8 * np, s);
-  emrt::note_launch(), k_pair_seq<<<152 * 8, 256, 0, s>>>(rec, n, cap, n_tx, n_rx, path_out, pair_out);
-  if (rx_out)
-    emrt::note_launch(), k_rx_power<<<ceil_div(n_rx, 256), 256, 0, s>>>(pair_out, n_tx, n_rx, tx_power_w, rx_out);
+  for (uint32_t q = 0; q < fs.n; q++) cudaMemsetAsync(fs.pair_out[q], 0, sizeof(double) * 8 * np, s);
+  emrt::note_launch(), k_pair_seq<<<dim3(152 * 8, fs.n), 256, 0, s>>>(rec, n, cap, n_tx, n_rx, fs);
+  bool any_rx = false;
+  for (uint32_t q = 0; q < fs.n; q++) any_rx = any_rx || fs.rx_out[q];
+  if (any_rx)
+    emrt::note_launch(), k_rx_power<<<dim3(ceil_div(n_rx, 256), fs.n), 256, 0, s>>>(n_tx, n_rx, tx_power_w, fs);
 }
 
 int adjoint_grid() { return 152 * 4; }

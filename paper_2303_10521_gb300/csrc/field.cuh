@@ -9,14 +9,20 @@ struct MatView {
   uint32_t n_mat, const_gamma;
 };
 
-// per-path (Re a, Im a, tau, f_D) for min(*n, cap) canonical records
-void launch_field(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
-                  uint32_t cap, double freq, double *path_out, cudaStream_t s);
-// per (tx, rx) statistics (zeros for pairs without paths) and per-receiver
-// powers; records must be in canonical order
-void launch_reduce(const uint32_t *rec, const uint32_t *n, uint32_t cap, const double *path_out,
-                   uint32_t n_tx, uint32_t n_rx, double tx_power_w, double *pair_out,
-                   double *rx_out, cudaStream_t s);
+// Frequencies of one channel evaluation and their outputs (rx_out[q] may be
+// null).
+constexpr uint32_t kMaxFreq = 8;
+struct FreqSet {
+  double f[kMaxFreq];
+  double *path_out[kMaxFreq], *pair_out[kMaxFreq], *rx_out[kMaxFreq];
+  uint32_t n;
+};
+// per frequency: per-path (Re a, Im a, tau, f_D) for min(*n, cap) canonical
+// records, per (tx, rx) statistics (zeros for pairs without paths) and
+// per-receiver powers; records must be in canonical order
+void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
+                    uint32_t cap, const FreqSet &fs, uint32_t n_tx, uint32_t n_rx,
+                    double tx_power_w, cudaStream_t s);
 // adjoint: gradients w.r.t. eps_r [n_mat], sigma [n_mat], tx position
 // [n_tx][3]; `partial` is per-path scratch of cap * (3 + 2 EMRT_MAX_DEPTH)
 // doubles (tangent contributions), reduced per parameter in a fixed order

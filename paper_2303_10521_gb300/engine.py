@@ -294,6 +294,30 @@ class Scene:
                                       C.byref(co), _stream(stream)), "emrt_channel")
         return out
 
+    def channels(self, paths: Paths, freqs, tx_power_w: Optional[float] = None,
+                 const_gamma=False, eps_r=None, sigma=None, outs=None,
+                 stream=None) -> list:
+        """channel() at several frequencies in one pass (emrt_channel_multi);
+        outs: optional list of ChannelResult to reuse."""
+        d = self.device
+        freqs = [float(f) for f in freqs]
+        outs = list(outs) if outs is not None else [None] * len(freqs)
+        for q, o in enumerate(outs):
+            if o is None:
+                outs[q] = ChannelResult(
+                    torch.empty((max(paths.capacity, 1), 4), dtype=torch.float64, device=d),
+                    torch.empty((self.n_tx, self.n_rx, 8), dtype=torch.float64, device=d),
+                    torch.empty((self.n_rx, 2), dtype=torch.float64, device=d))
+        m = self._mat(const_gamma, eps_r, sigma)
+        cos = (N.ChannelOut * len(freqs))(*[N.ChannelOut(o.path.data_ptr(), o.pair.data_ptr(),
+                                                          o.rx.data_ptr()) for o in outs])
+        fa = (C.c_double * len(freqs))(*freqs)
+        pc = paths.c()
+        pt = self.desc.tx_power_w if tx_power_w is None else tx_power_w
+        N.check(self.lib.emrt_channel_multi(self.h, C.byref(pc), C.byref(m), fa, len(freqs),
+                                            float(pt), cos, _stream(stream)), "emrt_channel_multi")
+        return outs
+
     def channel_backward(self, paths: Paths, freq: float, dloss_dh: torch.Tensor,
                          const_gamma=False, eps_r=None, sigma=None, stream=None):
         d = self.device

@@ -313,6 +313,23 @@ def test_dynamic_frames_vehicle_paths(engine):
     assert seen_vehicle
 
 
+def test_channel_multi_equals_single(engine):
+    """emrt_channel_multi (all frequencies in one pass) gives, frequency by
+    frequency, exactly the outputs of emrt_channel."""
+    sc = S.district_scene(seed=0)
+    g = _gpu(engine, sc)
+    p = g.trace(stride=61)
+    assert p.n() > 50
+    freqs = [3.5e9, 28e9, 5.9e9]
+    multi = g.channels(p, freqs)
+    for f, m in zip(freqs, multi):
+        one = g.channel(p, f)
+        n = p.n()
+        assert torch.equal(m.path[:n], one.path[:n])
+        assert torch.equal(m.pair, one.pair)
+        assert torch.equal(m.rx, one.rx)
+
+
 def test_constant_gamma_mode(engine):
     sc = S.toy_scene(seed=3)
     g = _gpu(engine, sc)
