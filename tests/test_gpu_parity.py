@@ -386,3 +386,19 @@ def test_invalid_arguments(engine):
     with pytest.raises(E.N.EmrtError) as ei:
         g.trace_async(out, n_rays=100, offset=100)
     assert ei.value.code == 1
+    # multi-frequency channel: 1..8 frequencies, all positive
+    paths = g.trace(n_rays=20_000)
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.channels(paths, [])
+    assert ei.value.code == 1
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.channels(paths, [3.5e9] * 9)
+    assert ei.value.code == 1
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.channels(paths, [3.5e9, -1.0])
+    assert ei.value.code == 1
+    # rediscovery does not keep rejected candidates
+    p = E.N.TraceParams(2, 20_000, 0, 1, 0, E.N.TRACE_KEEP_REJECTED)
+    pc = paths.c()
+    code = g.lib.emrt_rediscover(g.h, E.C.byref(p), E.C.byref(pc), None)
+    assert code == 1
