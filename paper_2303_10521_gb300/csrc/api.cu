@@ -141,16 +141,23 @@ cudaError_t ensure_cand(emrt_scene_s *s, uint64_t need) {
   return cudaSuccess;
 }
 
+constexpr int kDedupPasses = 4;
+
 // Sort + unique of records [0, *n) of `src` (capacity cap) into s->uniq;
 // unique count in ctr->n_unique.
 void dedup(emrt_scene_s *s, const uint32_t *src, const uint32_t *n, uint32_t cap, KeyLayout kl,
            cudaStream_t st) {
   Counters *c = s->ctr;
   launch_path_keys(src, n, cap, kl, s->keys[0], s->vals[0], &c->n_eff, st);
+  // radix passes over the top kDedupPasses bytes only; the runs equal there
+  // (a few candidates each) are then sorted in place by the whole key
+  const int passes = (kl.total + 7) / 8;
+  const int first = passes > kDedupPasses + 1 ? passes - kDedupPasses : 0;
   bool alt = radix_sort<4>(&c->n_eff, s->keys[0], s->vals[0], s->keys[1], s->vals[1], kl.total,
-                           s->hist, st, cap);
+                           s->hist, st, cap, first);
   KeyW<4> *ks = s->keys[alt ? 1 : 0];
   uint32_t *vs = s->vals[alt ? 1 : 0];
+  if (first) launch_sort_runs(ks, vs, &c->n_eff, 8 * first, st);
   launch_heads(ks, &c->n_eff, s->head, st);
   exclusive_scan(&c->n_eff, s->head, s->pos, &c->n_unique, s->partial, st);
   launch_unique(src, ks, vs, s->head, s->pos, &c->n_eff, s->uniq, st);

@@ -265,12 +265,13 @@ __global__ void __launch_bounds__(kPrimBlock) k_scan_down(const uint32_t *d_n, c
 
 template <int W>
 bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *keys2,
-                uint32_t *vals2, int bits, uint32_t *hist, cudaStream_t s, uint64_t max_n) {
+                uint32_t *vals2, int bits, uint32_t *hist, cudaStream_t s, uint64_t max_n,
+                int first_pass) {
   int passes = (bits + 7) / 8;
   // blocks: about 8 tiles of 256 keys each for the largest possible count
   int G = (int)std::min<uint64_t>(kPrimGrid, std::max<uint64_t>(1, (max_n + 2047) / 2048));
   bool alt = false;
-  for (int p = 0; p < passes; p++) {
+  for (int p = first_pass; p < passes; p++) {
     KeyW<W> *ki = alt ? keys2 : keys, *ko = alt ? keys : keys2;
     uint32_t *vi = alt ? vals2 : vals, *vo = alt ? vals : vals2;
     emrt::note_launch(), k_hist<W><<<G, kPrimBlock, 0, s>>>(d_n, ki, p, hist);
@@ -282,11 +283,11 @@ bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals, KeyW<W> *key
 }
 
 template bool radix_sort<1>(const uint32_t *, KeyW<1> *, uint32_t *, KeyW<1> *, uint32_t *,
-                            int, uint32_t *, cudaStream_t, uint64_t);
+                            int, uint32_t *, cudaStream_t, uint64_t, int);
 template bool radix_sort<2>(const uint32_t *, KeyW<2> *, uint32_t *, KeyW<2> *, uint32_t *,
-                            int, uint32_t *, cudaStream_t, uint64_t);
+                            int, uint32_t *, cudaStream_t, uint64_t, int);
 template bool radix_sort<4>(const uint32_t *, KeyW<4> *, uint32_t *, KeyW<4> *, uint32_t *,
-                            int, uint32_t *, cudaStream_t, uint64_t);
+                            int, uint32_t *, cudaStream_t, uint64_t, int);
 
 void exclusive_scan(const uint32_t *d_n, const uint32_t *in, uint32_t *out, uint32_t *d_total,
                     uint32_t *partial, cudaStream_t s) {

@@ -20,10 +20,12 @@ struct alignas(W == 1 ? 4 : (W == 2 ? 8 : 16)) KeyW {
 // (keys2, vals2); returns true when the result ends in (keys2, vals2).
 // hist must hold 256 * kPrimGrid + 1 words.  max_n is a host-side upper
 // bound of *d_n (the buffer capacity); it sets the grid size.
+// first_pass > 0 skips the low 8 * first_pass bits: the result is then
+// ordered by bits [8 * first_pass, bits) only.
 template <int W>
 bool radix_sort(const uint32_t *d_n, KeyW<W> *keys, uint32_t *vals,
                 KeyW<W> *keys2, uint32_t *vals2, int bits, uint32_t *hist,
-                cudaStream_t s, uint64_t max_n);
+                cudaStream_t s, uint64_t max_n, int first_pass = 0);
 
 // out[i] = sum_{k<i} in[i]; *d_total = sum (may alias nothing).  partial
 // must hold kPrimGrid + 1 words.

@@ -177,6 +177,72 @@ __global__ void k_merge_path(const KeyW<4> *keys, const uint32_t *vals, const ui
   }
 }
 
+// equal keys above bit lb
+__device__ inline bool key_prefix_eq(const KeyW<4> &a, const KeyW<4> &b, int lb) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int lo = 32 * q;
+    if (lo + 32 <= lb) continue;
+    const int sh = lb > lo ? lb - lo : 0;
+    if ((a.w[q] >> sh) != (b.w[q] >> sh)) return false;
+  }
+  return true;
+}
+
+// Completes a sort ordered by the key bits from lb up: each run of keys equal
+// in those bits is sorted by the whole key, in place, by the thread at its
+// head (insertion sort for short runs, heap sort for long ones; the order of
+// equal keys is not kept).
+__global__ void k_sort_runs(KeyW<4> *k, uint32_t *v, const uint32_t *n, int lb) {
+  const uint32_t cnt = *n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    if (i > 0 && key_prefix_eq(k[i], k[i - 1], lb)) continue;
+    uint32_t e = i + 1;
+    while (e < cnt && key_prefix_eq(k[e], k[i], lb)) e++;
+    const uint32_t len = e - i;
+    if (len < 2) continue;
+    KeyW<4> *kk = k + i;
+    uint32_t *vv = v + i;
+    if (len <= 32) {
+      for (uint32_t a = 1; a < len; a++) {
+        const KeyW<4> x = kk[a];
+        const uint32_t xv = vv[a];
+        uint32_t b = a;
+        while (b > 0 && key_lt(x, kk[b - 1])) {
+          kk[b] = kk[b - 1];
+          vv[b] = vv[b - 1];
+          b--;
+        }
+        kk[b] = x;
+        vv[b] = xv;
+      }
+      continue;
+    }
+    auto swap = [&](uint32_t a, uint32_t b) {
+      const KeyW<4> t = kk[a];
+      kk[a] = kk[b];
+      kk[b] = t;
+      const uint32_t tv = vv[a];
+      vv[a] = vv[b];
+      vv[b] = tv;
+    };
+    auto sift = [&](uint32_t root, uint32_t end) {
+      while (2 * root + 1 < end) {
+        uint32_t c = 2 * root + 1;
+        if (c + 1 < end && key_lt(kk[c], kk[c + 1])) c++;
+        if (!key_lt(kk[root], kk[c])) break;
+        swap(root, c);
+        root = c;
+      }
+    };
+    for (uint32_t r = len / 2; r-- > 0;) sift(r, len);
+    for (uint32_t end = len - 1; end > 0; end--) {
+      swap(0, end);
+      sift(0, end);
+    }
+  }
+}
+
 // Candidates already in the cache: for each of the *n unique candidates (in
 // canonical order) a binary search of the cache's canonical records;
 // flag[i] = 1 for a candidate the cache does not hold.  A candidate the
@@ -735,6 +801,10 @@ void launch_known(const uint32_t *cand, const uint32_t *n, uint32_t *cache, cons
 void launch_gather_records(const uint32_t *rec, const uint32_t *vals, const uint32_t *n,
                            uint32_t *out, uint32_t cap, Counters *ctr, cudaStream_t s) {
   emrt::note_launch(), k_gather_records<<<kPrimGrid * 4, 256, 0, s>>>(rec, vals, n, out, cap, ctr);
+}
+void launch_sort_runs(KeyW<4> *keys, uint32_t *vals, const uint32_t *n, int low_bits,
+                      cudaStream_t s) {
+  emrt::note_launch(), k_sort_runs<<<kPrimGrid * 4, 256, 0, s>>>(keys, vals, n, low_bits);
 }
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s) { emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(p, v); }
 

@@ -160,6 +160,10 @@ void launch_known(const uint32_t *cand, const uint32_t *n, uint32_t *cache, cons
 // out[k] = rec[vals[k]] for k < min(*n, cap); ERR_PATH_OVERFLOW when *n > cap.
 void launch_gather_records(const uint32_t *rec, const uint32_t *vals, const uint32_t *n,
                            uint32_t *out, uint32_t cap, Counters *ctr, cudaStream_t s);
+// Completes a sort of (keys, vals)[0, *n) that is ordered by the key bits
+// from low_bits up: runs equal in those bits are sorted by the whole key.
+void launch_sort_runs(KeyW<4> *keys, uint32_t *vals, const uint32_t *n, int low_bits,
+                      cudaStream_t s);
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
 
 // Backward tracing.  out[i] = pos[ids[i]] for i < n (source points of the
