@@ -141,8 +141,6 @@ cudaError_t ensure_cand(emrt_scene_s *s, uint64_t need) {
   return cudaSuccess;
 }
 
-constexpr int kDedupPasses = 4;
-
 // Sort + unique of records [0, *n) of `src` (capacity cap) into s->uniq;
 // unique count in ctr->n_unique.
 void dedup(emrt_scene_s *s, const uint32_t *src, const uint32_t *n, uint32_t cap, KeyLayout kl,

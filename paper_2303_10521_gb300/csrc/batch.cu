@@ -178,10 +178,13 @@ void enqueue(emrt_batch_s *b, int variant, bool sort_rays, cudaStream_t st) {
   }
   // deduplicate (keys carry the scene), accept, scatter to each scene
   launch_path_keys(b->cand, &c->n_cand, b->cand_cap, b->kl, b->keys[0], b->vals[0], &c->n_eff, st);
+  const int passes = (b->kl.total + 7) / 8;
+  const int first = passes > kDedupPasses + 1 ? passes - kDedupPasses : 0;
   bool alt = radix_sort<4>(&c->n_eff, b->keys[0], b->vals[0], b->keys[1], b->vals[1], b->kl.total,
-                           b->hist, st, b->cand_cap);
+                           b->hist, st, b->cand_cap, first);
   KeyW<4> *ks = b->keys[alt ? 1 : 0];
   uint32_t *vs = b->vals[alt ? 1 : 0];
+  if (first) launch_sort_runs(ks, vs, &c->n_eff, 8 * first, st);
   launch_heads(ks, &c->n_eff, b->head, st);
   exclusive_scan(&c->n_eff, b->head, b->pos, &c->n_unique, b->partial, st);
   launch_unique(b->cand, ks, vs, b->head, b->pos, &c->n_eff, b->uniq, st);

@@ -160,6 +160,10 @@ void launch_known(const uint32_t *cand, const uint32_t *n, uint32_t *cache, cons
 // out[k] = rec[vals[k]] for k < min(*n, cap); ERR_PATH_OVERFLOW when *n > cap.
 void launch_gather_records(const uint32_t *rec, const uint32_t *vals, const uint32_t *n,
                            uint32_t *out, uint32_t cap, Counters *ctr, cudaStream_t s);
+// Deduplication sorts run radix passes over the top kDedupPasses bytes of
+// the canonical key only and then launch_sort_runs (measured on the city:
+// 4 passes 0.11 ms, 5 0.13, 6 0.15, all 11 0.22).
+constexpr int kDedupPasses = 4;
 // Completes a sort of (keys, vals)[0, *n) that is ordered by the key bits
 // from low_bits up: runs equal in those bits are sorted by the whole key.
 void launch_sort_runs(KeyW<4> *keys, uint32_t *vals, const uint32_t *n, int low_bits,
