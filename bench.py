@@ -560,10 +560,12 @@ def main():
     torch.cuda.synchronize()
     e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fev = [torch.cuda.Event(enable_timing=True) for _ in range(nc)]
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nc)]
     e4.record(stream)
     for k in range(1, nc):
         fev[k - 1].record(stream)
         g.update(cframes[k])
+        sev[k][0].record(stream)
         if REFRESH and k % REFRESH == 0:
             g.rediscover(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc,
                          revalidate=True)
@@ -572,6 +574,7 @@ def main():
                          breadth_first=bf, static_cache=use_sc, revalidate=True)
         else:
             g.revalidate(cache)
+        sev[k][1].record(stream)
         chs[:] = g.channels(cache, sc.freqs, outs=chs)
         cached_rx.append(chs[0].rx[:, 0].clone())
         g.sync()
@@ -580,6 +583,12 @@ def main():
     torch.cuda.synchronize()
     cached_ms = max_over_ranks(e4.elapsed_time(e5), dev)
     cached_frame_ms = [fev[k].elapsed_time(fev[k + 1]) for k in range(nc - 1)]
+    # per-frame stages (CUDA events): update, revalidation + rediscovery,
+    # fields at both frequencies + the accuracy record + the sync
+    stage_rows = [(fev[k - 1].elapsed_time(sev[k][0]), sev[k][0].elapsed_time(sev[k][1]),
+                   sev[k][1].elapsed_time(fev[k])) for k in range(1, nc)]
+    cached_stages = {name: float(np.median([r[q] for r in stage_rows]))
+                     for q, name in enumerate(("update", "revalidate_rediscover", "fields_and_sync"))}
     cached_val = job_throughput(n_rx * (nc - 1), ws, cached_ms)
 
     def agree(pa, pb):
@@ -669,6 +678,7 @@ def main():
     accuracy = {
         "frames": nc, "refresh_every": REFRESH, "static_cache": use_sc, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
         "frame_ms_median": float(np.median(cached_frame_ms)),
+        "stage_ms_median": cached_stages,
         "frame_ms_max": float(np.max(cached_frame_ms)),
         "frame_ms": [round(x, 2) for x in cached_frame_ms],
         "reference": "plain retrace of the same frame with N = 1e7 rays per Tx",
