@@ -90,7 +90,8 @@ typedef enum {
                                emrt_stats reports the required sizes         */
   EMRT_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                 */
   EMRT_ERR_STATE = 6,       /* call order violated (e.g. trace before update) */
-  EMRT_ERR_DEVICE = 7       /* kernel-raised error (traversal stack overflow) */
+  EMRT_ERR_DEVICE = 7       /* kernel-raised error (traversal stack overflow,
+                               a non-finite field) */
 } emrt_status;
 
 typedef struct emrt_scene_s *emrt_scene;

@@ -821,7 +821,7 @@ emrt_status emrt_channel_multi(emrt_scene s, const emrt_paths *paths, const emrt
   }
   if (!s->updated) return EMRT_ERR_STATE;
   launch_channel(geom(s), matview(m), paths->rec, paths->count, paths->capacity, fs, s->n_tx,
-                 s->n_rx, tx_power_w, (cudaStream_t)stream);
+                 s->n_rx, tx_power_w, s->ctr, (cudaStream_t)stream);
   CK(cudaGetLastError());
   return EMRT_OK;
 }
@@ -986,7 +986,7 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
   emrt_status r = s->sticky;
   s->sticky = EMRT_OK;
   if (r != EMRT_OK) return r;
-  if (h.err & ERR_STACK) return EMRT_ERR_DEVICE;
+  if (h.err & (ERR_STACK | ERR_NONFINITE)) return EMRT_ERR_DEVICE;
   if (h.err & ERR_UNSORTED) return EMRT_ERR_INVALID_ARG;
   if (h.err & (ERR_CAND_OVERFLOW | ERR_PATH_OVERFLOW | ERR_RAY_OVERFLOW)) return EMRT_ERR_CAPACITY;
   return EMRT_OK;

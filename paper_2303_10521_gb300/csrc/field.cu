@@ -287,7 +287,7 @@ __device__ inline void pick_freq(const FreqSet &fs, double &freq, double *&out) 
 // Field of every path at the frequency blockIdx.y of fs (frequencies share
 // the launch, so a frame's ~1e4 paths at two frequencies fill twice the warps).
 __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32_t *n, uint32_t cap,
-                        FreqSet fs) {
+                        FreqSet fs, Counters *ctr) {
   double freq;
   double *out;
   pick_freq(fs, freq, out);
@@ -327,6 +327,8 @@ __global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32
     o.y = a.im;
     o.z = L / kC;
     o.w = -(freq / kC) * dL;
+    if (!isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z) || !isfinite(o.w))
+      atomicOr(&ctr->err, ERR_NONFINITE);
     reinterpret_cast<double4_32a *>(out)[i] = o;
   }
 }
@@ -611,11 +613,11 @@ void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, u
 
 void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                     uint32_t cap, const FreqSet &fs, uint32_t n_tx, uint32_t n_rx,
-                    double tx_power_w, cudaStream_t s) {
+                    double tx_power_w, Counters *ctr, cudaStream_t s) {
   // one warp per block: the ~1e4 paths of a frame spread over every SM's
   // FP64 units (128-thread blocks left half the SMs idle; measured 4 % of
   // the channel stage); one grid row per frequency
-  emrt::note_launch(), k_field<<<dim3(152 * 16, fs.n), 32, 0, s>>>(g, m, rec, n, cap, fs);
+  emrt::note_launch(), k_field<<<dim3(152 * 16, fs.n), 32, 0, s>>>(g, m, rec, n, cap, fs, ctr);
   uint32_t np = n_tx * n_rx;
   for (uint32_t q = 0; q < fs.n; q++) cudaMemsetAsync(fs.pair_out[q], 0, sizeof(double) * 8 * np, s);
   emrt::note_launch(), k_pair_seq<<<dim3(152 * 8, fs.n), 256, 0, s>>>(rec, n, cap, n_tx, n_rx, fs);

@@ -9,6 +9,11 @@ struct MatView {
   uint32_t n_mat, const_gamma;
 };
 
+// device error bit raised by the field kernel when a path's amplitude,
+// delay or Doppler is not finite (NaN or infinite material parameters or
+// positions); a bit of Counters::err beside the ones of common.cuh
+constexpr uint32_t ERR_NONFINITE = 32u;
+
 // Frequencies of one channel evaluation and their outputs (rx_out[q] may be
 // null).
 constexpr uint32_t kMaxFreq = 8;
@@ -22,7 +27,7 @@ struct FreqSet {
 // per-receiver powers; records must be in canonical order
 void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                     uint32_t cap, const FreqSet &fs, uint32_t n_tx, uint32_t n_rx,
-                    double tx_power_w, cudaStream_t s);
+                    double tx_power_w, Counters *ctr, cudaStream_t s);
 // adjoint: gradients w.r.t. eps_r [n_mat], sigma [n_mat], tx position
 // [n_tx][3]; `partial` is per-path scratch of cap * (3 + 2 EMRT_MAX_DEPTH)
 // doubles (tangent contributions), reduced per parameter in a fixed order

@@ -85,6 +85,28 @@ class ChannelResult:
     rx: torch.Tensor     # [n_rx, 2] float64 W: coherent, incoherent
 
 
+def rx_dbm(ch: ChannelResult, coherent: bool = True) -> np.ndarray:
+    """Received power per receiver in dBm from a channel result (coherent
+    per Tx and summed over Tx, or the fully incoherent sum); -inf where no
+    path arrives."""
+    p = ch.rx[:, 0 if coherent else 1].detach().to("cpu", torch.float64).numpy()
+    with np.errstate(divide="ignore"):
+        return 10.0 * np.log10(p) + 30.0
+
+
+def save_heatmap(path: str, ch: ChannelResult, rx_pos=None, coherent: bool = True):
+    """Per-receiver received power as a .npy heat-map array: float64
+    [n_rx, 4] (x, y, z, dBm) when rx_pos ([n_rx, 3]) is given, else [n_rx]
+    dBm."""
+    dbm = rx_dbm(ch, coherent)
+    if rx_pos is not None:
+        xyz = np.asarray(rx_pos.detach().cpu() if torch.is_tensor(rx_pos) else rx_pos,
+                         dtype=np.float64).reshape(-1, 3)
+        np.save(path, np.concatenate([xyz, dbm[:, None]], axis=1))
+    else:
+        np.save(path, dbm)
+
+
 class Scene:
     """A scene on one GPU: static geometry (with its BVH), per-frame
     dynamic state, scratch buffers.  Wraps ``emrt_scene``."""

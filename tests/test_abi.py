@@ -60,3 +60,23 @@ def test_paths_checkpoint_roundtrip(tmp_path):
     e = engine.Paths(4, "cpu")
     e.save(f)
     assert engine.Paths.load(f, "cpu").n() == 0
+
+
+def test_heatmap_export(tmp_path):
+    """Per-receiver dBm heat-map arrays: 1 W is 30 dBm, 1 mW 0 dBm, no path
+    -inf; with positions the file holds (x, y, z, dBm) rows."""
+    import torch
+    from paper_2303_10521_gb300 import engine
+    rx = torch.tensor([[1.0, 2.0], [1e-3, 0.5], [0.0, 0.0]], dtype=torch.float64)
+    ch = engine.ChannelResult(torch.zeros(1, 4, dtype=torch.float64),
+                              torch.zeros(1, 3, 8, dtype=torch.float64), rx)
+    d = engine.rx_dbm(ch)
+    assert d[0] == 30.0 and abs(d[1]) < 1e-12 and d[2] == -np.inf
+    assert abs(engine.rx_dbm(ch, coherent=False)[0] - (30.0 + 10 * np.log10(2.0))) < 1e-12
+    pos = np.array([[0, 0, 1.5], [10, 0, 1.5], [0, 20, 1.6]])
+    f = str(tmp_path / "heat.npy")
+    engine.save_heatmap(f, ch, rx_pos=pos)
+    h = np.load(f)
+    assert h.shape == (3, 4) and np.array_equal(h[:, :3], pos) and h[0, 3] == 30.0
+    engine.save_heatmap(f, ch)
+    assert np.load(f).shape == (3,)

@@ -397,6 +397,16 @@ def test_invalid_arguments(engine):
     with pytest.raises(E.N.EmrtError) as ei:
         g.channels(paths, [3.5e9, -1.0])
     assert ei.value.code == 1
+    # a non-finite material parameter surfaces as a device error at the next
+    # sync (host-injected fault); the error word is cleared by that sync
+    nan_eps = g.eps_r.clone()
+    nan_eps.fill_(float("nan"))
+    g.channel(paths, 3.5e9, eps_r=nan_eps)
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.sync()
+    assert ei.value.code == 7
+    g.channel(paths, 3.5e9)
+    g.sync()
     # rediscovery does not keep rejected candidates
     p = E.N.TraceParams(2, 20_000, 0, 1, 0, E.N.TRACE_KEEP_REJECTED)
     pc = paths.c()
