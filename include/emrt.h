@@ -260,10 +260,12 @@ emrt_status emrt_channel(emrt_scene sc, const emrt_paths *paths,
                          double tx_power_w, emrt_channel_out *out,
                          emrt_stream s);
 
-/* emrt_channel at n_freq frequencies (1..8) in one pass: outs[q] receives
- * the results at freq_hz[q] (host array), exactly as emrt_channel would (the
- * frequencies share each launch, one grid row per frequency).
- * outs[q].rx_out may be NULL. */
+/* emrt_channel (Sec. III-C, Eq. 3 generalised; Table III statistics) at
+ * n_freq frequencies (1..8) in one pass: outs[q] receives the results at
+ * freq_hz[q] (host array), exactly as emrt_channel would (the frequencies
+ * share each launch, one grid row per frequency).  outs[q].rx_out may be
+ * NULL.  A non-finite result (e.g. NaN material parameters) makes the next
+ * emrt_sync return EMRT_ERR_DEVICE; other errors as emrt_channel. */
 emrt_status emrt_channel_multi(emrt_scene sc, const emrt_paths *paths, const emrt_materials *m,
                                const double *freq_hz, uint32_t n_freq, double tx_power_w,
                                emrt_channel_out *outs, emrt_stream s);
