@@ -254,7 +254,9 @@ typedef struct {
 
 /* Field of every path in `paths` at frequency freq_hz (Sec. III-C, Eq. 3
  * generalised to moving endpoints and reflectors; Table III statistics).
- * Paths must be canonical (sorted). */
+ * Paths must be canonical (sorted).  Invalid arguments (null outputs,
+ * freq_hz <= 0) return EMRT_ERR_INVALID_ARG; a non-finite result (e.g. NaN
+ * material parameters) makes the next emrt_sync return EMRT_ERR_DEVICE. */
 emrt_status emrt_channel(emrt_scene sc, const emrt_paths *paths,
                          const emrt_materials *m, double freq_hz,
                          double tx_power_w, emrt_channel_out *out,
