@@ -1,0 +1,80 @@
+"""Host logic of bench.py, on the CPU: the clock samples kept for the timed
+region, the gating of the committed ncu figures by the kernel-source hash,
+and the whole-job throughput."""
+import datetime
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _row(t, sm, reasons=("Not Active",) * 4):
+    ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return ", ".join([ts, "0", str(sm), "2070", "900.00", "0x0"] + list(reasons))
+
+
+def _clocks(tmp_path, rows, t0, t1):
+    c = bench.Clocks.__new__(bench.Clocks)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    c.f = open(c.path, "a")
+
+    class P:  # a finished sampler process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c.proc = P()
+    c.t0, c.t1 = t0, t1
+    return c
+
+
+def test_clock_samples_inside_the_region(tmp_path):
+    t0 = 1_700_000_000.0
+    rows = [_row(t0 - 0.5, 1400), _row(t0 + 0.01, 2070), _row(t0 + 0.03, 2060),
+            _row(t0 + 0.5, 1500, ("Not Active", "Not Active", "Not Active", "Active"))]
+    out = _clocks(tmp_path, rows, t0, t0 + 0.05).stop()
+    assert out["samples"] == 2 and out["sm_mhz"] == 2065.0
+    assert out["reasons"] == [] and out["sm_max_mhz"] == 2070.0
+
+
+def test_clock_nearest_sample_for_a_short_region(tmp_path):
+    t0 = 1_700_000_000.0
+    rows = [_row(t0 - 0.2, 1300),
+            _row(t0 + 0.06, 2070, ("Active", "Not Active", "Not Active", "Not Active"))]
+    out = _clocks(tmp_path, rows, t0, t0 + 0.01).stop()
+    assert out["samples"] == 1 and out["sm_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_slowdown"]
+
+
+def test_ncu_figures_only_for_the_hashed_sources(tmp_path, monkeypatch):
+    f = tmp_path / "traffic.txt"
+    f.write_text(f"# comment\nkernel_hash = {bench.kernel_hash('depth_first')}\n"
+                 "dram_bytes_per_segment = 8.5\nissue_active_pct = 77.0\n")
+    monkeypatch.setitem(bench.TRAFFIC_FILE, "depth_first", str(f))
+    assert bench.ncu_summary("depth_first") == {"dram_bytes_per_segment": 8.5,
+                                                 "issue_active_pct": 77.0}
+    f.write_text("kernel_hash = 0000000000000000\ndram_bytes_per_segment = 8.5\n")
+    assert bench.ncu_summary("depth_first") is None
+
+
+def test_committed_traffic_files_parse():
+    for form in ("depth_first", "breadth_first"):
+        kv = {}
+        for line in open(bench.TRAFFIC_FILE[form]):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        assert len(kv["kernel_hash"]) == 16
+        assert float(kv["dram_bytes_per_segment"]) > 0
+
+
+def test_job_throughput():
+    assert bench.job_throughput(1000, 4, 500.0) == pytest.approx(8000.0)
