@@ -578,3 +578,131 @@ def test_refresh_schedule_rule_by_hand():
     due, _, _ = oracle.refresh_schedule(o3, st, np.array([[1, 1, 0]], np.uint8), f, 0.5, dt,
                                         10.0, 50)
     assert 0 not in due.tolist() and 2 not in due.tolist()
+
+
+# ---------------------------------------------------------------------------
+# received power, the loss of the differentiable-field workload and its
+# central finite differences (Sec. IV: transmit power and received power;
+# gradient over a frozen path topology)
+# ---------------------------------------------------------------------------
+def _hand_paths():
+    """Five hand-made paths on 2 Tx x 3 Rx with amplitudes chosen so that the
+    coherent per-Tx sum, the incoherent sum over Tx and a fully coherent sum
+    over Tx all differ."""
+    p = np.zeros(5, oracle.PATH_DTYPE)
+    p["tx"] = [0, 0, 1, 0, 0]
+    p["rx"] = [0, 0, 0, 1, 1]
+    a = np.array([1e-3, 1e-3, 1e-3, 2e-3, -2e-3], complex)
+    return p, a
+
+
+def test_rx_power_coherent_per_tx_incoherent_over_tx():
+    p, a = _hand_paths()
+    z = np.zeros(len(p))
+    st = oracle.reduce(p, a, z, z, 2, 3)
+    coh, inc = oracle.rx_power(st, 0.25)
+    # rx 0: tx 0 adds 1e-3 + 1e-3 in phase (|h|^2 = 4e-6), tx 1 adds 1e-6
+    # as power; rx 1: the two tx-0 paths cancel; rx 2 has no path
+    assert coh == pytest.approx([0.25 * 5e-6, 0.0, 0.0], rel=1e-14, abs=1e-30)
+    assert inc == pytest.approx([0.25 * 3e-6, 0.25 * 8e-6, 0.0], rel=1e-14, abs=1e-30)
+    # the same from a hand-written statistics array (Re h, Im h, sum |a|^2)
+    st2 = np.zeros((2, 3, 8))
+    st2[0, 0, :3] = (2e-3, 0.0, 2e-6)
+    st2[1, 0, :3] = (0.0, 1e-3, 1e-6)
+    st2[0, 2, :3] = (3e-3, -4e-3, 1e-5)
+    coh2, inc2 = oracle.rx_power(st2, 2.0)
+    assert coh2 == pytest.approx([2.0 * 5e-6, 0.0, 2.0 * 25e-6], rel=1e-14)
+    assert inc2 == pytest.approx([2.0 * 3e-6, 0.0, 2.0 * 1e-5], rel=1e-14)
+
+
+def test_power_loss_closed_form():
+    p, a = _hand_paths()
+    # add a third receiver reached by tx 1 only
+    p = np.concatenate([p, p[:1]])
+    p["tx"][-1], p["rx"][-1] = 1, 2
+    a = np.concatenate([a, [1e-3 * np.exp(0.7j)]])
+    pt = 0.25
+    target = np.array([-31.0, 0.0, -40.0])
+    mask = np.array([True, False, True])
+    got = oracle.power_loss(p, a, 2, 3, pt, target, mask)
+    p0 = pt * (4e-6 + 1e-6)      # coherent within tx 0, power of tx 1 added
+    p2 = pt * 1e-6
+    dbm = [10 * math.log10(p0 * 1e3), 10 * math.log10(p2 * 1e3)]
+    expect = (dbm[0] + 31.0) ** 2 + (dbm[1] + 40.0) ** 2
+    assert got == pytest.approx(expect, rel=1e-13)
+    # receiver 1 (its two paths cancel: zero power) is masked out and adds
+    # nothing; unmasking a receiver with power adds its term
+    mask2 = np.array([True, False, False])
+    assert oracle.power_loss(p, a, 2, 3, pt, target, mask2) == pytest.approx(
+        (dbm[0] + 31.0) ** 2, rel=1e-13)
+
+
+def _wall_los_scene(f):
+    wall = S.rect_wall_x(20.0, -100, 100, -50, 50, facing=-1)
+    tx, rx = (0.0, 0.0, 5.0), (3.0, 40.0, 5.0)
+    return _one(tx, rx, [wall], [S.MAT_CONCRETE], freq=f)
+
+
+def test_fd_gradient_materials_single_wall_closed_form():
+    """LoS + one s-polarised wall bounce, coherently summed: the derivative
+    of |h|^2 w.r.t. the wall's eps_r and sigma follows from
+    dGamma_s / d eps_c = -cos(theta) / (s (cos(theta) + s)^2),
+    s = sqrt(eps_c - sin^2 theta), eps_c = eps_r - j sigma / (2 pi f eps0)."""
+    f = 28e9
+    sc, o = _wall_los_scene(f)
+    fr = sc.frame(0)
+    paths = oracle.enumerate_paths(o, 1)
+    assert sorted(paths["depth"].tolist()) == [0, 1]
+    eps, sig = S.material_table()[:2]
+    e0 = 8.8541878128e-12
+    k = 2 * math.pi * f / C
+    d1 = math.hypot(3.0, 40.0)
+    d2 = math.hypot(40.0, 37.0)
+    ct = 37.0 / d2
+    ec = complex(eps[S.MAT_CONCRETE], -sig[S.MAT_CONCRETE] / (2 * math.pi * f * e0))
+    s = np.sqrt(ec - (1 - ct * ct))
+    gs = (ct - s) / (ct + s)
+    dg = -ct / (s * (ct + s) ** 2)
+    a_los = _lam(f) / (4 * math.pi * d1) * np.exp(-1j * k * d1)
+    a_w = gs * _lam(f) / (4 * math.pi * d2) * np.exp(-1j * k * d2)
+    h = a_los + a_w
+    pt = 10.0 ** ((50 - 30) / 10)  # 50 dBm
+    dbm = 10 * math.log10(pt * abs(h) ** 2 * 1e3)
+    target = np.array([dbm - 3.0])
+    mask = np.array([True])
+    # d loss / d|h|^2 = 2 (dBm - target) 10 / (ln 10 |h|^2)
+    dl = 2 * 3.0 * 10 / (math.log(10) * abs(h) ** 2)
+    dh_deps = a_w / gs * dg
+    dh_dsig = dh_deps * (-1j / (2 * math.pi * f * e0))
+    g_eps_cf = dl * 2 * (np.conj(h) * dh_deps).real
+    g_sig_cf = dl * 2 * (np.conj(h) * dh_dsig).real
+    # the coherent sum matters: the incoherent one gives another value
+    g_inc = dl * 2 * (np.conj(a_w) * dh_deps).real * abs(h) ** 2 / (abs(a_los) ** 2 + abs(a_w) ** 2)
+    assert abs(g_inc - g_eps_cf) > 0.05 * abs(g_eps_cf)
+    g_eps, g_sig, g_tx = oracle.fd_gradient(sc, fr, paths, f, pt, target, mask)
+    assert g_eps[S.MAT_CONCRETE] == pytest.approx(g_eps_cf, rel=1e-6)
+    assert g_sig[S.MAT_CONCRETE] == pytest.approx(g_sig_cf, rel=1e-6)
+    # materials the paths never meet have zero gradient (no other term)
+    others = np.arange(len(eps)) != S.MAT_CONCRETE
+    assert np.all(g_eps[others] == 0.0) and np.all(g_sig[others] == 0.0)
+
+
+def test_fd_gradient_tx_position_friis():
+    """LoS only: P = P_t (lambda / 4 pi d)^2, so d loss / d Tx =
+    2 (dBm - target) (-20 / (d ln 10)) (Tx - Rx) / d; no material enters."""
+    f = 3.5e9
+    tx, rx = (1.0, -2.0, 10.0), (401.25, 37.5, 1.5)
+    sc, o = _one(tx, rx, freq=f)
+    fr = sc.frame(0)
+    paths = oracle.enumerate_paths(o, 2)
+    assert len(paths) == 1
+    t = np.float32(tx).astype(float)
+    r = np.float32(rx).astype(float)
+    d = np.linalg.norm(t - r)
+    pt = 100.0
+    dbm = 10 * math.log10(pt * (_lam(f) / (4 * math.pi * d)) ** 2 * 1e3)
+    target = np.array([dbm + 2.0])
+    g_eps, g_sig, g_tx = oracle.fd_gradient(sc, fr, paths, f, pt, target, np.array([True]))
+    expect = 2 * (-2.0) * (-20 / (d * math.log(10))) * (t - r) / d
+    assert g_tx[0] == pytest.approx(expect, rel=1e-6)
+    assert np.all(g_eps == 0.0) and np.all(g_sig == 0.0)
