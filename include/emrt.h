@@ -275,7 +275,9 @@ emrt_status emrt_channel_multi(emrt_scene sc, const emrt_paths *paths, const emr
 /* Adjoint of emrt_channel's coherent sums over a frozen path topology:
  * given dloss_dh [n_tx][n_rx][2] (d loss / d Re h, d loss / d Im h),
  * accumulates (overwrites) grad_eps [n_mat], grad_sigma [n_mat] and
- * grad_tx [n_tx][3].  Reflection points are recomputed, not stored. */
+ * grad_tx [n_tx][3].  Reflection points are recomputed, not stored.  A
+ * non-finite amplitude or tangent (e.g. NaN material parameters) makes the
+ * next emrt_sync return EMRT_ERR_DEVICE. */
 emrt_status emrt_channel_backward(emrt_scene sc, const emrt_paths *paths,
                                   const emrt_materials *m, double freq_hz,
                                   const double *dloss_dh, double *grad_eps,
@@ -283,10 +285,11 @@ emrt_status emrt_channel_backward(emrt_scene sc, const emrt_paths *paths,
                                   emrt_stream s);
 
 /* Allocation-free variant of emrt_channel_backward, for callers that must
- * not allocate device memory after set-up: code running inside a CUDA graph
- * capture (cudaMalloc is not allowed there), applications whose device memory
- * is owned by another allocator or capped, and real-time loops that
- * pre-allocate once.  The paper has no counterpart; it is a library service.
+ * not allocate device memory after set-up: applications whose device memory
+ * is owned by another allocator or capped (a cudaMalloc there can fail or
+ * break the owner's accounting), and real-time loops that pre-allocate once
+ * so that no call can stall in the allocator.  The paper has no counterpart;
+ * it is a library service.
  *
  * Same arguments and results as emrt_channel_backward, but the per-path
  * tangent scratch lives in a fixed device array compiled into libemrt.so
@@ -297,13 +300,17 @@ emrt_status emrt_channel_backward(emrt_scene sc, const emrt_paths *paths,
  *  - paths->capacity must be <= EMRT_NOALLOC_MAX_PATHS, otherwise
  *    EMRT_ERR_INVALID_ARG is returned and nothing is launched;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins;
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture
+ *    begins.  cudaDeviceReset ends the library's use of that device (it also
+ *    frees every scene there): the kept address is not looked up again;
  *  - every call on a device shares the one array: calls whose kernels overlap
  *    on the GPU (different streams without ordering) race and give wrong
  *    gradients; order them on one stream.  The array keeps the last call's
  *    contents; each call overwrites every entry it reads, so no clearing is
- *    needed. */
+ *    needed;
+ *  - a non-finite amplitude or tangent makes the next emrt_sync return
+ *    EMRT_ERR_DEVICE, as for emrt_channel_backward. */
 #define EMRT_NOALLOC_MAX_PATHS 65536u
 emrt_status emrt_channel_backward_noalloc(emrt_scene sc, const emrt_paths *paths,
                                           const emrt_materials *m, double freq_hz,

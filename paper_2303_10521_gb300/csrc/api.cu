@@ -700,7 +700,13 @@ emrt_status emrt_rediscover(emrt_scene s, const emrt_trace_params *p, emrt_paths
     CK(cudaEventRecord(s->ev_side[0], s->side[0]));
     after = s->ev_side[0];
   }
-  return run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, cache, st, cache, after);
+  const emrt_status r =
+      run_trace(s, p, count, geom(s), s->n_tx, 24, false, nullptr, cache, st, cache, after);
+  // whatever run_trace returned (an early return skips its merge, which
+  // waits for the revalidation), the caller's stream is ordered after the
+  // side stream's writes to the cache
+  if (after) cudaStreamWaitEvent(st, after, 0);
+  return r;
 }
 
 emrt_status emrt_trace_backward(emrt_scene s, const emrt_trace_params *p, const uint32_t *rx_ids,
@@ -838,7 +844,7 @@ emrt_status emrt_channel_backward(emrt_scene s, const emrt_paths *paths, const e
   CK(grow(&s->contrib, s->contrib_cap, std::max<uint64_t>(need, s->contrib_cap)));
   GeomView g = geom(s);
   launch_field_adjoint(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, dloss_dh,
-                       s->n_rx, s->contrib, grad_eps, grad_sigma, grad_tx, st);
+                       s->n_rx, s->contrib, grad_eps, grad_sigma, grad_tx, s->ctr, st);
   CK(cudaGetLastError());
   return EMRT_OK;
 }
@@ -893,7 +899,7 @@ emrt_status emrt_channel_backward_noalloc(emrt_scene s, const emrt_paths *paths,
   cudaStream_t st = (cudaStream_t)stream;
   GeomView g = geom(s);
   launch_field_adjoint(g, matview(m), paths->rec, paths->count, paths->capacity, freq_hz, dloss_dh,
-                       s->n_rx, scratch, grad_eps, grad_sigma, grad_tx, st);
+                       s->n_rx, scratch, grad_eps, grad_sigma, grad_tx, s->ctr, st);
   CK(cudaGetLastError());
   return EMRT_OK;
 }

@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_field_tangents(GeomView g, MatVie
                                                               const uint32_t *rec, const uint32_t *n,
                                                               uint32_t cap, double freq,
                                                               const double *dloss_dh, uint32_t n_rx,
-                                                              double *contrib) {
+                                                              double *contrib, Counters *ctr) {
   using D = Dual<kTan>;
   uint32_t cnt = min(*n, cap);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
@@ -435,7 +435,14 @@ __global__ void __launch_bounds__(kAdjBlock) k_field_tangents(GeomView g, MatVie
     path_field<D>(P, txp, rxp, epsr, sig, gam, m.const_gamma != 0, freq, a, L, kh);
     const double *gh = dloss_dh + 2ull * (tx * n_rx + rx);
     double gx = gh[0], gy = gh[1];
-    for (int t = 0; t < kTan; t++) c[t] = gx * a.re.d[t] + gy * a.im.d[t];
+    bool finite = isfinite(a.re.v) && isfinite(a.im.v);
+    for (int t = 0; t < kTan; t++) {
+      c[t] = gx * a.re.d[t] + gy * a.im.d[t];
+      finite = finite && isfinite(c[t]);
+    }
+    // a non-finite amplitude or tangent (e.g. NaN material parameters) is
+    // reported as for the forward field
+    if (!finite) atomicOr(&ctr->err, ERR_NONFINITE);
   }
 }
 
@@ -632,9 +639,9 @@ int adjoint_grid() { return 152 * 4; }
 void launch_field_adjoint(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                           uint32_t cap, double freq, const double *dloss_dh, uint32_t n_rx,
                           double *contrib, double *grad_eps, double *grad_sigma, double *grad_tx,
-                          cudaStream_t s) {
+                          Counters *ctr, cudaStream_t s) {
   emrt::note_launch(), k_field_tangents<<<adjoint_grid(), kAdjBlock, 0, s>>>(g, m, rec, n, cap, freq, dloss_dh, n_rx,
-                                                        contrib);
+                                                        contrib, ctr);
   uint32_t n_par = 2 * m.n_mat + 3 * g.n_tx;
   emrt::note_launch(), k_grad_reduce<<<n_par, 256, 0, s>>>(g, m, rec, n, cap, contrib, grad_eps, grad_sigma, grad_tx);
 }

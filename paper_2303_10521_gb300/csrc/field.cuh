@@ -30,11 +30,12 @@ void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uin
                     double tx_power_w, Counters *ctr, cudaStream_t s);
 // adjoint: gradients w.r.t. eps_r [n_mat], sigma [n_mat], tx position
 // [n_tx][3]; `partial` is per-path scratch of cap * (3 + 2 EMRT_MAX_DEPTH)
-// doubles (tangent contributions), reduced per parameter in a fixed order
+// doubles (tangent contributions), reduced per parameter in a fixed order; a
+// non-finite amplitude or tangent raises ERR_NONFINITE in ctr->err
 void launch_field_adjoint(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                           uint32_t cap, double freq, const double *dloss_dh, uint32_t n_rx,
                           double *partial, double *grad_eps, double *grad_sigma, double *grad_tx,
-                          cudaStream_t s);
+                          Counters *ctr, cudaStream_t s);
 int adjoint_grid();
 // Eq. 1 (normalised autocovariance of |h| over frames) and Eq. 2 (coherence
 // time) of Sec. III-B

@@ -73,3 +73,36 @@ def compare_field(a_g, tau_g, fd_g, a_o, tau_o, fd_o, amp_rel=1e-4, phase_rad=1e
                 tau=float(tau_err.max(initial=0)), fd=float(fd_err.max(initial=0)),
                 ok=bool((amp_err <= amp_rel).all() and (ph_err <= phase_rad).all()
                         and (tau_err <= 1e-12).all() and (fd_err <= 1e-9).all()))
+
+
+def compare_accepted(os_, gpu_acc, orc_cands, ray_marg):
+    """Parity of a final accepted path set (discovery + acceptance) with the
+    oracle's on the same rays: the oracle deduplicates its candidates and
+    accepts them itself.  An oracle-accepted path may be missing on the GPU
+    only if the oracle flags its discovery or acceptance as marginal; a GPU
+    path the oracle does not accept must be flagged: by the GPU (reflection
+    point within the margin), by the oracle's acceptance margin, or by the
+    oracle's discovery margin of the ray that found it.  Returns a summary
+    dict."""
+    ou = oracle.dedup(orc_cands)
+    acc_o, marg_o = oracle.validate(os_, ou)
+    okeys = keys(ou)
+    o_acc = {k: (int(f) != 0 or int(m) != 0)
+             for k, a, f, m in zip(okeys, acc_o, ou["flag"], marg_o) if a}
+    o_cand_marg = {k: int(m) != 0 for k, a, m in zip(okeys, acc_o, marg_o) if not a}
+    gkeys = keys(gpu_acc)
+    gset = set(gkeys)
+    missing = [k for k, flagged in o_acc.items() if not flagged and k not in gset]
+    extra_bad, extra_flagged = [], 0
+    for k, p in zip(gkeys, gpu_acc):
+        if k in o_acc:
+            continue
+        flagged = bool(int(p["flag"]) & 2) or o_cand_marg.get(k, False) or \
+            ray_marg[int(p["tx"]), int(p["ray"])] <= int(p["depth"])
+        if flagged:
+            extra_flagged += 1
+        else:
+            extra_bad.append(k)
+    return dict(n_gpu=len(gset), n_orc=len(o_acc), missing=missing, extra_bad=extra_bad,
+                extra_flagged=extra_flagged,
+                missing_flagged=sum(1 for k, f in o_acc.items() if f and k not in gset))

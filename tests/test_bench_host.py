@@ -78,3 +78,31 @@ def test_committed_traffic_files_parse():
 
 def test_job_throughput():
     assert bench.job_throughput(1000, 4, 500.0) == pytest.approx(8000.0)
+
+
+def test_traversal_roofline_issue_bound():
+    ncu = {"warp_inst_per_segment": 140.0, "dram_bytes_per_segment": 9.0, "l2_hit_pct": 82.0}
+    clk = {"sm_mhz": 2000.0}
+    r = bench.traversal_roofline(2.0e11, 8.0e7, 0.01, 6800.0, "measured", ncu, clk)
+    issue_peak = 152 * 4 * 2000e6 / 1e9
+    assert r["bound"] == "issue" and r["peak"] == pytest.approx(issue_peak)
+    assert r["achieved"] == pytest.approx(140.0 * 8.0e7 / 0.01 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / issue_peak)
+    assert r["traffic"] == pytest.approx(9.0 * 8.0e7)
+    assert r["dram"]["frac"] == pytest.approx(9.0 * 8.0e7 / 0.01 / 1e9 / 6800.0)
+    assert r["algorithmic"]["frac_of_hbm_peak"] == pytest.approx(2.0e11 / 0.01 / 1e9 / 6800.0)
+    assert r["ncu"] == {"l2_hit_pct": 82.0}
+    # without a capture of this kernel source: no issue or DRAM figure
+    r = bench.traversal_roofline(2.0e11, 8.0e7, 0.01, 6800.0, "measured", None, None)
+    assert r["frac"] is None and r["traffic"] is None and r["dram"]["frac"] is None
+    assert "maximum SM clock" in r["peak_source"]
+
+
+def test_cpu_baseline_scales_only_the_ray_work():
+    from paper_2303_10521_gb300 import scenes
+    sc = scenes.toy_scene(seed=0)
+    r = bench.run_cpu_baseline(sc, sc.frame(0), stride=50)
+    frame_s = r["setup_s"] + 50 * (r["discovery_s"] + r["accept_field_s"])
+    assert r["frame_s_extrapolated"] == pytest.approx(frame_s)
+    assert r["value"] == pytest.approx(len(sc.frame(0).rx_pos) / frame_s)
+    assert r["segments"] > 0 and r["s_per_segment"] > 0

@@ -120,22 +120,26 @@ def test_toy_scene_full_parity(engine):
     assert rx[:, 1] == pytest.approx(inc, rel=1e-6)
 
 
-@pytest.mark.parametrize("stride,offset", [(97, 5), (211, 0)])
-def test_district_subsample_parity(engine, stride, offset):
+@pytest.mark.parametrize("stride,offset,form", [(97, 5, "depth_first"), (211, 0, "depth_first"),
+                                                (131, 3, "wide_bvh")])
+def test_district_subsample_parity(engine, stride, offset, form):
     """District (400 buildings, 200 vehicles, 1000 Rx, 2 Tx, K = 3) on a
-    strided subset of the 1M rays, traced identically on both sides."""
+    strided subset of the 1M rays, traced identically on both sides; the
+    default depth-first discovery and the breadth-first discovery through the
+    4-wide BVH."""
     sc = S.district_scene(seed=0)
     fr = sc.frame(0)
     g = _gpu(engine, sc)
     o = oracle.OracleScene(sc, fr)
-    allc = g.trace(stride=stride, offset=offset, keep_rejected=True)
+    kw = dict(wide_bvh=True) if form == "wide_bvh" else {}
+    allc = g.trace(stride=stride, offset=offset, keep_rejected=True, **kw)
     gu = rec_to_paths(allc.records())
     cands, ray_marg, _ = oracle.trace(o, sc.n_rays, sc.max_depth, offset=offset, stride=stride)
     rc = compare_candidates(gu, cands, ray_marg)
     assert not rc["missing"] and not rc["extra_bad"], {k: v for k, v in rc.items() if k != "bad"}
     ra = compare_acceptance(o, gu)
     assert ra["n_diff_unflagged"] == 0, ra
-    acc = g.trace(stride=stride, offset=offset)
+    acc = g.trace(stride=stride, offset=offset, **kw)
     ga = rec_to_paths(acc.records())
     a, tau, fd, _ = _field(g, acc, 3.5e9)
     rf = compare_field(a, tau, fd, *oracle.field(o, ga, 3.5e9))
@@ -406,6 +410,15 @@ def test_invalid_arguments(engine):
         g.sync()
     assert ei.value.code == 7
     g.channel(paths, 3.5e9)
+    g.sync()
+    # the same for the adjoint: NaN materials give NaN tangents, reported at
+    # the next sync
+    cot = torch.ones((g.n_tx, g.n_rx, 2), dtype=torch.float64, device=g.device)
+    g.channel_backward(paths, 3.5e9, cot, eps_r=nan_eps)
+    with pytest.raises(E.N.EmrtError) as ei:
+        g.sync()
+    assert ei.value.code == 7
+    g.channel_backward(paths, 3.5e9, cot)
     g.sync()
     # rediscovery does not keep rejected candidates
     p = E.N.TraceParams(2, 20_000, 0, 1, 0, E.N.TRACE_KEEP_REJECTED)

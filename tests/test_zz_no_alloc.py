@@ -1,8 +1,8 @@
 """The allocation-free adjoint entry point, emrt_channel_backward_noalloc.
 
-Some callers cannot call cudaMalloc once they are running: code inside a CUDA
-graph capture, applications whose device memory belongs to another allocator,
-and real-time loops that allocate everything up front.  For them the library
+Some callers cannot call cudaMalloc once they are running: applications whose
+device memory belongs to another allocator or is capped, and real-time loops
+that allocate everything up front so that no call stalls in the allocator.  For them the library
 offers this variant of emrt_channel_backward, whose scratch is a fixed device
 array inside libemrt.so.  This test calls it through the C-ABI, twice in a
 row, and checks both results against the existing entry point; it also checks
@@ -64,3 +64,13 @@ def test_noalloc_adjoint_matches_allocating_entry_point():
         _grads(lib, lib.emrt_channel_backward_noalloc, g, big, mats, freq, cot,
                "emrt_channel_backward_noalloc")
     assert ei.value.code == 1
+
+    # NaN materials: reported at the next sync like the allocating adjoint
+    nan_eps = torch.full_like(g.eps_r, float("nan"))  # kept alive across the call
+    nan = g._mat(eps_r=nan_eps)
+    _grads(lib, lib.emrt_channel_backward_noalloc, g, paths, nan, freq, cot,
+           "emrt_channel_backward_noalloc")
+    with pytest.raises(N.EmrtError) as ei:
+        g.sync()
+    assert ei.value.code == 7
+    g.sync()
