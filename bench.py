@@ -737,7 +737,8 @@ def main():
         rec = float(np.minimum(pa[m], pb[m]).sum() / max(pb[m].sum(), 1e-300))
         with np.errstate(divide="ignore"):
             db = np.abs(10 * np.log10(pa[m]) - 10 * np.log10(pb[m]))
-        return rec, float(np.mean(db > 0.5)), float(np.median(db))
+        return (rec, float(np.mean(db > 0.5)), float(np.median(db)),
+                float(np.percentile(db, 95)))
 
     acc_c, acc_p = [], []
     plain_ref = {}
@@ -813,7 +814,8 @@ def main():
             "accuracy_vs_plain": {"power_recall_mean": float(acc_r[:, 0].mean()),
                                   "power_recall_min": float(acc_r[:, 0].min()),
                                   "frac_rx_over_0p5db": float(acc_r[:, 1].mean()),
-                                  "median_abs_db": float(acc_r[:, 2].mean())}
+                                  "median_abs_db": float(acc_r[:, 2].mean()),
+                                  "p95_abs_db": float(acc_r[:, 3].mean())}
             if len(acc_r) else None}
     accuracy = {
         "frames": nc, "refresh_every": REFRESH, "static_cache": use_sc, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
@@ -822,17 +824,23 @@ def main():
         "frame_ms_max": float(np.max(cached_frame_ms)),
         "frame_ms": [round(x, 2) for x in cached_frame_ms],
         "reference": "plain retrace of the same frame with N = 1e7 rays per Tx",
+        "criterion": "equal accuracy = the cached method differs from the plain retrace of "
+                     "the same frame no more than the plain method with another ray set of "
+                     "similar density (0.9 N) does: power recall and the per-receiver |dB| "
+                     "percentiles of the two rows side by side",
         "cached": {"power_recall_mean": float(acc_c[:, 0].mean()),
                    "power_recall_min": float(acc_c[:, 0].min()),
                    "frac_rx_over_0p5db": float(acc_c[:, 1].mean()),
-                   "median_abs_db": float(acc_c[:, 2].mean())},
+                   "median_abs_db": float(acc_c[:, 2].mean()),
+                   "p95_abs_db": float(acc_c[:, 3].mean())},
         "plain_other_ray_set": {"note": "plain retrace with 0.9 N rays (another Fibonacci set of "
                                         "similar density) against the same reference: the "
                                         "ray-set variability of the plain method itself",
                                 "power_recall_mean": float(acc_p[:, 0].mean()),
                                 "power_recall_min": float(acc_p[:, 0].min()),
                                 "frac_rx_over_0p5db": float(acc_p[:, 1].mean()),
-                                "median_abs_db": float(acc_p[:, 2].mean())}}
+                                "median_abs_db": float(acc_p[:, 2].mean()),
+                                "p95_abs_db": float(acc_p[:, 3].mean())}}
 
     batched = None if args.no_batched else run_batched(engine, scenes, dev)
 
