@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--breadth-first", action="store_true",
                     help="plain frames: trace bounce by bounce (k_bounce) instead of "
                          "depth-first chains (k_walk)")
+    ap.add_argument("--wide-bvh", action="store_true",
+                    help="plain frames: static closest hits through the compressed 8-wide "
+                         "BVH instead of the binary one")
     ap.add_argument("--no-sort-rays", action="store_true",
                     help="breadth-first form: do not reorder reflected rays between bounces")
     ap.add_argument("--per-rx-frames", type=int, default=30,
@@ -511,9 +514,11 @@ def main():
     bf = args.breadth_first
     form = "breadth_first" if bf else "depth_first"
 
+    wide = args.wide_bvh
+
     def step(k, stats):
         g.update(frames[k])
-        g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf)
+        g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf, wide_bvh=wide)
         chs[:] = g.channels(out, sc.freqs, outs=chs)
         st = g.sync()
         stats.append(st)
@@ -551,7 +556,8 @@ def main():
     byt = 0
     for s in stats:
         sg = s["segments"]
-        byt += 64 * (s["node_visits"] + s["dyn_node_visits"] + s["rx_node_visits"])
+        byt += (80 if wide else 64) * s["node_visits"]
+        byt += 64 * (s["dyn_node_visits"] + s["rx_node_visits"])
         byt += 48 * s["tri_tests"] + 32 * s["box_tests"] + 16 * s["rx_tests"]
         if bf:
             byt += 16 * sg[0] + 48 * sum(sg[1:])      # ray reads
@@ -627,11 +633,54 @@ def main():
         "mrays_per_s": sum(sum(s["segments"]) for s in stats_c) /
                        (sum(s["bounce_ms"] for s in stats_c) / 1e3) / 1e6}
 
+    # ---------------- the same frames through the compressed 8-wide BVH
+    # (8-bit child boxes): records checked against the binary tree's
+    def step_w(k, st_list):
+        g.update(frames[k])
+        g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf, wide_bvh=not wide)
+        chs[:] = g.channels(out, sc.freqs, outs=chs)
+        st_list.append(g.sync())
+
+    for k in range(args.warmup):
+        step_w(k, [])
+    torch.cuda.synchronize()
+    stats_w = []
+    e8, e9 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e8.record(stream)
+    for k in range(args.warmup, total):
+        step_w(k, stats_w)
+    e9.record(stream)
+    torch.cuda.synchronize()
+    w_ms = max_over_ranks(e8.elapsed_time(e9), dev)
+    rec_w = out.records()
+
+    def tree_row(st_list, node_bytes):
+        sg = sum(sum(x["segments"]) for x in st_list)
+        tm = sum(x["bounce_ms"] for x in st_list)
+        nv = sum(x["node_visits"] for x in st_list) / sg
+        tt = sum(x["tri_tests"] for x in st_list) / sg
+        return {"mrays_per_s": sg / (tm / 1e3) / 1e6, "traversal_ms": tm / len(st_list),
+                "static_node_fetches_per_segment": nv, "tri_tests_per_segment": tt,
+                "node_bytes_per_segment": node_bytes * nv,
+                "static_bytes_per_segment": node_bytes * nv + 48 * tt}
+
+    g.trace_async(out, stride=rs, sort_rays=sort_rays, breadth_first=bf, wide_bvh=wide)
+    g.sync()
+    other = tree_row(stats_w, 64 if wide else 80)
+    other.update({"receiver_frames_per_s": job_throughput(n_rx * args.steps, ws, w_ms),
+                  "ms_per_step": w_ms / args.steps,
+                  "identical_to_plain": bool(np.array_equal(rec_w, out.records()))})
+    trees = {"binary_sah" if not wide else "compressed_8wide": tree_row(stats, 80 if wide else 64),
+             "compressed_8wide" if not wide else "binary_sah": other,
+             "note": "static closest-hit traversal of the plain frames through each tree; "
+                     "binary: 64 B per node (2 child boxes), compressed 8-wide: 80 B per node "
+                     "(8 child boxes of 8-bit grid coordinates)"}
+
     if args.profile:
         if rank == 0:
             last = stats[-1]
         print(json.dumps({"profile": True, "ms_per_step": t_ms / args.steps,
-                          "static_cache": static_cache,
+                          "static_cache": static_cache, "bvh_forms": trees,
                           "mrays_per_s": mrays, "roofline": roofline,
                           "per_segment": {k: last[k] / max(1, sum(last["segments"])) for k in
                                           ("node_visits", "tri_tests", "dyn_node_visits",
@@ -863,6 +912,7 @@ def main():
             "mrays_per_s": mrays,
             "receiver_frames_per_s_cached": cached_val,
             "plain_with_static_cache": static_cache,
+            "bvh_forms": trees,
             "cached": accuracy,
             "cached_per_receiver": per_rx,
             "batched": batched,

@@ -58,10 +58,12 @@ extern "C" {
 #define EMRT_TRACE_SORT_RAYS 0x2u      /* breadth-first form: reorder rays
                                           between bounces by origin cell and
                                           direction bin                       */
-#define EMRT_TRACE_WIDE_BVH 0x4u       /* breadth-first form through the 4-wide
-                                          BVH of the static geometry (same
-                                          results; on GB300 the binary BVH is
-                                          faster for the city scenes measured) */
+#define EMRT_TRACE_WIDE_BVH 0x4u       /* static closest hits through the
+                                          compressed 8-wide BVH (8-bit child
+                                          boxes on a per-node grid, 80 B per
+                                          node; Sec. II-A BVH) instead of the
+                                          binary one, in either traversal
+                                          form; same results bit for bit   */
 #define EMRT_TRACE_STATIC_CACHE 0x8u   /* keep the static-geometry closest hit of
                                           every ray segment between calls (see
                                           emrt_trace); same results bit for bit */

@@ -1,6 +1,7 @@
 // C-ABI of libemrt.so: scene lifetime, argument checks, scratch management
 // and the order of kernel launches for each entry point.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -231,19 +232,33 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = grow(&s->partial, c, kPrimGrid + 1))) return fail(e); c = 0;
   cudaMemsetAsync(s->ctr, 0, sizeof(Counters), st);
   bbox_of_tris(d->tri_xyz, s->T, s->bbox, st);
+  // leaf-box pad of every tree of the scene: 2^-21 x the largest static
+  // coordinate (at least 1 m), see BVHBuf::pad
+  float pad = 4.76837158e-7f;
+  if (s->T) {
+    float4 bb[2];
+    if ((e = cudaMemcpyAsync(bb, s->bbox, sizeof(bb), cudaMemcpyDeviceToHost, st))) return fail(e);
+    if ((e = cudaStreamSynchronize(st))) return fail(e);
+    float m = 1.f;
+    for (float v : {bb[0].x, bb[0].y, bb[0].z, bb[1].x, bb[1].y, bb[1].z})
+      if (std::isfinite(v)) m = std::max(m, std::fabs(v));
+    pad = 4.76837158e-7f * m;
+  }
   if ((e = bvh_alloc(s->stat, PRIM_TRI, std::max(s->T, 2u)))) return fail(e);
+  s->stat.pad = pad;
   // static geometry: binned-SAH tree (built once); the LBVH if the SAH tree
   // would be deeper than the traversal stack
-  if (bvh_build_tris_sah(s->stat, d->tri_xyz, d->tri_face, s->T, st) != cudaSuccess) {
+  if (bvh_build_tris_sah(s->stat, d->tri_xyz, d->tri_face, s->T, s->Fs, st) != cudaSuccess) {
     cudaGetLastError();
     if ((e = bvh_build_tris(s->stat, d->tri_xyz, d->tri_face, s->T, s->bbox, s->hist, st)))
       return fail(e);
   }
-  if ((e = bvh4_collapse(s->stat, st))) return fail(e);
+  if ((e = bvh8_build(s->stat, st))) return fail(e);
   if ((e = bvh_alloc(s->dyn, PRIM_BOX, std::max(s->V, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->rxb, PRIM_POINT, std::max(s->max_rx, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->txb, PRIM_POINT, std::max(s->max_tx, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->mix, PRIM_BOX, std::max(s->V + s->max_rx, 2u)))) return fail(e);
+  s->dyn.pad = s->rxb.pad = s->txb.pad = s->mix.pad = pad;
   if ((e = grow(&s->mix_lo, c, s->V + s->max_rx))) return fail(e); c = 0;
   if ((e = grow(&s->mix_hi, c, s->V + s->max_rx))) return fail(e); c = 0;
   uint32_t V1 = std::max(s->V, 1u);
@@ -467,9 +482,8 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
   // the static-hit cache form runs in the chain walker alone: no per-bounce
   // ray buffers or sorts
   const bool cache = (p->flags & EMRT_TRACE_STATIC_CACHE) && !backward;
-  // depth-first chains unless the breadth-first form is asked for (the
-  // 4-wide BVH is traversed by the breadth-first kernel only)
-  const bool walk = !cache && !(p->flags & (EMRT_TRACE_BREADTH_FIRST | EMRT_TRACE_WIDE_BVH));
+  // depth-first chains unless the breadth-first form is asked for
+  const bool walk = !cache && !(p->flags & EMRT_TRACE_BREADTH_FIRST);
   if (!cache && !walk && p->max_depth > 0 && nrays > s->ray_cap) {
     cudaFree(s->rays[0]);
     cudaFree(s->rays[1]);
@@ -575,7 +589,7 @@ emrt_status run_trace(emrt_scene_s *s, const emrt_trace_params *p, uint64_t coun
     L.K = (int)p->max_depth;
     L.jbits = jbits;
     cudaEventRecord(s->evb[0], st);
-    launch_walk(L, st);
+    launch_walk(L, st, (p->flags & EMRT_TRACE_WIDE_BVH) != 0);
     cudaEventRecord(s->evb[1], st);
     nev = 1;
   }

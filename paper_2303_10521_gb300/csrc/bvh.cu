@@ -179,7 +179,7 @@ __device__ inline Box prim_box(const float4 *prims, uint32_t g) {
 // leaf_parent 0xFFFFFFFF.
 template <int KIND, bool MULTI = false>
 __global__ void k_refit(const float4 *prims, uint32_t n, float4 *nodes, const uint32_t *leaf_parent,
-                        uint32_t *flags) {
+                        uint32_t *flags, float pad) {
   uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n || n < 2) return;
   if (MULTI && leaf_parent[g] == 0xffffffffu) return;
@@ -194,6 +194,8 @@ __global__ void k_refit(const float4 *prims, uint32_t n, float4 *nodes, const ui
       b.hi = make_float3(fmaxf(b.hi.x, c.hi.x), fmaxf(b.hi.y, c.hi.y), fmaxf(b.hi.z, c.hi.z));
     }
   }
+  b.lo = make_float3(b.lo.x - pad, b.lo.y - pad, b.lo.z - pad);
+  b.hi = make_float3(b.hi.x + pad, b.hi.y + pad, b.hi.z + pad);
   for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
     int p = code >> 1, side = code & 1;
     float4 *np = nodes + 4ll * p;
@@ -232,19 +234,73 @@ __device__ inline float half_area(const Child &c) {
   return dx * dy + dy * dz + dz * dx;
 }
 
-// one thread per 4-wide node of the current level
-__global__ void k_collapse(const float4 *bn, const uint32_t *in_bin, const uint32_t *in_dst,
-                           const uint32_t *n_in, float4 *out4, uint32_t *out_bin,
-                           uint32_t *out_dst, uint32_t *n_out, uint32_t *n_alloc) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// ---------------------------------------------------------------------------
+// Compressed 8-wide BVH: the quantised wide-BVH family of Ylitie, Karras and
+// Laine (HPG 2017), restated.  A node holds up to 8 children of the binary
+// tree (the inner child of largest surface area is opened until 8 are
+// gathered); their boxes are 8-bit offsets on a per-node grid -- origin P,
+// a power-of-two quantum per axis -- so a node is 80 B for 8 child boxes
+// where the binary tree spends 64 B on 2.  Children are placed in the 8
+// slots so that a ray whose direction has sign pattern o (bit a set when
+// axis a is negative) meets them roughly near to far when it visits slots
+// o ^ 0, o ^ 1, ..., o ^ 7: slot s receives, greedily, the child with the
+// smallest offset from the node centre along the diagonal of sign pattern s.
+// Node layout (5 x uint4):
+//   [0] P.x, P.y, P.z (float bits), e_x | e_y << 8 | e_z << 16 | imask << 24
+//       (e: biased exponent of the quantum, 2^(e - 127); imask: inner slots)
+//   [1] first child node | lmask << 24 (leaf slots), first triangle,
+//       leaf meta of slots 0-3 and 4-7 (byte: offset | (count - 1) << 5)
+//   [2] x: low bytes of slots 0-3, 4-7, high bytes of slots 0-3, 4-7
+//   [3] y, [4] z, as [2]
+// Inner children of a node are consecutive nodes in slot order; the
+// triangles of its leaf children are consecutive in the wide tree's own
+// triangle array.  Every quantised box contains its child's box grown by two
+// quanta (and the quantum is at least one float ulp of the node's
+// coordinates), which covers the rounding of the traversal's decode.
+constexpr int kWideQuantPad = 2;
+
+__device__ inline float wide_ulp(float a) {
+  const float m = fabsf(a);
+  return m > 0.f ? nextafterf(m, 3.4e38f) - m : 1.17549435e-38f;
+}
+
+// Quantises one axis of up to 8 child boxes on the node's grid: returns the
+// biased exponent and the origin; q_lo/q_hi receive the grid coordinates.
+__device__ inline uint32_t wide_axis(const float *clo, const float *chi, int cnt, float lo, float hi,
+                                     float &P, uint8_t *q_lo, uint8_t *q_hi) {
+  const double ext = (double)hi - (double)lo;
+  const float u = fmaxf(wide_ulp(lo), wide_ulp(hi));
+  int e = ilogb(u);  // the quantum is at least one ulp of the coordinates
+  while (e < 127 && ldexp(1.0, e) * (255.0 - 2.0 * kWideQuantPad - 1.0) < ext) e++;
+  for (;; e++) {
+    const double q = ldexp(1.0, e);
+    P = (float)((double)lo - kWideQuantPad * q);
+    bool ok = true;
+    for (int k = 0; k < cnt && ok; k++) {
+      const double a = floor(((double)clo[k] - (double)P) / q) - kWideQuantPad;
+      const double b = ceil(((double)chi[k] - (double)P) / q) + kWideQuantPad;
+      if (b > 255.0 || b < 0.0) { ok = false; break; }
+      q_lo[k] = (uint8_t)(a < 0.0 ? 0.0 : a);
+      q_hi[k] = (uint8_t)b;
+    }
+    if (ok || e >= 127) return (uint32_t)(e + 127);  // e >= 127: degenerate input
+  }
+}
+
+// one thread per wide node of the current level
+__global__ void k_wide8(const float4 *bn, const float4 *bprims, uint32_t leaf_bits,
+                        const uint32_t *in_bin, const uint32_t *in_dst, const uint32_t *n_in,
+                        uint4 *out8, float4 *tris8, uint32_t *out_bin, uint32_t *out_dst,
+                        uint32_t *n_out, uint32_t *n_alloc, uint32_t *t_alloc) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *n_in) return;
-  int b = (int)in_bin[i];
-  uint32_t dst = in_dst[i];
-  Child c[4];
+  const int b = (int)in_bin[i];
+  const uint32_t dst = in_dst[i];
+  Child c[8];
   int cnt = 2;
   c[0] = child_of(bn, b, 0);
   c[1] = child_of(bn, b, 1);
-  while (cnt < 4) {
+  while (cnt < 8) {
     int best = -1;
     float ba = -1.f;
     for (int k = 0; k < cnt; k++)
@@ -253,34 +309,96 @@ __global__ void k_collapse(const float4 *bn, const uint32_t *in_bin, const uint3
         best = k;
       }
     if (best < 0) break;
-    int nb = c[best].code;
+    const int nb = c[best].code;
     c[best] = child_of(bn, nb, 0);
     c[cnt++] = child_of(bn, nb, 1);
   }
-  float4 *o = out4 + 8ull * dst;
-  float v[6][4];
-  int codes[4] = {0, 0, 0, 0};
-  for (int k = 0; k < 4; k++) {
-    bool ok = k < cnt;
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  for (int k = 0; k < cnt; k++)
     for (int a = 0; a < 3; a++) {
-      v[2 * a][k] = ok ? c[k].lo[a] : 0.f;
-      v[2 * a + 1][k] = ok ? c[k].hi[a] : 0.f;
+      lo[a] = fminf(lo[a], c[k].lo[a]);
+      hi[a] = fmaxf(hi[a], c[k].hi[a]);
     }
-    if (!ok) continue;
-    if (c[k].code < 0) {
-      codes[k] = c[k].code;
+  // slots: greedily the (slot, child) pair of smallest offset along the
+  // slot's diagonal
+  int in_slot[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  uint32_t used_child = 0;
+  for (int round = 0; round < cnt; round++) {
+    float bc = 3.4e38f;
+    int bs = -1, bk = -1;
+    for (int sl = 0; sl < 8; sl++) {
+      if (in_slot[sl] >= 0) continue;
+      for (int k = 0; k < cnt; k++) {
+        if (used_child >> k & 1u) continue;
+        float d = 0.f;
+        for (int a = 0; a < 3; a++) {
+          const float off = (c[k].lo[a] + c[k].hi[a]) - (lo[a] + hi[a]);
+          d += (sl >> a & 1) ? -off : off;
+        }
+        if (d < bc) { bc = d; bs = sl; bk = k; }
+      }
+    }
+    in_slot[bs] = bk;
+    used_child |= 1u << bk;
+  }
+  uint32_t n_inner = 0, n_tris = 0;
+  for (int k = 0; k < cnt; k++) {
+    if (c[k].code >= 0) {
+      n_inner++;
     } else {
-      uint32_t ni = atomicAdd(n_alloc, 1u);
-      uint32_t slot = atomicAdd(n_out, 1u);
-      out_bin[slot] = (uint32_t)c[k].code;
-      out_dst[slot] = ni;
-      codes[k] = (int)ni;
+      const uint32_t lc = (uint32_t)(~c[k].code);
+      n_tris += leaf_bits ? (lc & 3u) + 1u : 1u;
     }
   }
-  for (int r = 0; r < 6; r++) o[r] = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
-  o[6] = make_float4(__int_as_float(codes[0]), __int_as_float(codes[1]), __int_as_float(codes[2]),
-                     __int_as_float(codes[3]));
-  o[7] = make_float4(__int_as_float(cnt), 0.f, 0.f, 0.f);
+  const uint32_t child_base = n_inner ? atomicAdd(n_alloc, n_inner) : 0u;
+  const uint32_t tri_base = n_tris ? atomicAdd(t_alloc, n_tris) : 0u;
+  uint32_t imask = 0, lmask = 0, meta[2] = {0u, 0u}, rank = 0, off = 0;
+  float clo[3][8], chi[3][8];
+  int ord = 0;
+  for (int sl = 0; sl < 8; sl++) {
+    const int k = in_slot[sl];
+    if (k < 0) continue;
+    for (int a = 0; a < 3; a++) {
+      clo[a][ord] = c[k].lo[a];
+      chi[a][ord] = c[k].hi[a];
+    }
+    ord++;
+    if (c[k].code >= 0) {
+      imask |= 1u << sl;
+      const uint32_t q = atomicAdd(n_out, 1u);
+      out_bin[q] = (uint32_t)c[k].code;
+      out_dst[q] = child_base + rank++;
+    } else {
+      const uint32_t lc = (uint32_t)(~c[k].code);
+      const uint32_t first = leaf_bits ? lc >> 2 : lc, n = leaf_bits ? (lc & 3u) + 1u : 1u;
+      for (uint32_t t = 0; t < n; t++)
+        for (int w = 0; w < 3; w++)
+          tris8[3ull * (tri_base + off + t) + w] = bprims[3ull * (first + t) + w];
+      lmask |= 1u << sl;
+      meta[sl >> 2] |= (off | (n - 1u) << 5) << (8 * (sl & 3));
+      off += n;
+    }
+  }
+  uint8_t qlo[3][8] = {}, qhi[3][8] = {};
+  float P[3];
+  uint32_t ex[3];
+  for (int a = 0; a < 3; a++) ex[a] = wide_axis(clo[a], chi[a], cnt, lo[a], hi[a], P[a], qlo[a], qhi[a]);
+  // bytes back from child order to slot order
+  uint32_t w[3][4] = {};
+  ord = 0;
+  for (int sl = 0; sl < 8; sl++) {
+    if (in_slot[sl] < 0) continue;
+    for (int a = 0; a < 3; a++) {
+      w[a][sl >> 2] |= (uint32_t)qlo[a][ord] << (8 * (sl & 3));
+      w[a][2 + (sl >> 2)] |= (uint32_t)qhi[a][ord] << (8 * (sl & 3));
+    }
+    ord++;
+  }
+  uint4 *o = out8 + 5ull * dst;
+  o[0] = make_uint4(__float_as_uint(P[0]), __float_as_uint(P[1]), __float_as_uint(P[2]),
+                    ex[0] | ex[1] << 8 | ex[2] << 16 | imask << 24);
+  o[1] = make_uint4(child_base | lmask << 24, tri_base, meta[0], meta[1]);
+  for (int a = 0; a < 3; a++) o[2 + a] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
 }
 
 __device__ inline uint32_t f2o(float f) {
@@ -338,7 +456,7 @@ cudaError_t finish_build(BVHBuf &b, cudaStream_t s) {
   if (n >= 2) {
     emrt::note_launch(), k_hierarchy<<<ceil_div(n - 1, 256), 256, 0, s>>>(b.keys, (int)n, b.nodes, b.leaf_parent);
     cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
-    emrt::note_launch(), k_refit<KIND><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+    emrt::note_launch(), k_refit<KIND><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags, b.pad);
   }
   return cudaGetLastError();
 }
@@ -361,7 +479,8 @@ cudaError_t sort_codes(BVHBuf &b, uint32_t *hist, cudaStream_t s) {
 
 BVHView BVHBuf::view() const {
   BVHView v;
-  v.nodes4 = nodes4;
+  v.nodes8 = nodes8;
+  v.prims8 = prims8;
   v.nodes = nodes;
   v.prims = prims;
   v.root = n >= 2 ? 0 : ~0;
@@ -392,9 +511,11 @@ cudaError_t bvh_alloc(BVHBuf &b, PrimKind kind, uint32_t cap) {
 void bvh_free(BVHBuf &b) {
   cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.leaf_parent); cudaFree(b.flags);
   cudaFree(b.keys); cudaFree(b.keys2); cudaFree(b.idx); cudaFree(b.idx2); cudaFree(b.d_n);
-  cudaFree(b.nodes4);
-  b.nodes4 = nullptr;
-  b.n4 = 0;
+  cudaFree(b.nodes8);
+  cudaFree(b.prims8);
+  b.nodes8 = nullptr;
+  b.prims8 = nullptr;
+  b.n8 = 0;
   b.nodes = b.prims = nullptr;
   b.leaf_parent = b.flags = b.idx = b.idx2 = b.d_n = nullptr;
   b.keys = b.keys2 = nullptr;
@@ -427,7 +548,7 @@ cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaS
   emrt::note_launch(), k_move_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, b.prims);
   if (n >= 2) {
     cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
-    emrt::note_launch(), k_refit<PRIM_BOX><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+    emrt::note_launch(), k_refit<PRIM_BOX><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags, b.pad);
   }
   return cudaGetLastError();
 }
@@ -453,9 +574,11 @@ namespace {
 constexpr int kSahBins = 64;
 constexpr int kSahBlock = 256;
 constexpr int kSahMaxDepth = 60;  // levels; the traversal stack holds 64 entries
-// ranges of up to this many triangles become leaves (1-4; on the city 1 is
-// fastest: 4-triangle leaves cut node visits 29.0 -> 25.7 per segment but
-// raised triangle tests 2.5 -> 6.7 and the traversal 16.0 -> 18.8 ms)
+// ranges of up to this many clusters become leaves (a cluster is one
+// triangle or the two triangles of a quad face; on the city one cluster per
+// leaf is fastest: leaves of up to 4 triangles chosen by the SAH cut node
+// visits 29.0 -> 25.7 per segment but raised triangle tests 2.5 -> 6.7 and
+// the traversal 16.0 -> 18.8 ms)
 constexpr uint32_t kSahLeafMax = 1;
 
 struct SahTask {
@@ -476,6 +599,92 @@ __global__ void k_tri_bounds(const float *t, uint32_t n, float4 *cen, float4 *lo
   cen[i] = make_float4((v[0] + v[3] + v[6]) * (1.f / 3.f), (v[1] + v[4] + v[7]) * (1.f / 3.f),
                        (v[2] + v[5] + v[8]) * (1.f / 3.f), 0.f);
   perm[i] = i;
+}
+
+// Leaf clusters of the SAH build: the two triangles of a face made of exactly
+// two (a planar quad -- a wall, a ground tile -- whose triangles share one
+// bounding box) form one leaf, every other triangle a leaf of its own.  The
+// quad's two tests are those the two single-triangle leaves would get
+// whenever its box is entered; the inner node that split them is saved.
+__global__ void k_face_tris(const uint32_t *tri_face, uint32_t n, uint32_t n_faces,
+                            uint32_t *cnt, uint32_t *first, uint32_t *last) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t f = tri_face[i];
+  if (f >= n_faces) return;
+  atomicAdd(&cnt[f], 1u);
+  atomicMin(&first[f], i);
+  atomicMax(&last[f], i);
+}
+
+__device__ inline bool quad_face(const uint32_t *tri_face, uint32_t n_faces, const uint32_t *cnt,
+                                 uint32_t i, uint32_t &f) {
+  f = tri_face[i];
+  return f < n_faces && cnt[f] == 2u;
+}
+
+// flag[i] = 1 when triangle i starts a cluster (quad clustering on or off)
+__global__ void k_cluster_flags(const uint32_t *tri_face, uint32_t n, uint32_t n_faces,
+                                const uint32_t *cnt, const uint32_t *first, int quads,
+                                uint32_t *flag) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t f;
+  flag[i] = (!quads || !quad_face(tri_face, n_faces, cnt, i, f) || first[f] == i) ? 1u : 0u;
+}
+
+// cluster list (first triangle, second triangle or ~0) and the SAH inputs:
+// box of the cluster, centroid = mean of its triangles' centroids
+__global__ void k_cluster_bounds(const float *t, const uint32_t *tri_face, uint32_t n,
+                                 uint32_t n_faces, const uint32_t *cnt, const uint32_t *last,
+                                 int quads, const uint32_t *flag, const uint32_t *pos,
+                                 uint2 *cl, float4 *cen, float4 *lo, float4 *hi, uint32_t *perm) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !flag[i]) return;
+  uint32_t f;
+  const uint32_t j = (quads && quad_face(tri_face, n_faces, cnt, i, f)) ? last[f] : 0xffffffffu;
+  const uint32_t c = pos[i];
+  cl[c] = make_uint2(i, j);
+  float a[3] = {3.4e38f, 3.4e38f, 3.4e38f}, b[3] = {-3.4e38f, -3.4e38f, -3.4e38f}, m[3] = {0, 0, 0};
+  const uint32_t tt[2] = {i, j};
+  const int k = j == 0xffffffffu ? 1 : 2;
+  for (int q = 0; q < k; q++) {
+    const float *v = t + 9ull * tt[q];
+    for (int d = 0; d < 3; d++) {
+      a[d] = fminf(a[d], fminf(v[d], fminf(v[3 + d], v[6 + d])));
+      b[d] = fmaxf(b[d], fmaxf(v[d], fmaxf(v[3 + d], v[6 + d])));
+      m[d] += (v[d] + v[3 + d] + v[6 + d]) * (1.f / 3.f);
+    }
+  }
+  const float w = 1.f / (float)k;
+  lo[c] = make_float4(a[0], a[1], a[2], 0.f);
+  hi[c] = make_float4(b[0], b[1], b[2], 0.f);
+  cen[c] = make_float4(m[0] * w, m[1] * w, m[2] * w, 0.f);
+  perm[c] = c;
+}
+
+__global__ void k_cluster_sizes(const uint2 *cl, const uint32_t *perm, uint32_t nc, uint32_t *sz) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nc) sz[p] = cl[perm[p]].y == 0xffffffffu ? 1u : 2u;
+}
+
+// triangle order of the leaves, triangle leaf parents and the final leaf
+// codes ~(first triangle << 2 | count - 1)
+__global__ void k_cluster_expand(const uint2 *cl, const uint32_t *perm, const uint32_t *tstart,
+                                 const uint32_t *lp_cl, uint32_t nc, uint32_t *tri_idx,
+                                 uint32_t *leaf_parent, float4 *nodes) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nc) return;
+  const uint2 c = cl[perm[p]];
+  const uint32_t t0 = tstart[p], lp = lp_cl[p];
+  const uint32_t k = c.y == 0xffffffffu ? 1u : 2u;
+  tri_idx[t0] = c.x;
+  leaf_parent[t0] = lp;
+  if (k == 2u) {
+    tri_idx[t0 + 1] = c.y;
+    leaf_parent[t0 + 1] = 0xffffffffu;
+  }
+  reinterpret_cast<int *>(nodes + 4ll * (lp >> 1) + 3)[lp & 1u] = ~(int)(t0 << 2 | (k - 1u));
 }
 
 __device__ inline float sel(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -701,23 +910,47 @@ __global__ void __launch_bounds__(kSahBlock) k_sah_level(
 }  // namespace
 
 cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_face, uint32_t n,
-                               cudaStream_t s) {
+                               uint32_t n_faces, cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
   cudaError_t e;
   float4 *cen = nullptr, *lo = nullptr, *hi = nullptr;
-  uint32_t *tmp = nullptr, *ctr = nullptr;
+  uint32_t *tmp = nullptr, *ctr = nullptr, *fbuf = nullptr, *cbuf = nullptr;
+  uint2 *cl = nullptr;
   SahTask *tasks[2] = {nullptr, nullptr};
+  const uint32_t nf = n_faces ? n_faces : 1u;
   if ((e = cudaMalloc(&cen, sizeof(float4) * n))) return e;
   if ((e = cudaMalloc(&lo, sizeof(float4) * n))) return e;
   if ((e = cudaMalloc(&hi, sizeof(float4) * n))) return e;
   if ((e = cudaMalloc(&tmp, sizeof(uint32_t) * n))) return e;
   if ((e = cudaMalloc(&tasks[0], sizeof(SahTask) * (n / 2 + 2)))) return e;
   if ((e = cudaMalloc(&tasks[1], sizeof(SahTask) * (n / 2 + 2)))) return e;
-  if ((e = cudaMalloc(&ctr, sizeof(uint32_t) * 4))) return e;
-  emrt::note_launch(), k_tri_bounds<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, n, cen, lo, hi, b.idx);
-  if (n >= 2) {
-    SahTask root{0u, n, 0u, 0u};
+  if ((e = cudaMalloc(&ctr, sizeof(uint32_t) * 8))) return e;
+  if ((e = cudaMalloc(&fbuf, sizeof(uint32_t) * 3 * (size_t)nf))) return e;
+  // flags, positions, cluster leaf parents, sizes, starts, scan partials
+  if ((e = cudaMalloc(&cbuf, sizeof(uint32_t) * (5 * (size_t)n + kPrimGrid + 1)))) return e;
+  if ((e = cudaMalloc(&cl, sizeof(uint2) * n))) return e;
+  uint32_t *cnt = fbuf, *first = fbuf + nf, *last = fbuf + 2 * nf;
+  uint32_t *flag = cbuf, *pos = cbuf + n, *lp_cl = cbuf + 2 * (size_t)n, *sz = cbuf + 3 * (size_t)n,
+           *tstart = cbuf + 4 * (size_t)n, *partial = cbuf + 5 * (size_t)n;
+  cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nf, s);
+  cudaMemsetAsync(first, 0xff, sizeof(uint32_t) * nf, s);
+  cudaMemsetAsync(last, 0, sizeof(uint32_t) * nf, s);
+  emrt::note_launch(), k_face_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_face, n, n_faces, cnt, first, last);
+  // clusters: quads kept together unless that leaves fewer than two leaves
+  uint32_t nc = 0;
+  for (int quads = 1; quads >= 0; quads--) {
+    emrt::note_launch(), k_cluster_flags<<<ceil_div(n, 256), 256, 0, s>>>(tri_face, n, n_faces, cnt, first, quads, flag);
+    emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(ctr + 4, n);
+    exclusive_scan(ctr + 4, flag, pos, ctr + 5, partial, s);
+    cudaMemcpyAsync(&nc, ctr + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) break;
+    emrt::note_launch(), k_cluster_bounds<<<ceil_div(n, 256), 256, 0, s>>>(
+        tri_xyz, tri_face, n, n_faces, cnt, last, quads, flag, pos, cl, cen, lo, hi, b.idx);
+    if (nc >= 2 || n < 2) break;
+  }
+  if (!e && nc >= 2) {
+    SahTask root{0u, nc, 0u, 0u};
     uint32_t init[4] = {1, 0, 1, 0};  // level sizes [0],[1]; nodes allocated [2]
     cudaMemcpyAsync(tasks[0], &root, sizeof(root), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, s);
@@ -726,7 +959,7 @@ cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *
     for (; n_level && levels < kSahMaxDepth; levels++) {
       cudaMemcpyAsync(ctr + (cur ^ 1), &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
       emrt::note_launch(), k_sah_level<<<n_level, kSahBlock, 0, s>>>(
-          tasks[cur], ctr + cur, cen, lo, hi, b.idx, tmp, b.nodes, b.leaf_parent, tasks[cur ^ 1],
+          tasks[cur], ctr + cur, cen, lo, hi, b.idx, tmp, b.nodes, lp_cl, tasks[cur ^ 1],
           ctr + (cur ^ 1), ctr + 2);
       cudaMemcpyAsync(&n_level, ctr + (cur ^ 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
       if ((e = cudaStreamSynchronize(s))) break;
@@ -735,32 +968,46 @@ cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *
     // a tree deeper than the traversal stack can serve is not used: the
     // caller falls back to the LBVH
     if (!e && n_level) e = cudaErrorNotSupported;
+    if (!e) {  // leaves of clusters -> leaves of triangles
+      emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(ctr + 4, nc);
+      emrt::note_launch(), k_cluster_sizes<<<ceil_div(nc, 256), 256, 0, s>>>(cl, b.idx, nc, sz);
+      exclusive_scan(ctr + 4, sz, tstart, ctr + 5, partial, s);
+      emrt::note_launch(), k_cluster_expand<<<ceil_div(nc, 256), 256, 0, s>>>(
+          cl, b.idx, tstart, lp_cl, nc, b.idx2, b.leaf_parent, b.nodes);
+    }
+  } else if (!e) {  // a single triangle
+    emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(b.idx2, 0u);
   }
   if (!e) {
-    emrt::note_launch(), k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
+    emrt::note_launch(), k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx2, n, b.prims);
     if (n >= 2) {
       cudaMemsetAsync(b.flags, 0, sizeof(uint32_t) * n, s);
-      emrt::note_launch(), k_refit<PRIM_TRI, true><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags);
+      emrt::note_launch(), k_refit<PRIM_TRI, true><<<ceil_div(n, 256), 256, 0, s>>>(b.prims, n, b.nodes, b.leaf_parent, b.flags, b.pad);
     }
     e = cudaStreamSynchronize(s);
     if (!e) b.leaf_bits = 2;
   }
   cudaFree(cen); cudaFree(lo); cudaFree(hi); cudaFree(tmp);
-  cudaFree(tasks[0]); cudaFree(tasks[1]); cudaFree(ctr);
+  cudaFree(tasks[0]); cudaFree(tasks[1]); cudaFree(ctr); cudaFree(fbuf); cudaFree(cbuf);
+  cudaFree(cl);
   if (e) return e;
   return cudaGetLastError();
 }
 
-cudaError_t bvh4_collapse(BVHBuf &b, cudaStream_t s) {
-  if (b.n < 2) return cudaSuccess;
+cudaError_t bvh8_build(BVHBuf &b, cudaStream_t s) {
+  cudaFree(b.nodes8);
+  cudaFree(b.prims8);
+  b.nodes8 = nullptr;
+  b.prims8 = nullptr;
+  b.n8 = 0;
+  if (b.n < 2 || b.kind != PRIM_TRI) return cudaSuccess;
   cudaError_t e;
-  cudaFree(b.nodes4);
-  b.nodes4 = nullptr;
-  if ((e = cudaMalloc(&b.nodes4, sizeof(float4) * 8 * (size_t)b.n))) return e;
-  uint32_t *buf = nullptr;  // two level lists (binary index, 4-wide index) + counters
+  if ((e = cudaMalloc(&b.nodes8, sizeof(uint4) * 5 * (size_t)(b.n - 1)))) return e;
+  if ((e = cudaMalloc(&b.prims8, sizeof(float4) * 3 * (size_t)b.n))) return e;
+  uint32_t *buf = nullptr;  // two level lists (binary index, wide index) + counters
   if ((e = cudaMalloc(&buf, sizeof(uint32_t) * (4 * (size_t)b.n + 4)))) return e;
   uint32_t *lb[2] = {buf, buf + b.n}, *ld[2] = {buf + 2 * b.n, buf + 3 * b.n};
-  uint32_t *ctr = buf + 4 * b.n;  // [0],[1]: level sizes, [2]: nodes allocated
+  uint32_t *ctr = buf + 4 * b.n;  // [0],[1]: level sizes, [2]: nodes, [3]: triangles
   uint32_t init[4] = {1, 0, 1, 0};
   uint32_t zero = 0;
   cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, s);
@@ -770,17 +1017,24 @@ cudaError_t bvh4_collapse(BVHBuf &b, cudaStream_t s) {
   int cur = 0;
   for (int guard = 0; n_level && guard < 4096; guard++) {
     cudaMemcpyAsync(ctr + (cur ^ 1), &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-    emrt::note_launch(), k_collapse<<<ceil_div(n_level, 128), 128, 0, s>>>(
-        b.nodes, lb[cur], ld[cur], ctr + cur, b.nodes4, lb[cur ^ 1], ld[cur ^ 1], ctr + (cur ^ 1),
-        ctr + 2);
+    emrt::note_launch(), k_wide8<<<ceil_div(n_level, 64), 64, 0, s>>>(
+        b.nodes, b.prims, b.leaf_bits, lb[cur], ld[cur], ctr + cur, b.nodes8, b.prims8,
+        lb[cur ^ 1], ld[cur ^ 1], ctr + (cur ^ 1), ctr + 2, ctr + 3);
     cudaMemcpyAsync(&n_level, ctr + (cur ^ 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) break;
     cur ^= 1;
   }
-  cudaMemcpyAsync(&b.n4, ctr + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&b.n8, ctr + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   cudaFree(buf);
   if (e) return e;
+  if (b.n8 >= (1u << 24)) {  // child indices hold 24 bits: no wide tree
+    cudaFree(b.nodes8);
+    cudaFree(b.prims8);
+    b.nodes8 = nullptr;
+    b.prims8 = nullptr;
+    b.n8 = 0;
+  }
   return cudaGetLastError();
 }
 

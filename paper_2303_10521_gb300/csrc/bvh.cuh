@@ -19,9 +19,16 @@ struct BVHBuf {
   KeyW<2> *keys = nullptr, *keys2 = nullptr;  // [cap]
   uint32_t *idx = nullptr, *idx2 = nullptr;   // [cap]
   uint32_t *d_n = nullptr;       // device copy of n
-  float4 *nodes4 = nullptr;      // 4-wide collapse (static BVH), or null
-  uint32_t n4 = 0;
+  uint4 *nodes8 = nullptr;       // compressed 8-wide tree (static BVH), or null
+  float4 *prims8 = nullptr;      // its triangles, in its own leaf order
+  uint32_t n8 = 0;
   uint32_t leaf_bits = 0;        // see BVHView (2: multi-triangle SAH leaves)
+  // Every leaf box is grown by `pad` metres on each side.  A box test takes a
+  // plane's t as p idir - o idir, so the rounding of o idir shifts the plane
+  // by up to 2^-24 |o| along its axis; the pad, 2^-21 times the largest
+  // coordinate of the scene, keeps the test conservative for ray origins in
+  // the scene (no cracks at box planes that are also triangle edges).
+  float pad = 0.f;
   BVHView view() const;
 };
 
@@ -41,17 +48,20 @@ cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint3
 cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const float4 *bbox,
                              uint32_t *hist, cudaStream_t s);
 // Top-down binned-SAH build of a triangle BVH (same node format as the
-// LBVH; used for the static geometry, which is built once).  Synchronises.
+// LBVH; used for the static geometry, which is built once).  The two
+// triangles of a face made of exactly two (faces 0..n_faces-1 of tri_face)
+// share one leaf; other leaves hold one triangle.  Synchronises.
 cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_face,
-                               uint32_t n, cudaStream_t s);
+                               uint32_t n, uint32_t n_faces, cudaStream_t s);
 // Moves box primitives to new corners (vehicle id kept in lo.w) and refits.
 cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaStream_t s);
 
-// Collapses the binary tree of b (built, refitted) into 4-wide nodes
-// (b.nodes4): every 4-wide node takes its binary node's two children and
-// repeatedly opens the inner child of largest surface area until it holds 4
-// children.  Synchronises the stream (build time only).
-cudaError_t bvh4_collapse(BVHBuf &b, cudaStream_t s);
+// Builds the compressed 8-wide tree of a triangle BVH b (built, refitted)
+// into b.nodes8 / b.prims8 (layout in BVHView): every wide node takes its
+// binary node's two children and repeatedly opens the inner child of largest
+// surface area until it holds 8 children; child boxes are quantised to 8 bits
+// on the node's grid.  Synchronises the stream (build time only).
+cudaError_t bvh8_build(BVHBuf &b, cudaStream_t s);
 
 // Axis-aligned bounds of n float[9] triangles, written to bbox[2].
 void bbox_of_tris(const float *tri_xyz, uint32_t n, float4 *bbox, cudaStream_t s);

@@ -14,7 +14,7 @@
 // and faces met; the segment index b of its first segment is the number of
 // faces met.  Candidates carry w0 in word 0 and jj (the ray index) in word 7.
 // Segments, candidates and cache entries are exactly those of k_bounce.
-template <bool CACHE>
+template <bool CACHE, bool WIDE = false>
 __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const GeomView &g, float kappa,
                                             int K, uint32_t w0, uint32_t tx, uint32_t item,
                                             uint32_t jj, const Ray &R, float3 rlo, float3 rhi,
@@ -49,7 +49,7 @@ __device__ __forceinline__ void carry_chain(const BounceLaunch &L, const GeomVie
       }
     }
     if (!have) {
-      trace_tris<false, false>(g.stat, q, 0.f, tbest, face, prev, NO, stk, st);
+      trace_tris<false, WIDE>(g.stat, q, 0.f, tbest, face, prev, NO, stk, st);
       if (keep) L.stab[slot] = make_uint4(__float_as_uint(tbest), face, ep, 0u);
     }
     const uint32_t exv = (prev != NO && prev >= fs) ? (prev - fs) / 6u : NO;
@@ -218,9 +218,10 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_chain(BounceLaunch L, C
 // a warp.  BATCH: primary items of many scenes (table tab, each item's scene
 // the last whose range starts at or before it; candidates carry
 // scene << 8 | tx); otherwise the single scene in L.g.  Segments and
-// candidates are exactly those of k_bounce.
-template <int BLOCK, bool BATCH>
-__global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L,
+// candidates are exactly those of k_bounce.  WIDE: closest hits through the
+// compressed 8-wide tree of the static geometry (same hits).
+template <int BLOCK, bool BATCH, bool WIDE = false>
+__global__ void __launch_bounds__(BLOCK, (WIDE ? 1024 : 1280) / BLOCK) k_walk(BounceLaunch L,
                                                              const BatchScene *__restrict__ tab,
                                                              uint32_t n_scenes) {
   StackSlot stk[kStack];
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(BLOCK, 1280 / BLOCK) k_walk(BounceLaunch L,
       R.o_L = make_float4(p.x, p.y, p.z, 0.f);
       R.d_id = dj;
       R.faces = make_uint4(NO, NO, NO, NO);
-      carry_chain<false>(L, g, BATCH ? tab[sc].kappa : L.kappa, BATCH ? (int)tab[sc].K : L.K,
+      carry_chain<false, WIDE>(L, g, BATCH ? tab[sc].kappa : L.kappa, BATCH ? (int)tab[sc].K : L.K,
                          BATCH ? (sc << 8 | tx) : tx, tx, local, __float_as_uint(dj.w), R, rlo,
                          rhi, stk, st, segs, unused);
     }

@@ -48,9 +48,11 @@ struct Counters {
 //   [2] c0.lo.z c0.hi.z c1.lo.z c1.hi.z
 //   [3] (int) c0, c1, parent, 0     child >= 0: inner node, < 0: leaf ~prim
 struct BVHView {
-  const float4 *nodes4;  // optional 4-wide collapse of `nodes` (8 float4 per
-                         // node: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the 4
-                         // children, int4 child codes, int child count)
+  const uint4 *nodes8;   // optional compressed 8-wide tree of a triangle BVH
+                         // (5 uint4 per node: origin, exponents and inner
+                         // mask; first child, leaf mask, first triangle,
+                         // leaf meta; 8-bit child boxes along x, y, z)
+  const float4 *prims8;  // its triangles (3 float4 each, as prims)
   const float4 *nodes;
   const float4 *prims;  // triangles: 3 float4 (v0 with face id bits in .w,
                         // v1, v2); boxes: 2 float4 (lo with vehicle id bits in

@@ -629,20 +629,25 @@ void launch_chain(const BounceLaunch &L, const ChainBufs &D, int grid, cudaStrea
   emrt::note_launch(), k_chain<kBounceBlock><<<grid, kBounceBlock, 0, s>>>(L, D);
 }
 
-int g_walk_grid = 0;
+int g_walk_grid[2] = {0, 0};
+template <bool WIDE>
 int walk_grid() {
-  if (!g_walk_grid) {
+  if (!g_walk_grid[WIDE]) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<kBounceBlock, false>, kBounceBlock, 0);
-    g_walk_grid = sms * (per > 0 ? per : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<kBounceBlock, false, WIDE>,
+                                                  kBounceBlock, 0);
+    g_walk_grid[WIDE] = sms * (per > 0 ? per : 1);
   }
-  return g_walk_grid;
+  return g_walk_grid[WIDE];
 }
 
-void launch_walk(const BounceLaunch &L, cudaStream_t s) {
-  emrt::note_launch(), k_walk<kBounceBlock, false><<<walk_grid(), kBounceBlock, 0, s>>>(L, nullptr, 1);
+void launch_walk(const BounceLaunch &L, cudaStream_t s, bool wide) {
+  if (wide)
+    emrt::note_launch(), k_walk<kBounceBlock, false, true><<<walk_grid<true>(), kBounceBlock, 0, s>>>(L, nullptr, 1);
+  else
+    emrt::note_launch(), k_walk<kBounceBlock, false><<<walk_grid<false>(), kBounceBlock, 0, s>>>(L, nullptr, 1);
 }
 
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,
@@ -677,11 +682,12 @@ Variant g_variants[] = {
     {"block128_fetch128", 128, k_bounce<true, 128, 128, false>, false, 0},
     {"block256_fetch64", 256, k_bounce<true, 256, 64, false>, false, 0},
     {"block64_fetch128", 64, k_bounce<true, 64, 128, false>, false, 0},
-    {"block128_fetch32_bvh4", 128, k_bounce<true, 128, 32, true>, false, 0},
-    {"block64_fetch32_bvh4", 64, k_bounce<true, 64, 32, true>, false, 0},
+    {"block128_fetch32_bvh8", 128, k_bounce<true, 128, 32, true>, false, 0},
+    {"block64_fetch32_bvh8", 64, k_bounce<true, 64, 32, true>, false, 0},
     {"depth_first_block128", 128, k_walk<128, true>, true, 0},
     {"depth_first_block64", 64, k_walk<64, true>, true, 0},
     {"depth_first_block256", 256, k_walk<256, true>, true, 0},
+    {"depth_first_block128_bvh8", 128, k_walk<128, true, true>, true, 0},
 };
 constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 }  // namespace

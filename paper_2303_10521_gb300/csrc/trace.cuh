@@ -60,8 +60,9 @@ uint64_t chain_queue_entries();
 void launch_chain(const BounceLaunch &L, const ChainBufs &D, int grid, cudaStream_t s);
 int chain_grid();
 // Depth-first discovery of L.n_primary primary rays without the cache
-// (persistent grid; cursor L.work).
-void launch_walk(const BounceLaunch &L, cudaStream_t s);
+// (persistent grid; cursor L.work); wide: static closest hits through the
+// compressed 8-wide tree.
+void launch_walk(const BounceLaunch &L, cudaStream_t s, bool wide = false);
 // epoch[t] += 1 and ref[t] = pos[t] for every transmitter whose position
 // differs (bitwise) from ref[t]
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,

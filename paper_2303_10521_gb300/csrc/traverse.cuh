@@ -122,18 +122,16 @@ struct TravStats {
     return hit;                        \
   }
 
-// One triangle leaf (1-4 triangles, see BVHView::leaf_bits): watertight
-// tests, exclusion of faces ex0/ex1, closest-hit tie to the lower face ID.
-// Returns true when tmax/face changed.
+// Triangles first .. first + cnt - 1 of `prims`: watertight tests, exclusion
+// of faces ex0/ex1, closest-hit tie to the lower face ID.  Returns true when
+// tmax/face changed.
 template <bool ANY>
-__device__ inline bool leaf_tri(const BVHView &b, uint32_t code, const RayQ &r, float tmin,
-                                float &tmax, uint32_t &face, uint32_t ex0, uint32_t ex1,
-                                TravStats &st) {
-  const uint32_t g0 = b.leaf_bits ? code >> 2 : code;
-  const uint32_t cnt = b.leaf_bits ? (code & 3u) + 1u : 1u;
+__device__ inline bool tri_range(const float4 *prims, uint32_t first, uint32_t cnt,
+                                 const RayQ &r, float tmin, float &tmax, uint32_t &face,
+                                 uint32_t ex0, uint32_t ex1, TravStats &st) {
   bool changed = false;
   for (uint32_t q = 0; q < cnt; q++) {
-    const float4 *tp = b.prims + 3ull * (g0 + q);
+    const float4 *tp = prims + 3ull * (first + q);
     float4 a = ldg4(tp), bb = ldg4(tp + 1), c = ldg4(tp + 2);
     st.tris++;
     uint32_t f = __float_as_uint(a.w);
@@ -153,89 +151,146 @@ __device__ inline bool leaf_tri(const BVHView &b, uint32_t code, const RayQ &r, 
   return changed;
 }
 
-// 4-wide traversal: each node fetch (8 x 16 B) tests four child boxes; the
-// nearest hit child is entered, the others are pushed far-to-near.
+// One triangle leaf (1-4 triangles, see BVHView::leaf_bits).
 template <bool ANY>
-__device__ inline bool trace_tris4(const BVHView &b, const RayQ &r, float tmin, float &tmax,
+__device__ inline bool leaf_tri(const BVHView &b, uint32_t code, const RayQ &r, float tmin,
+                                float &tmax, uint32_t &face, uint32_t ex0, uint32_t ex1,
+                                TravStats &st) {
+  const uint32_t g0 = b.leaf_bits ? code >> 2 : code;
+  const uint32_t cnt = b.leaf_bits ? (code & 3u) + 1u : 1u;
+  return tri_range<ANY>(b.prims, g0, cnt, r, tmin, tmax, face, ex0, ex1, st);
+}
+
+// Compressed 8-wide traversal (node layout in BVHView::nodes8).  Per node:
+// one 80-byte fetch, the 8 quantised child boxes decoded and slab-tested in
+// straight-line code, the hits turned into a mask in visiting order (bit k =
+// slot k ^ o, o the ray's sign pattern: roughly near to far, no sort).  The
+// stack holds node groups -- first child, inner-slot mask and the children
+// still to visit -- so one entry serves up to 7 siblings.  A lane descends
+// until it holds leaf children to test (then the warp's leaf tests run
+// together), tests them nearest slot first, and continues.
+__device__ inline uint32_t wide_kmask(uint32_t v, uint32_t oct) {
+  // bit s of each byte -> bit s ^ oct
+  if (oct & 1u) v = ((v & 0x5555u) << 1) | ((v >> 1) & 0x5555u);
+  if (oct & 2u) v = ((v & 0x3333u) << 2) | ((v >> 2) & 0x3333u);
+  if (oct & 4u) v = ((v & 0x0f0fu) << 4) | ((v >> 4) & 0x0f0fu);
+  return v;
+}
+
+template <bool ANY>
+__device__ inline bool trace_tris8(const BVHView &b, const RayQ &r, float tmin, float &tmax,
                                    uint32_t &face, uint32_t ex0, uint32_t ex1, StackSlot *stk,
                                    TravStats &st) {
+  const bool nx = r.idir.x < 0.f, ny = r.idir.y < 0.f, nz = r.idir.z < 0.f;
+  const uint32_t oct = (nx ? 1u : 0u) | (ny ? 2u : 0u) | (nz ? 4u : 0u);
   bool hit = false;
   int sp = 0;
-  int node = 0;
   uint32_t iter = 0;
+  uint32_t gb = 0, gi = 0, gk = 0;               // inner group: first child, mask, to visit
+  uint32_t lb = 0, lk = 0, lm0 = 0, lm1 = 0;      // leaf group: first tri, to test, meta
+  uint32_t node = 0;                              // the root is visited first
   for (;;) {
-    EMRT_ITER_GUARD(st)
-    if (node >= 0) {
-      const float4 *np = b.nodes4 + 8ll * node;
-      float4 lx = ldg4(np), hx = ldg4(np + 1), ly = ldg4(np + 2), hy = ldg4(np + 3);
-      float4 lz = ldg4(np + 4), hz = ldg4(np + 5), cc = ldg4(np + 6), nn = ldg4(np + 7);
-      st.nodes++;
-      int cnt = __float_as_int(nn.x);
-      float tn[4];
-      bool h[4];
-      h[0] = slab(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tmin, tmax, tn[0]);
-      h[1] = slab(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tmin, tmax, tn[1]);
-      h[2] = cnt > 2 && slab(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tmin, tmax, tn[2]);
-      h[3] = cnt > 3 && slab(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tmin, tmax, tn[3]);
-      int code[4] = {__float_as_int(cc.x), __float_as_int(cc.y), __float_as_int(cc.z),
-                     __float_as_int(cc.w)};
-      int best = -1;
-      float bt = 3.4e38f;
-      for (int k = 0; k < 4; k++)
-        if (h[k] && tn[k] < bt) {
-          bt = tn[k];
-          best = k;
-        }
-      if (best >= 0) {
-        // push the other hits far-to-near (insertion sort within this
-        // node's group, so the nearest remaining child is popped first)
-        const int g0 = sp;
-        for (int k = 0; k < 4; k++) {
-          if (!h[k] || k == best) continue;
-          if (sp >= kStack) {
-            st.overflow = true;
-            continue;
-          }
-          int q = sp++;
-          while (q > g0 && stk[q - 1].t < tn[k]) {
-            stk[q] = stk[q - 1];
-            q--;
-          }
-          stk[q] = StackSlot{code[k], tn[k]};
-        }
-        node = code[best];
-        continue;
+    while (lk == 0) {
+      if (++iter > kMaxIter) {
+        st.overflow = true;
+        return hit;
       }
-    } else {
-      if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
+      if (iter > 1) {
+        if (gk == 0) {
+          if (sp == 0) return hit;
+          sp--;
+          gb = (uint32_t)stk[sp].node & 0xffffffu;
+          gi = (uint32_t)stk[sp].node >> 24;
+          gk = __float_as_uint(stk[sp].t);
+        }
+        const uint32_t s = (uint32_t)(__ffs(gk) - 1) ^ oct;
+        gk &= gk - 1u;
+        node = gb + __popc(gi & ((1u << s) - 1u));
+        if (gk) {
+          if (sp < kStack) {
+            stk[sp] = StackSlot{(int)(gb | gi << 24), __uint_as_float(gk)};
+            sp++;
+          } else {
+            st.overflow = true;
+          }
+        }
+      }
+      const uint4 *np = b.nodes8 + 5ull * node;
+      const uint4 h0 = __ldg(np), h1 = __ldg(np + 1), qx = __ldg(np + 2), qy = __ldg(np + 3),
+                  qz = __ldg(np + 4);
+      st.nodes++;
+      // t of grid coordinate q along an axis: (2^23 + q) * ax + cx, the
+      // 2^23 offset coming from the byte-to-float conversion
+      const float ax = __uint_as_float((h0.w & 0xffu) << 23) * r.idir.x;
+      const float ay = __uint_as_float(((h0.w >> 8) & 0xffu) << 23) * r.idir.y;
+      const float az = __uint_as_float(((h0.w >> 16) & 0xffu) << 23) * r.idir.z;
+      const float cx = fmaf(-8388608.f, ax, fmaf(__uint_as_float(h0.x), r.idir.x, -r.ood.x));
+      const float cy = fmaf(-8388608.f, ay, fmaf(__uint_as_float(h0.y), r.idir.y, -r.ood.y));
+      const float cz = fmaf(-8388608.f, az, fmaf(__uint_as_float(h0.z), r.idir.z, -r.ood.z));
+      // near and far planes by the direction's sign
+      const uint32_t nx0 = nx ? qx.z : qx.x, nx1 = nx ? qx.w : qx.y;
+      const uint32_t fx0 = nx ? qx.x : qx.z, fx1 = nx ? qx.y : qx.w;
+      const uint32_t ny0 = ny ? qy.z : qy.x, ny1 = ny ? qy.w : qy.y;
+      const uint32_t fy0 = ny ? qy.x : qy.z, fy1 = ny ? qy.y : qy.w;
+      const uint32_t nz0 = nz ? qz.z : qz.x, nz1 = nz ? qz.w : qz.y;
+      const uint32_t fz0 = nz ? qz.x : qz.z, fz1 = nz ? qz.y : qz.w;
+      uint32_t hits = 0;
+#pragma unroll
+      for (int sl = 0; sl < 8; sl++) {
+        const uint32_t sel = 0x7440u | (uint32_t)(sl & 3);
+        const float tnx = fmaf(__uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x4B000000u, sel)), ax, cx);
+        const float tfx = fmaf(__uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x4B000000u, sel)), ax, cx);
+        const float tny = fmaf(__uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x4B000000u, sel)), ay, cy);
+        const float tfy = fmaf(__uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x4B000000u, sel)), ay, cy);
+        const float tnz = fmaf(__uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x4B000000u, sel)), az, cz);
+        const float tfz = fmaf(__uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x4B000000u, sel)), az, cz);
+        const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));
+        const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+        if (tn <= tf * 1.00000024f) hits |= 1u << sl;
+      }
+      const uint32_t imask = h0.w >> 24, lmask = h1.x >> 24;
+      const uint32_t k = wide_kmask((hits & imask) | (hits & lmask) << 8, oct);
+      gb = h1.x & 0xffffffu;
+      gi = imask;
+      gk = k & 0xffu;
+      lk = k >> 8;
+      lb = h1.y;
+      lm0 = h1.z;
+      lm1 = h1.w;
+    }
+    // leaf children of the last node, nearest slot first
+    while (lk) {
+      const uint32_t s = (uint32_t)(__ffs(lk) - 1) ^ oct;
+      lk &= lk - 1u;
+      const uint32_t meta = __byte_perm(lm0, lm1, s) & 0xffu;
+      if (tri_range<ANY>(b.prims8, lb + (meta & 31u), ((meta >> 5) & 3u) + 1u, r, tmin, tmax,
+                         face, ex0, ex1, st)) {
         hit = true;
         if (ANY) return true;
       }
     }
-    for (;;) {
-      if (sp == 0) return hit;
-      sp--;
-      if (stk[sp].t <= tmax) break;
-    }
-    node = stk[sp].node;
   }
 }
 
 // Closest hit (ANY = false) or any hit (ANY = true) over the triangle BVH with
 // t in (tmin, tmax).  Triangles of faces ex0/ex1 are skipped.  On a hit
 // tmax and face are updated.  Ties in t go to the lower face ID.
-// WIDE: use the 4-wide collapse when the BVH has one.
+// WIDE: use the compressed 8-wide tree when the BVH has one.
 template <bool ANY, bool WIDE = false>
 __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, float &tmax,
                                   uint32_t &face, uint32_t ex0, uint32_t ex1, StackSlot *stk,
                                   TravStats &st) {
   if (b.n_prims == 0) return false;
-  if (WIDE && b.nodes4 && b.n_prims >= 2)
-    return trace_tris4<ANY>(b, r, tmin, tmax, face, ex0, ex1, stk, st);
+  if (WIDE && b.nodes8 && b.n_prims >= 2)
+    return trace_tris8<ANY>(b, r, tmin, tmax, face, ex0, ex1, stk, st);
   bool hit = false;
   int sp = 0;
   int node = b.root;
   uint32_t iter = 0;
+  // a popped subtree is skipped only when its entry lies beyond the bound
+  // with the slab test's own slack (closest hit), so that pruning on pop and
+  // on visit agree and exact ties in t can still reach the lower face ID
+  const float pop_slack = ANY ? 1.f : 1.00000024f;
   for (;;) {
     // descend through inner nodes until this lane reaches a leaf, so that
     // the lanes of a warp test their leaves together
@@ -263,7 +318,7 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
       for (;;) {
         if (sp == 0) return hit;
         sp--;
-        if (stk[sp].t <= tmax) break;
+        if (stk[sp].t <= tmax * pop_slack) break;
       }
       node = stk[sp].node;
     }
@@ -275,7 +330,7 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
     for (;;) {
       if (sp == 0) return hit;
       sp--;
-      if (stk[sp].t <= tmax) break;
+      if (stk[sp].t <= tmax * pop_slack) break;
     }
     node = stk[sp].node;
   }

@@ -187,8 +187,9 @@ class Scene:
                     static_cache=False, breadth_first=False):
         """Plain discovery into out (no sync).  static_cache: reuse the static
         closest hits of earlier calls with this ray set; breadth_first: trace
-        bounce by bounce (sort_rays and wide_bvh apply to that form) instead
-        of depth-first chains.  Identical output either way."""
+        bounce by bounce (sort_rays applies to that form) instead of
+        depth-first chains; wide_bvh: static closest hits through the
+        compressed 8-wide tree.  Identical output either way."""
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
                           int(self.desc.n_rays if n_rays is None else n_rays), int(offset),
                           int(stride), int(count),
@@ -214,7 +215,7 @@ class Scene:
     def trace_backward_async(self, out: Paths, rx_ids: Optional[torch.Tensor] = None,
                              n_rays=None, max_depth=None, offset=0, stride=1, count=0,
                              keep_rejected=False, sort_rays=True, stream=None,
-                             breadth_first=False):
+                             breadth_first=False, wide_bvh=False):
         """Backward discovery from the receivers rx_ids (device int tensor;
         None = every receiver); paths come out in forward orientation."""
         p = N.TraceParams(int(self.desc.max_depth if max_depth is None else max_depth),
@@ -222,6 +223,7 @@ class Scene:
                           int(stride), int(count),
                           (N.TRACE_KEEP_REJECTED if keep_rejected else 0) |
                           (N.TRACE_SORT_RAYS if sort_rays else 0) |
+                          (N.TRACE_WIDE_BVH if wide_bvh else 0) |
                           (N.TRACE_BREADTH_FIRST if breadth_first else 0))
         ids, n_ids = None, 0
         if rx_ids is not None:
@@ -238,12 +240,12 @@ class Scene:
     def trace_backward(self, rx_ids: Optional[torch.Tensor] = None, n_rays=None, max_depth=None,
                        offset=0, stride=1, count=0, keep_rejected=False, capacity=None,
                        stream=None, retries=3, sort_rays=True,
-                       breadth_first=False) -> Paths:
+                       breadth_first=False, wide_bvh=False) -> Paths:
         """Backward discovery; grows scratch and output on capacity errors."""
         return self._retry(lambda out: self.trace_backward_async(
             out, rx_ids, n_rays, max_depth, offset, stride, count, keep_rejected,
-            sort_rays=sort_rays, stream=stream, breadth_first=breadth_first), capacity, stream,
-            retries, "emrt_trace_backward")
+            sort_rays=sort_rays, stream=stream, breadth_first=breadth_first, wide_bvh=wide_bvh),
+            capacity, stream, retries, "emrt_trace_backward")
 
     def _retry(self, launch, capacity, stream, retries, name) -> Paths:
         cap = capacity or max(4096, 8 * self.n_tx * self.n_rx)

@@ -47,6 +47,21 @@ def test_city_depth_first_equals_breadth_first(city):
     assert np.array_equal(b, allc.records())
 
 
+def test_city_wide_bvh_identical(city):
+    """Full-size city frame through the compressed 8-wide tree (8-bit child
+    boxes), depth-first and breadth-first: the binary tree's records and
+    segments, bit for bit; fewer node fetches per segment."""
+    sc, fr, g, allc, acc, o = city
+    g.trace(keep_rejected=True)
+    s2 = dict(g.last_stats)
+    for kw in (dict(), dict(breadth_first=True)):
+        w = g.trace(keep_rejected=True, wide_bvh=True, **kw).records()
+        s8 = dict(g.last_stats)
+        assert np.array_equal(w, allc.records()), kw
+        assert s8["segments"] == s2["segments"], kw
+        assert s8["node_visits"] < 0.7 * s2["node_visits"], (s8["node_visits"], s2["node_visits"])
+
+
 def test_city_acceptance_every_candidate(city):
     sc, fr, g, allc, acc, o = city
     gu = rec_to_paths(allc.records())

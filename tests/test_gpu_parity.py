@@ -148,12 +148,13 @@ def test_district_subsample_parity(engine, stride, offset, form):
 
 def test_district_traversal_forms_identical(engine):
     """The depth-first chains (default), the breadth-first form with and
-    without the ray sort and through the 4-wide BVH, forward and backward:
-    the same records bit for bit and the same segments per bounce."""
+    without the ray sort, and both through the compressed 8-wide BVH,
+    forward and backward: the same records bit for bit and the same segments
+    per bounce."""
     sc = S.district_scene(seed=0)
     g = _gpu(engine, sc)
     forms = [dict(), dict(breadth_first=True), dict(breadth_first=True, sort_rays=False),
-             dict(wide_bvh=True)]
+             dict(wide_bvh=True), dict(wide_bvh=True, breadth_first=True)]
     ref, ref_segs = None, None
     for kw in forms:
         rec = g.trace(stride=13, offset=7, keep_rejected=True, **kw).records()
@@ -166,7 +167,8 @@ def test_district_traversal_forms_identical(engine):
     ids = torch.arange(0, g.n_rx, 7, dtype=torch.int32, device="cuda")
     b0 = g.trace_backward(ids, n_rays=20_000, keep_rejected=True).records()
     b1 = g.trace_backward(ids, n_rays=20_000, keep_rejected=True, breadth_first=True).records()
-    assert len(b0) > 10 and np.array_equal(b0, b1)
+    b2 = g.trace_backward(ids, n_rays=20_000, keep_rejected=True, wide_bvh=True).records()
+    assert len(b0) > 10 and np.array_equal(b0, b1) and np.array_equal(b0, b2)
 
 
 @pytest.mark.parametrize("seed", range(6))
