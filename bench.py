@@ -781,13 +781,20 @@ def main():
     cached_val = job_throughput(n_rx * (nc - 1), ws, cached_ms)
 
     def agree(pa, pb):
-        """Agreement of per-receiver powers pa against pb (W)."""
+        """Agreement of per-receiver powers pa against pb (W): power recall,
+        share of receivers more than 0.5 dB apart (a receiver with power on
+        one side only counts as apart), median and 95th percentile of |dB|
+        over the receivers with power on both sides, share with power on one
+        side only."""
         m = (pa > 0) | (pb > 0)
         rec = float(np.minimum(pa[m], pb[m]).sum() / max(pb[m].sum(), 1e-300))
-        with np.errstate(divide="ignore"):
-            db = np.abs(10 * np.log10(pa[m]) - 10 * np.log10(pb[m]))
-        return (rec, float(np.mean(db > 0.5)), float(np.median(db)),
-                float(np.percentile(db, 95)))
+        both = (pa > 0) & (pb > 0)
+        db = np.abs(10 * np.log10(pa[both]) - 10 * np.log10(pb[both]))
+        one = int(m.sum() - both.sum())
+        return (rec, float((np.sum(db > 0.5) + one) / max(1, m.sum())),
+                float(np.median(db)) if len(db) else 0.0,
+                float(np.percentile(db, 95)) if len(db) else 0.0,
+                float(one / max(1, m.sum())))
 
     acc_c, acc_p = [], []
     plain_ref = {}
@@ -864,7 +871,8 @@ def main():
                                   "power_recall_min": float(acc_r[:, 0].min()),
                                   "frac_rx_over_0p5db": float(acc_r[:, 1].mean()),
                                   "median_abs_db": float(acc_r[:, 2].mean()),
-                                  "p95_abs_db": float(acc_r[:, 3].mean())}
+                                  "p95_abs_db": float(acc_r[:, 3].mean()),
+                   "frac_rx_power_one_side_only": float(acc_r[:, 4].mean())}
             if len(acc_r) else None}
     accuracy = {
         "frames": nc, "refresh_every": REFRESH, "static_cache": use_sc, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
@@ -881,7 +889,8 @@ def main():
                    "power_recall_min": float(acc_c[:, 0].min()),
                    "frac_rx_over_0p5db": float(acc_c[:, 1].mean()),
                    "median_abs_db": float(acc_c[:, 2].mean()),
-                   "p95_abs_db": float(acc_c[:, 3].mean())},
+                   "p95_abs_db": float(acc_c[:, 3].mean()),
+                   "frac_rx_power_one_side_only": float(acc_c[:, 4].mean())},
         "plain_other_ray_set": {"note": "plain retrace with 0.9 N rays (another Fibonacci set of "
                                         "similar density) against the same reference: the "
                                         "ray-set variability of the plain method itself",
@@ -889,7 +898,8 @@ def main():
                                 "power_recall_min": float(acc_p[:, 0].min()),
                                 "frac_rx_over_0p5db": float(acc_p[:, 1].mean()),
                                 "median_abs_db": float(acc_p[:, 2].mean()),
-                                "p95_abs_db": float(acc_p[:, 3].mean())}}
+                                "p95_abs_db": float(acc_p[:, 3].mean()),
+                   "frac_rx_power_one_side_only": float(acc_p[:, 4].mean())}}
 
     batched = None if args.no_batched else run_batched(engine, scenes, dev)
 
