@@ -281,6 +281,189 @@ def run_batched(engine, scenes, dev, reps=5):
                                              "best of %d" % reps}
 
 
+def run_cached_batched(engine, scenes, dev, frames=21, refresh=10, low=10, n_streams=16):
+    """Cached-plus-batched: the path caches of the 64 uneven scenes of the
+    batched leg, refreshed together, every frame one CUDA graph.  Per frame
+    each scene is updated and its cache revalidated (image method + occlusion
+    rays on the cached face sequences), one batched low-density rediscovery
+    (N / low rays per transmitter of every scene, reception radius for that
+    density; the full ray set every `refresh` frames) serves all scenes at
+    once, its paths are merged into each scene's cache and the scene's fields
+    are computed.  The per-scene work is spread over n_streams streams during
+    the capture, so independent scenes run side by side on the GPU.  The
+    frame's poses of all scenes sit in one device buffer that the graph
+    reads (one copy per frame).  Against it: the plain batched retrace of the
+    same frames (updates, full-density batched discovery, fields), captured
+    the same way.  CUDA events over all frames; accuracy per frame against
+    the plain retrace of that frame, over every receiver of every scene."""
+    import torch
+    names = ("veh_pos", "veh_vel", "rx_pos", "rx_vel", "tx_pos", "tx_vel")
+    descs = scenes.batched_scenes(seed=0, n=64)
+    scs = []
+    for d in descs:
+        g = engine.Scene(d, device=dev)
+        g.update(d.frame(0))
+        scs.append(g)
+    # flat pose buffer: every scene's six arrays back to back, one row per frame
+    layout, off = [], 0
+    for d in descs:
+        f0 = d.frame(0)
+        row = {}
+        for nm in names:
+            a = np.asarray(getattr(f0, nm), np.float32)
+            row[nm] = (off, a.shape)
+            off += a.size
+        layout.append(row)
+    host = np.zeros((frames, off), np.float32)
+    for k in range(frames):
+        for d, row in zip(descs, layout):
+            fk = d.frame(k)
+            for nm, (o, shp) in row.items():
+                host[k, o:o + int(np.prod(shp))] = np.asarray(getattr(fk, nm), np.float32).ravel()
+    flat = torch.as_tensor(host).to(dev)
+    cur = torch.empty(off, dtype=torch.float32, device=dev)
+
+    class F:
+        pass
+
+    views = []
+    for row in layout:
+        v = F()
+        for nm, (o, shp) in row.items():
+            setattr(v, nm, cur[o:o + int(np.prod(shp))].view(*shp))
+        views.append(v)
+    caps = [max(4096, 8 * g.n_tx * g.n_rx) for g in scs]
+    full = engine.Batch(scs, capacity=caps)
+    lowb = engine.Batch(scs, capacity=caps,
+                        params=[dict(n_rays=max(1, d.n_rays // low)) for d in descs])
+    caches = [engine.Paths(4 * c, dev) for c in caps]
+    chs = [None] * len(scs)
+    n_rx = sum(g.n_rx for g in scs)
+    streams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
+
+    def per_scene(fn):
+        main = torch.cuda.current_stream()
+        for st in streams:
+            st.wait_stream(main)
+        for i in range(len(scs)):
+            fn(i, streams[i % n_streams])
+        for st in streams:
+            main.wait_stream(st)
+
+    def cached_frame(b):
+        per_scene(lambda i, st: (scs[i].update(views[i], stream=st),
+                                 scs[i].revalidate(caches[i], stream=st)))
+        b.trace_async(stream=torch.cuda.current_stream())
+        per_scene(lambda i, st: (scs[i].merge(caches[i], b.outs[i], stream=st),
+                                 chs.__setitem__(i, scs[i].channel(caches[i], descs[i].freqs[0],
+                                                                   out=chs[i], stream=st))))
+
+    def plain_frame():
+        per_scene(lambda i, st: scs[i].update(views[i], stream=st))
+        full.trace_async(stream=torch.cuda.current_stream())
+        per_scene(lambda i, st: chs.__setitem__(
+            i, scs[i].channel(full.outs[i], descs[i].freqs[0], out=chs[i], stream=st)))
+
+    # untimed: frame 0 fills the caches; every call once outside a capture
+    # (scratch sized, batch graphs captured, output buffers allocated)
+    cur.copy_(flat[0])
+    full.trace_async()
+    full.sync()
+    for g, c, o in zip(scs, caches, full.outs):
+        g.merge(c, o)
+    lowb.trace_async()
+    lowb.sync()
+    for i, g in enumerate(scs):
+        g.revalidate(caches[i])
+        chs[i] = g.channel(caches[i], descs[i].freqs[0])
+        g.sync()
+    torch.cuda.synchronize()
+    graphs = {}
+    try:
+        for name, fn in (("low", lambda: cached_frame(lowb)), ("refresh", lambda: cached_frame(full)),
+                         ("plain", plain_frame)):
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, capture_error_mode="thread_local"):
+                fn()
+            graphs[name] = gr
+    except Exception as e:  # report, run without graphs
+        return {"error": f"capture failed: {e}"}
+    torch.cuda.synchronize()
+    for g in scs:
+        g.sync()
+    # restart the caches from the plain retrace of frame 0
+    cur.copy_(flat[0])
+    graphs["plain"].replay()
+    for g, c, o in zip(scs, caches, full.outs):
+        c.count.zero_()
+        g.merge(c, o)
+    torch.cuda.synchronize()
+
+    def run(kind):
+        got = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(1, frames):
+            cur.copy_(flat[k])
+            if kind == "plain":
+                graphs["plain"].replay()
+            else:
+                graphs["refresh" if k % refresh == 0 else "low"].replay()
+            if k % 5 == 2:
+                got[k] = torch.cat([c.rx[:, 0] for c in chs]).clone()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), got
+
+    cached_ms, got = run("cached")
+    errs = sum(g.sync()["error_bits"] for g in scs)
+    plain_ms, ref = run("plain")
+    errs += sum(g.sync()["error_bits"] for g in scs)
+    full.sync()
+    lowb.sync()
+    # the plain per-frame retrace issued scene by scene (update, emrt_trace,
+    # fields; no batch, no graph), as a caller without the batched form runs
+    # it
+    outs = [engine.Paths(c, dev) for c in caps]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(1, frames):
+        cur.copy_(flat[k])
+        for i, g in enumerate(scs):
+            g.update(views[i])
+            g.trace_async(outs[i])
+            chs[i] = g.channel(outs[i], descs[i].freqs[0], out=chs[i])
+        for g in scs:
+            errs += g.sync()["error_bits"]
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    rec, over = [], []
+    for k in got:
+        pa, pb = got[k].cpu().numpy(), ref[k].cpu().numpy()
+        m = (pa > 0) | (pb > 0)
+        rec.append(float(np.minimum(pa[m], pb[m]).sum() / max(pb[m].sum(), 1e-300)))
+        both = (pa > 0) & (pb > 0)
+        db = np.abs(10 * np.log10(pa[both]) - 10 * np.log10(pb[both]))
+        over.append(float((np.sum(db > 0.5) + (m.sum() - both.sum())) / max(1, m.sum())))
+    nf = frames - 1
+    return {"scenes": len(scs), "receivers": int(n_rx), "frames": nf, "refresh_every": refresh,
+            "rediscovery": f"N/{low} rays per transmitter of every scene, batched",
+            "cached_batched_receiver_frames_per_s": n_rx * nf / (cached_ms / 1e3),
+            "plain_batched_receiver_frames_per_s": n_rx * nf / (plain_ms / 1e3),
+            "plain_sequential_receiver_frames_per_s": n_rx * nf / (seq_ms / 1e3),
+            "speedup_vs_plain_batched": plain_ms / cached_ms,
+            "speedup_vs_plain_sequential": seq_ms / cached_ms,
+            "cached_frame_ms": cached_ms / nf, "plain_frame_ms": plain_ms / nf,
+            "plain_sequential_frame_ms": seq_ms / nf,
+            "accuracy_vs_plain": {"power_recall_mean": float(np.mean(rec)),
+                                  "power_recall_min": float(np.min(rec)),
+                                  "frac_rx_over_0p5db": float(np.mean(over))},
+            "errors": int(errs),
+            "timing": "CUDA events around all frames; each frame one CUDA graph replay "
+                      f"(per-scene work on {n_streams} streams at capture)"}
+
+
 def run_cpu_baseline(sc, fr, stride):
     """The oracle as it stands on a strided ray sample of the same frame.
     The per-frame set-up (the oracle's polygon scene for this frame's poses)
@@ -902,6 +1085,7 @@ def main():
                    "frac_rx_power_one_side_only": float(acc_p[:, 4].mean())}}
 
     batched = None if args.no_batched else run_batched(engine, scenes, dev)
+    cached_batched = None if args.no_batched else run_cached_batched(engine, scenes, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -926,6 +1110,7 @@ def main():
             "cached": accuracy,
             "cached_per_receiver": per_rx,
             "batched": batched,
+            "cached_batched": cached_batched,
             "segments_per_frame": seg / len(stats),
             "paths_per_frame": last["accepted"],
             "candidates_per_frame": last["candidates"],

@@ -435,7 +435,13 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n,
                               uint32_t flags, emrt_stream s, emrt_batch *out);
 /* Discovery, deduplication and acceptance for every scene with the current
  * poses (the same result as emrt_trace on each scene).  Asynchronous; the
- * first call captures the graph. */
+ * first call captures the graph.  After that first call, a call on a stream
+ * that the caller is capturing into its own CUDA graph records the batch's
+ * launch sequence into that graph instead (no host synchronisation; the
+ * pinned per-scene table is copied by a node of the caller's graph, so the
+ * scenes must keep their transmitter and receiver counts while the caller's
+ * graph is replayed); calling it before the first uncaptured call returns
+ * EMRT_ERR_STATE. */
 emrt_status emrt_batch_trace(emrt_batch b, emrt_stream s);
 /* Waits and reports errors as emrt_sync (stats summed over the batch). */
 emrt_status emrt_batch_sync(emrt_batch b, emrt_stream s, emrt_stats *st);

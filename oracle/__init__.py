@@ -346,10 +346,11 @@ def power_loss(paths, a, n_tx, n_rx, tx_power_w, target_dbm, mask):
 
 
 def fd_gradient(scene, frame, paths, freq, tx_power_w, target_dbm, mask,
-                h_rel=1e-4, eps_r=None, sigma=None):
+                h_rel=1e-4, eps_r=None, sigma=None, tx_h=1e-4):
     """Central finite differences (relative step h_rel) of power_loss with
     respect to eps_r[m], sigma[m] (m over the material table) and each
-    transmitter position, over a frozen path topology."""
+    transmitter position (step near tx_h metres), over a frozen path
+    topology."""
     eps0 = np.array(scene.eps_r if eps_r is None else eps_r, np.float64)
     sig0 = np.array(scene.sigma if sigma is None else sigma, np.float64)
     n_tx, n_rx = len(frame.tx_pos), len(frame.rx_pos)
@@ -376,11 +377,11 @@ def fd_gradient(scene, frame, paths, freq, tx_power_w, target_dbm, mask,
     for t in range(n_tx):
         for c in range(3):
             # positions are float32 inputs: the step is a power-of-two number
-            # of float32 ulps near 1e-4 m, so both perturbed positions are
+            # of float32 ulps near tx_h, so both perturbed positions are
             # exact and the difference stays centred
             x = np.float32(frame.tx_pos[t, c])
             ulp = float(np.spacing(np.abs(x)))
-            h = ulp * 2.0 ** max(0, int(np.floor(np.log2(1e-4 / ulp))))
+            h = ulp * 2.0 ** max(0, int(np.floor(np.log2(tx_h / ulp))))
             up = frame.tx_pos.copy()
             dn = frame.tx_pos.copy()
             up[t, c] = np.float32(float(x) + h)

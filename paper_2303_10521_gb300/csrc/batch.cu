@@ -487,6 +487,18 @@ emrt_status emrt_batch_trace(emrt_batch b, emrt_stream stream) {
   for (uint32_t i = 0; i < b->n; i++)
     if (b->scenes[i]->n_tx != b->n_tx[i] || !b->scenes[i]->updated) return EMRT_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  BCK(cudaStreamIsCapturing(st, &cap));
+  if (cap == cudaStreamCaptureStatusActive) {
+    // the caller is capturing its own graph: record the table copy and the
+    // batch's launch sequence into it (no host sync, no allocation; the
+    // batch must have been traced once before, so that its scratch is sized)
+    if (!b->exec) return EMRT_ERR_STATE;
+    fill_table(b);
+    BCK(cudaMemcpyAsync(b->d_tab, b->h_tab, sizeof(BatchScene) * b->n, cudaMemcpyHostToDevice, st));
+    enqueue(b, b->variant, b->sort_rays, st);
+    return EMRT_OK;
+  }
   if (b->want_cand > b->cand_cap) {  // a previous call overflowed: grow, re-capture
     drop_graph(b);
     BCK(alloc_cand(b, b->want_cand));

@@ -151,3 +151,35 @@ def test_batched_oracle_parity(breadth_first):
         assert rf["ok"], (d.name, rf)
         checked += rc["n_gpu"]
     assert checked > 50 and with_paths >= 3, (checked, with_paths)
+
+
+def test_batch_trace_inside_a_caller_graph():
+    """After its first call, emrt_batch_trace on a stream the caller captures
+    is recorded into the caller's CUDA graph: replaying that graph after a
+    frame update gives the per-scene traces' records of the new poses."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_10521_gb300 import engine
+    descs = _small_batch(n=4, seed=5)
+    scs = []
+    for d in descs:
+        g = engine.Scene(d)
+        g.update(d.frame(0))
+        scs.append(g)
+    caps = [max(4096, 8 * g.n_tx * g.n_rx) for g in scs]
+    b = engine.Batch(scs, capacity=caps)
+    b.trace_async()
+    b.sync()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr, capture_error_mode="thread_local"):
+        b.trace_async(stream=torch.cuda.current_stream())
+    for frame in (1, 2):
+        for d, g in zip(descs, scs):
+            g.update(d.frame(frame))
+        torch.cuda.synchronize()
+        gr.replay()
+        torch.cuda.synchronize()
+        assert b.sync()["error_bits"] == 0
+        for d, g, o in zip(descs, scs, b.outs):
+            ref = g.trace(capacity=o.capacity).records()
+            assert np.array_equal(o.records(), ref), (frame, d.name)
