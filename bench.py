@@ -961,7 +961,64 @@ def main():
                    sev[k][1].elapsed_time(fev[k])) for k in range(1, nc)]
     cached_stages = {name: float(np.median([r[q] for r in stage_rows]))
                      for q, name in enumerate(("update", "revalidate_rediscover", "fields_and_sync"))}
-    cached_val = job_throughput(n_rx * (nc - 1), ws, cached_ms)
+    cached_eager_val = job_throughput(n_rx * (nc - 1), ws, cached_ms)
+    cached_rx_eager = [x.clone() for x in cached_rx]
+
+    # ---------------- the same cached frames, each one CUDA graph replay: the
+    # update, the rediscovery with its revalidation and the fields are
+    # captured once per kind of frame and read the frame's poses from one
+    # device buffer
+    pose_names = ("veh_pos", "veh_vel", "rx_pos", "rx_vel", "tx_pos", "tx_vel")
+    flat_c = torch.stack([torch.cat([getattr(cframes[k], f).reshape(-1) for f in pose_names])
+                          for k in range(nc)])
+    cur_pose = torch.empty_like(flat_c[0])
+    offs, o = {}, 0
+    for f in pose_names:
+        n = getattr(cframes[0], f).numel()
+        offs[f] = cur_pose[o:o + n].view(getattr(cframes[0], f).shape)
+        o += n
+    cv = F(offs)
+
+    def kind_of(k):
+        return "refresh" if REFRESH and k % REFRESH == 0 else ("low" if R_LOW else "revalidate")
+
+    def cached_step(kind):
+        g.update(cv)
+        if kind == "refresh":
+            g.rediscover(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc,
+                         revalidate=True)
+        elif kind == "low":
+            g.rediscover(cache, n_rays=sc.n_rays // R_LOW, sort_rays=sort_rays,
+                         breadth_first=bf, static_cache=use_sc, revalidate=True)
+        else:
+            g.revalidate(cache)
+        chs[:] = g.channels(cache, sc.freqs, outs=chs)
+
+    graphs = {}
+    for kind in sorted({kind_of(k) for k in range(1, nc)}):
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, capture_error_mode="thread_local"):
+            cached_step(kind)
+        graphs[kind] = gr
+    g.update(cframes[0])
+    g.trace_async(cache, sort_rays=sort_rays, breadth_first=bf, static_cache=use_sc)
+    g.sync()
+    cached_rx = []
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e4.record(stream)
+    for k in range(1, nc):
+        cur_pose.copy_(flat_c[k])
+        graphs[kind_of(k)].replay()
+        cached_rx.append(chs[0].rx[:, 0].clone())
+        g.sync()
+    e5.record(stream)
+    torch.cuda.synchronize()
+    cached_graph_ms = max_over_ranks(e4.elapsed_time(e5), dev)
+    cached_val = job_throughput(n_rx * (nc - 1), ws, cached_graph_ms)
+    graph_same = all(torch.equal(a, b) for a, b in zip(cached_rx, cached_rx_eager))
 
     def agree(pa, pb):
         """Agreement of per-receiver powers pa against pb (W): power recall,
@@ -1059,6 +1116,13 @@ def main():
             if len(acc_r) else None}
     accuracy = {
         "frames": nc, "refresh_every": REFRESH, "static_cache": use_sc, "rediscovery_rays_per_tx": sc.n_rays // R_LOW if R_LOW else 0,
+        "timing": "receiver_frames_per_s_cached: each cached frame one CUDA graph replay "
+                  "(update, rediscovery with revalidation, fields at both frequencies; one "
+                  "graph per kind of frame) + the sync; the per-frame and per-stage times "
+                  "below come from the same frames issued call by call",
+        "graph_frame_ms_mean": cached_graph_ms / (nc - 1),
+        "eager_receiver_frames_per_s": cached_eager_val,
+        "graph_results_identical_to_eager": bool(graph_same),
         "frame_ms_median": float(np.median(cached_frame_ms)),
         "stage_ms_median": cached_stages,
         "frame_ms_max": float(np.max(cached_frame_ms)),

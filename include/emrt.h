@@ -22,6 +22,14 @@
  * Doppler shift (Sec. III-C, Eq. 3), reduced per receiver into the
  * statistics of Table III (Sec. V-D).
  *
+ * Per-frame calls (emrt_scene_update_dynamic, emrt_trace, emrt_rediscover,
+ * emrt_revalidate, emrt_cache_merge, emrt_channel, emrt_channel_multi,
+ * emrt_batch_trace) allocate only when a problem larger than any before
+ * arrives and do not synchronise the host while their stream is being
+ * captured; once a call has run with its sizes, the same call can be
+ * recorded into a caller's CUDA graph (stream capture) and replayed,
+ * reading its inputs from the same device buffers.
+ *
  * Geometry conventions
  *  - float32 metres centred on the scene origin, z up.
  *  - Static faces are convex planar polygons (CCW seen from outside); the
@@ -386,7 +394,8 @@ typedef struct {
   /* device time of the last emrt_trace (CUDA events on its stream), ms:
    * discovery stage (traversal kernels and ray sorts), deduplication,
    * image-method acceptance, whole call, and the closest-hit traversal
-   * kernels alone (sum over bounces) */
+   * kernels alone (sum over bounces); a trace recorded into a caller's CUDA
+   * graph and replayed from it leaves them at their last values */
   float traverse_ms, dedup_ms, accept_ms, trace_ms, bounce_ms;
   uint32_t pad2;
   uint64_t static_reused;     /* segments whose static closest hit came from

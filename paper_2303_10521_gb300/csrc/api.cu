@@ -999,6 +999,9 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
         cudaEventElapsedTime(&t, s->evb[2 * b], s->evb[2 * b + 1]);
         out->bounce_ms += t;
       }
+      // a trace recorded into a caller's CUDA graph leaves these events
+      // without a time: the query's error is dropped, not reported later
+      (void)cudaGetLastError();
     }
     out->required_candidates = h.n_cand;
     out->required_paths = h.n_accepted;
