@@ -248,7 +248,7 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   s->stat.pad = pad;
   // static geometry: binned-SAH tree (built once); the LBVH if the SAH tree
   // would be deeper than the traversal stack
-  if (bvh_build_tris_sah(s->stat, d->tri_xyz, d->tri_face, s->T, s->Fs, st) != cudaSuccess) {
+  if (bvh_build_tris_sah(s->stat, d->tri_xyz, d->tri_face, s->T, st) != cudaSuccess) {
     cudaGetLastError();
     if ((e = bvh_build_tris(s->stat, d->tri_xyz, d->tri_face, s->T, s->bbox, s->hist, st)))
       return fail(e);

@@ -601,48 +601,49 @@ __global__ void k_tri_bounds(const float *t, uint32_t n, float4 *cen, float4 *lo
   perm[i] = i;
 }
 
-// Leaf clusters of the SAH build: the two triangles of a face made of exactly
-// two (a planar quad -- a wall, a ground tile -- whose triangles share one
-// bounding box) form one leaf, every other triangle a leaf of its own.  The
-// quad's two tests are those the two single-triangle leaves would get
-// whenever its box is entered; the inner node that split them is saved.
-__global__ void k_face_tris(const uint32_t *tri_face, uint32_t n, uint32_t n_faces,
-                            uint32_t *cnt, uint32_t *first, uint32_t *last) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t f = tri_face[i];
-  if (f >= n_faces) return;
-  atomicAdd(&cnt[f], 1u);
-  atomicMin(&first[f], i);
-  atomicMax(&last[f], i);
+// Leaf clusters of the SAH build: two consecutive triangles of one face with
+// the same bounding box (the two halves of a planar quad -- a wall, a ground
+// tile) form one leaf, every other triangle a leaf of its own.  The pair's
+// two tests are those the two single-triangle leaves would get whenever
+// their common box is entered; the inner node that split them is saved.
+// Triangle i+1 joins i when the pair matches and i does not itself join
+// i-1, so pairs never overlap.
+__device__ inline bool same_box_pair(const float *t, const uint32_t *tri_face, uint32_t n,
+                                     uint32_t i) {
+  if (i + 1 >= n || tri_face[i] != tri_face[i + 1]) return false;
+  const float *a = t + 9ull * i, *b = a + 9;
+  for (int d = 0; d < 3; d++) {
+    const float alo = fminf(a[d], fminf(a[3 + d], a[6 + d]));
+    const float ahi = fmaxf(a[d], fmaxf(a[3 + d], a[6 + d]));
+    const float blo = fminf(b[d], fminf(b[3 + d], b[6 + d]));
+    const float bhi = fmaxf(b[d], fmaxf(b[3 + d], b[6 + d]));
+    if (alo != blo || ahi != bhi) return false;
+  }
+  return true;
 }
 
-__device__ inline bool quad_face(const uint32_t *tri_face, uint32_t n_faces, const uint32_t *cnt,
-                                 uint32_t i, uint32_t &f) {
-  f = tri_face[i];
-  return f < n_faces && cnt[f] == 2u;
+__device__ inline bool joins_previous(const float *t, const uint32_t *tri_face, uint32_t n,
+                                      uint32_t i) {
+  return i > 0 && same_box_pair(t, tri_face, n, i - 1) &&
+         !(i > 1 && same_box_pair(t, tri_face, n, i - 2));
 }
 
-// flag[i] = 1 when triangle i starts a cluster (quad clustering on or off)
-__global__ void k_cluster_flags(const uint32_t *tri_face, uint32_t n, uint32_t n_faces,
-                                const uint32_t *cnt, const uint32_t *first, int quads,
+// flag[i] = 1 when triangle i starts a cluster (pairing on or off)
+__global__ void k_cluster_flags(const float *t, const uint32_t *tri_face, uint32_t n, int pairs,
                                 uint32_t *flag) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t f;
-  flag[i] = (!quads || !quad_face(tri_face, n_faces, cnt, i, f) || first[f] == i) ? 1u : 0u;
+  flag[i] = (!pairs || !joins_previous(t, tri_face, n, i)) ? 1u : 0u;
 }
 
 // cluster list (first triangle, second triangle or ~0) and the SAH inputs:
 // box of the cluster, centroid = mean of its triangles' centroids
-__global__ void k_cluster_bounds(const float *t, const uint32_t *tri_face, uint32_t n,
-                                 uint32_t n_faces, const uint32_t *cnt, const uint32_t *last,
-                                 int quads, const uint32_t *flag, const uint32_t *pos,
-                                 uint2 *cl, float4 *cen, float4 *lo, float4 *hi, uint32_t *perm) {
+__global__ void k_cluster_bounds(const float *t, const uint32_t *tri_face, uint32_t n, int pairs,
+                                 const uint32_t *flag, const uint32_t *pos, uint2 *cl, float4 *cen,
+                                 float4 *lo, float4 *hi, uint32_t *perm) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || !flag[i]) return;
-  uint32_t f;
-  const uint32_t j = (quads && quad_face(tri_face, n_faces, cnt, i, f)) ? last[f] : 0xffffffffu;
+  const uint32_t j = (pairs && joins_previous(t, tri_face, n, i + 1)) ? i + 1 : 0xffffffffu;
   const uint32_t c = pos[i];
   cl[c] = make_uint2(i, j);
   float a[3] = {3.4e38f, 3.4e38f, 3.4e38f}, b[3] = {-3.4e38f, -3.4e38f, -3.4e38f}, m[3] = {0, 0, 0};
@@ -910,15 +911,14 @@ __global__ void __launch_bounds__(kSahBlock) k_sah_level(
 }  // namespace
 
 cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_face, uint32_t n,
-                               uint32_t n_faces, cudaStream_t s) {
+                               cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
   cudaError_t e;
   float4 *cen = nullptr, *lo = nullptr, *hi = nullptr;
-  uint32_t *tmp = nullptr, *ctr = nullptr, *fbuf = nullptr, *cbuf = nullptr;
+  uint32_t *tmp = nullptr, *ctr = nullptr, *cbuf = nullptr;
   uint2 *cl = nullptr;
   SahTask *tasks[2] = {nullptr, nullptr};
-  const uint32_t nf = n_faces ? n_faces : 1u;
   if ((e = cudaMalloc(&cen, sizeof(float4) * n))) return e;
   if ((e = cudaMalloc(&lo, sizeof(float4) * n))) return e;
   if ((e = cudaMalloc(&hi, sizeof(float4) * n))) return e;
@@ -926,27 +926,21 @@ cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *
   if ((e = cudaMalloc(&tasks[0], sizeof(SahTask) * (n / 2 + 2)))) return e;
   if ((e = cudaMalloc(&tasks[1], sizeof(SahTask) * (n / 2 + 2)))) return e;
   if ((e = cudaMalloc(&ctr, sizeof(uint32_t) * 8))) return e;
-  if ((e = cudaMalloc(&fbuf, sizeof(uint32_t) * 3 * (size_t)nf))) return e;
   // flags, positions, cluster leaf parents, sizes, starts, scan partials
   if ((e = cudaMalloc(&cbuf, sizeof(uint32_t) * (5 * (size_t)n + kPrimGrid + 1)))) return e;
   if ((e = cudaMalloc(&cl, sizeof(uint2) * n))) return e;
-  uint32_t *cnt = fbuf, *first = fbuf + nf, *last = fbuf + 2 * nf;
   uint32_t *flag = cbuf, *pos = cbuf + n, *lp_cl = cbuf + 2 * (size_t)n, *sz = cbuf + 3 * (size_t)n,
            *tstart = cbuf + 4 * (size_t)n, *partial = cbuf + 5 * (size_t)n;
-  cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nf, s);
-  cudaMemsetAsync(first, 0xff, sizeof(uint32_t) * nf, s);
-  cudaMemsetAsync(last, 0, sizeof(uint32_t) * nf, s);
-  emrt::note_launch(), k_face_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_face, n, n_faces, cnt, first, last);
-  // clusters: quads kept together unless that leaves fewer than two leaves
+  // clusters: pairs kept together unless that leaves fewer than two leaves
   uint32_t nc = 0;
-  for (int quads = 1; quads >= 0; quads--) {
-    emrt::note_launch(), k_cluster_flags<<<ceil_div(n, 256), 256, 0, s>>>(tri_face, n, n_faces, cnt, first, quads, flag);
+  for (int pairs = 1; pairs >= 0; pairs--) {
+    emrt::note_launch(), k_cluster_flags<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, n, pairs, flag);
     emrt::note_launch(), k_set_u32<<<1, 1, 0, s>>>(ctr + 4, n);
     exclusive_scan(ctr + 4, flag, pos, ctr + 5, partial, s);
     cudaMemcpyAsync(&nc, ctr + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) break;
     emrt::note_launch(), k_cluster_bounds<<<ceil_div(n, 256), 256, 0, s>>>(
-        tri_xyz, tri_face, n, n_faces, cnt, last, quads, flag, pos, cl, cen, lo, hi, b.idx);
+        tri_xyz, tri_face, n, pairs, flag, pos, cl, cen, lo, hi, b.idx);
     if (nc >= 2 || n < 2) break;
   }
   if (!e && nc >= 2) {
@@ -988,7 +982,7 @@ cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *
     if (!e) b.leaf_bits = 2;
   }
   cudaFree(cen); cudaFree(lo); cudaFree(hi); cudaFree(tmp);
-  cudaFree(tasks[0]); cudaFree(tasks[1]); cudaFree(ctr); cudaFree(fbuf); cudaFree(cbuf);
+  cudaFree(tasks[0]); cudaFree(tasks[1]); cudaFree(ctr); cudaFree(cbuf);
   cudaFree(cl);
   if (e) return e;
   return cudaGetLastError();

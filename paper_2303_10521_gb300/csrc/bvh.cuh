@@ -48,11 +48,12 @@ cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint3
 cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const float4 *bbox,
                              uint32_t *hist, cudaStream_t s);
 // Top-down binned-SAH build of a triangle BVH (same node format as the
-// LBVH; used for the static geometry, which is built once).  The two
-// triangles of a face made of exactly two (faces 0..n_faces-1 of tri_face)
-// share one leaf; other leaves hold one triangle.  Synchronises.
+// LBVH; used for the static geometry, which is built once).  Two
+// consecutive triangles of one face with the same bounding box (the halves
+// of a planar quad) share one leaf; other leaves hold one triangle.
+// Synchronises.
 cudaError_t bvh_build_tris_sah(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_face,
-                               uint32_t n, uint32_t n_faces, cudaStream_t s);
+                               uint32_t n, cudaStream_t s);
 // Moves box primitives to new corners (vehicle id kept in lo.w) and refits.
 cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaStream_t s);
 
