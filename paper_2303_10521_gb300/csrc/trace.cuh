@@ -67,7 +67,7 @@ void launch_walk(const BounceLaunch &L, cudaStream_t s, bool wide = false);
 // differs (bitwise) from ref[t]
 void launch_tx_epoch(const float4 *pos, float4 *ref, uint32_t *epoch, uint32_t n_tx,
                      cudaStream_t s);
-// wide: traverse the static BVH's 4-wide collapse
+// wide: static closest hits through the compressed 8-wide tree
 void launch_bounce(const BounceLaunch &L, int grid, cudaStream_t s, bool wide = false);
 int bounce_grid();  // persistent grid size (SMs x resident blocks)
 

@@ -125,8 +125,8 @@ def test_toy_scene_full_parity(engine):
 def test_district_subsample_parity(engine, stride, offset, form):
     """District (400 buildings, 200 vehicles, 1000 Rx, 2 Tx, K = 3) on a
     strided subset of the 1M rays, traced identically on both sides; the
-    default depth-first discovery and the breadth-first discovery through the
-    4-wide BVH."""
+    default depth-first discovery through the binary BVH and through the
+    compressed 8-wide BVH."""
     sc = S.district_scene(seed=0)
     fr = sc.frame(0)
     g = _gpu(engine, sc)
