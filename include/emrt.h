@@ -450,7 +450,9 @@ emrt_status emrt_batch_create(const emrt_scene *scenes, uint32_t n,
  * pinned per-scene table is copied by a node of the caller's graph, so the
  * scenes must keep their transmitter and receiver counts while the caller's
  * graph is replayed); calling it before the first uncaptured call returns
- * EMRT_ERR_STATE. */
+ * EMRT_ERR_STATE.  Begin such a capture after the batch's earlier calls have
+ * completed (e.g. after emrt_batch_sync): the captured call rewrites the
+ * pinned table without waiting for a copy still pending from them. */
 emrt_status emrt_batch_trace(emrt_batch b, emrt_stream s);
 /* Waits and reports errors as emrt_sync (stats summed over the batch). */
 emrt_status emrt_batch_sync(emrt_batch b, emrt_stream s, emrt_stats *st);
