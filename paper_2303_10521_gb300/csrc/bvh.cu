@@ -450,6 +450,144 @@ __global__ void k_bbox_fin(const uint32_t *acc, float4 *bb) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-block LBVH build of a small per-frame tree (n <= kSmallBuildMax boxes or
+// points): Morton codes, a bitonic sort of (code << 32 | index) keys in
+// shared memory, the Karras hierarchy over the sorted keys, the primitives
+// gathered in leaf order and the bottom-up boxes -- one launch where the
+// device-wide path takes about twenty (code, four sort passes of three
+// kernels, gather, hierarchy, flag reset, refit) whose launch latencies set
+// the time of a small tree's update.  The index in the low key bits makes
+// every key distinct, which is the tie-break of equal codes by position.
+// Above 4096 primitives the one block's sort costs more than the launches
+// it saves (measured: the city's 15k-primitive merged tree took 0.57 ms of
+// update instead of 0.25), so larger trees take the device-wide path.
+constexpr uint32_t kSmallBuildMax = 4096;
+constexpr int kSmallBlock = 1024;
+
+__device__ inline int delta_u64(const unsigned long long *k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  return __clzll(k[i] ^ k[j]);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kSmallBlock) k_small_build(
+    const float4 *a, const float4 *b, uint32_t n, uint32_t np2, const float4 *bb, float4 *prims,
+    float4 *nodes, uint32_t *leaf_parent, float pad) {
+  extern __shared__ unsigned long long sk[];   // np2 keys, then n arrival counters
+  uint32_t *sflag = reinterpret_cast<uint32_t *>(sk + np2);
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t i = tid; i < np2; i += blockDim.x) {
+    unsigned long long key = ~0ull;
+    if (i < n) {
+      const float4 p = a[i];
+      float3 c = f3(p);
+      if (KIND == PRIM_BOX) {
+        const float4 q = b[i];
+        c = make_float3(0.5f * (p.x + q.x), 0.5f * (p.y + q.y), 0.5f * (p.z + q.z));
+      }
+      key = (unsigned long long)morton_code<kMortonBitsDyn>(c, bb) << 32 | i;
+    }
+    sk[i] = key;
+  }
+  for (uint32_t i = tid; i < n; i += blockDim.x) sflag[i] = 0u;
+  __syncthreads();
+  for (uint32_t k = 2; k <= np2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = tid; i < (np2 >> 1); i += blockDim.x) {
+        const uint32_t lo = 2u * i - (i & (j - 1u)), hi = lo + j;
+        const unsigned long long x = sk[lo], y = sk[hi];
+        if ((x > y) == ((lo & k) == 0u)) {
+          sk[lo] = y;
+          sk[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // primitives in leaf order (the source index kept in .w)
+  for (uint32_t g = tid; g < n; g += blockDim.x) {
+    const uint32_t src = (uint32_t)sk[g];
+    const float4 p = a[src];
+    if (KIND == PRIM_BOX) {
+      const float4 q = b[src];
+      prims[2ull * g + 0] = make_float4(p.x, p.y, p.z, __uint_as_float(src));
+      prims[2ull * g + 1] = make_float4(q.x, q.y, q.z, 0.f);
+    } else {
+      prims[g] = make_float4(p.x, p.y, p.z, __uint_as_float(src));
+    }
+  }
+  if (n < 2) return;
+  // hierarchy: inner node i over the sorted keys
+  const int nn = (int)n;
+  for (int i = (int)tid; i < nn - 1; i += (int)blockDim.x) {
+    const int d = (delta_u64(sk, nn, i, i + 1) - delta_u64(sk, nn, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta_u64(sk, nn, i, i - d);
+    int lmax = 2;
+    while (delta_u64(sk, nn, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+      if (delta_u64(sk, nn, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta_u64(sk, nn, i, j);
+    int sp = 0, t = l;
+    do {
+      t = (t + 1) >> 1;
+      if (delta_u64(sk, nn, i, i + (sp + t) * d) > dnode) sp += t;
+    } while (t > 1);
+    const int gamma = i + sp * d + min(d, 0);
+    const int left = min(i, j) == gamma ? ~gamma : gamma;
+    const int right = max(i, j) == gamma + 1 ? ~(gamma + 1) : gamma + 1;
+    int *n3 = reinterpret_cast<int *>(nodes + 4ll * i + 3);
+    n3[0] = left;
+    n3[1] = right;
+    n3[3] = 0;
+    if (left < 0) leaf_parent[~left] = 2u * i;
+    else reinterpret_cast<int *>(nodes + 4ll * left + 3)[2] = 2 * i;
+    if (right < 0) leaf_parent[~right] = 2u * i + 1u;
+    else reinterpret_cast<int *>(nodes + 4ll * right + 3)[2] = 2 * i + 1;
+    if (i == 0) n3[2] = -1;
+  }
+  __threadfence_block();
+  __syncthreads();
+  // bottom-up boxes: the second thread to reach a node merges its children
+  for (uint32_t g = tid; g < n; g += blockDim.x) {
+    Box bx = prim_box<KIND>(prims, g);
+    bx.lo = make_float3(bx.lo.x - pad, bx.lo.y - pad, bx.lo.z - pad);
+    bx.hi = make_float3(bx.hi.x + pad, bx.hi.y + pad, bx.hi.z + pad);
+    int code = (int)__ldcg(leaf_parent + g);
+    for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
+      const int p = code >> 1, side = code & 1;
+      float4 *np = nodes + 4ll * p;
+      reinterpret_cast<float4 *>(np + side)[0] = make_float4(bx.lo.x, bx.hi.x, bx.lo.y, bx.hi.y);
+      reinterpret_cast<float2 *>(np + 2)[side] = make_float2(bx.lo.z, bx.hi.z);
+      __threadfence();
+      if (atomicAdd(&sflag[p], 1u) == 0) break;
+      __threadfence();
+      const float4 a0 = __ldcg(np), a1 = __ldcg(np + 1), a2 = __ldcg(np + 2);
+      bx.lo = make_float3(fminf(a0.x, a1.x), fminf(a0.z, a1.z), fminf(a2.x, a2.z));
+      bx.hi = make_float3(fmaxf(a0.y, a1.y), fmaxf(a0.w, a1.w), fmaxf(a2.y, a2.w));
+      const int pc = __ldcg(reinterpret_cast<const int *>(np + 3) + 2);
+      if (pc < 0) break;
+      code = pc;
+    }
+  }
+}
+
+template <int KIND>
+cudaError_t small_build(BVHBuf &b, const float4 *a, const float4 *bx, uint32_t n,
+                        const float4 *bbox, cudaStream_t s) {
+  uint32_t np2 = 2;
+  while (np2 < n) np2 <<= 1;
+  const size_t smem = sizeof(unsigned long long) * np2 + sizeof(uint32_t) * n;
+  static_assert(sizeof(unsigned long long) * kSmallBuildMax + sizeof(uint32_t) * kSmallBuildMax <=
+                    48 * 1024,
+                "the one-block build fits the default shared-memory limit");
+  emrt::note_launch(), k_small_build<KIND><<<1, kSmallBlock, smem, s>>>(a, bx, n, np2, bbox, b.prims,
+                                                                       b.nodes, b.leaf_parent, b.pad);
+  return cudaGetLastError();
+}
+
 template <int KIND>
 cudaError_t finish_build(BVHBuf &b, cudaStream_t s) {
   uint32_t n = b.n;
@@ -536,6 +674,7 @@ cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint3
                             const float4 *bbox, uint32_t *hist, cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
+  if (n <= kSmallBuildMax) return small_build<PRIM_BOX>(b, lo, hi, n, bbox, s);
   emrt::note_launch(), k_morton_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_BOX>(b, hist, s);
   emrt::note_launch(), k_gather_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, b.idx, n, b.prims);
@@ -557,6 +696,7 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
                              uint32_t *hist, cudaStream_t s) {
   b.n = n;
   if (n == 0) return cudaSuccess;
+  if (n <= kSmallBuildMax) return small_build<PRIM_POINT>(b, pts, nullptr, n, bbox, s);
   emrt::note_launch(), k_morton_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_POINT>(b, hist, s);
   emrt::note_launch(), k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, b.idx, n, b.prims);
