@@ -106,3 +106,35 @@ def test_cpu_baseline_scales_only_the_ray_work():
     assert r["frame_s_extrapolated"] == pytest.approx(frame_s)
     assert r["value"] == pytest.approx(len(sc.frame(0).rx_pos) / frame_s)
     assert r["segments"] > 0 and r["s_per_segment"] > 0
+
+
+def test_oracle_check_counts_and_errors():
+    """The bench's untimed FP64 check on records and fields it is handed: a
+    path set the oracle accepts with its own fields gives no rejection and
+    zero error; a field perturbed by 1e-3 shows up as that error."""
+    import numpy as np
+    import oracle
+    from paper_2303_10521_gb300 import scenes
+    sc = scenes.toy_scene(seed=0)
+    fr = sc.frame(0)
+    o = oracle.OracleScene(sc, fr)
+    p = oracle.enumerate_paths(o, 2)
+    acc, _ = oracle.validate(o, p)
+    p = p[acc][:40]
+    rec = np.zeros((len(p), 8), np.uint32)
+    rec[:, 0], rec[:, 1] = p["tx"], p["rx"]
+    rec[:, 2] = p["depth"] | 0x100
+    rec[:, 3:7] = p["face"]
+    fields = []
+    for f in sc.freqs:
+        a, tau, fd = oracle.field(o, p, f)
+        fields.append(np.column_stack([a.real, a.imag, tau, fd]))
+    r = bench.oracle_check(sc, fr, rec, fields, rec)
+    assert r["paths"] == len(p) and r["oracle_rejects"] == 0
+    assert r["acceptance_disagreements"] == 0
+    e = r["field_vs_fp64_oracle"][f"{sc.freqs[0] / 1e9:g} GHz"]
+    assert e["max_rel_amplitude_error"] == 0.0 and e["max_phase_error_rad"] < 1e-15
+    fields[0][3, 0:2] *= 1.001
+    r = bench.oracle_check(sc, fr, rec, fields, None)
+    e = r["field_vs_fp64_oracle"][f"{sc.freqs[0] / 1e9:g} GHz"]
+    assert e["max_rel_amplitude_error"] == pytest.approx(1e-3, rel=1e-6)
