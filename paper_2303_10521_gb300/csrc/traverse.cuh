@@ -48,9 +48,9 @@ __device__ inline void ray_setup(RayQ &r, float3 o, float3 d) {
   float dz = sel3(d, kz);
   if (dz < 0.f) { int t = kx; kx = ky; ky = t; }
   r.kx = kx; r.ky = ky; r.kz = kz;
-  r.Sx = sel3(d, kx) / dz;
-  r.Sy = sel3(d, ky) / dz;
   r.Sz = 1.f / dz;
+  r.Sx = sel3(d, kx) * r.Sz;
+  r.Sy = sel3(d, ky) * r.Sz;
 }
 
 // slab test of one child box against [tmin, tmax]; conservative far bound
@@ -286,7 +286,9 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
   bool hit = false;
   int sp = 0;
   int node = b.root;
-  uint32_t iter = 0;
+  // node visits bound the loop (every leaf visit follows a visit or a pop of
+  // an entry a visit pushed): a well-formed tree never comes close
+  const uint32_t lim = st.nodes > 0xffffffffu - kMaxIter ? 0xffffffffu : st.nodes + kMaxIter;
   // a popped subtree is skipped only when its entry lies beyond the bound
   // with the slab test's own slack (closest hit), so that pruning on pop and
   // on visit agree and exact ties in t can still reach the lower face ID
@@ -295,7 +297,10 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
     // descend through inner nodes until this lane reaches a leaf, so that
     // the lanes of a warp test their leaves together
     while (node >= 0) {
-      EMRT_ITER_GUARD(st)
+      if (st.nodes >= lim) {
+        st.overflow = true;
+        return hit;
+      }
       const float4 *np = b.nodes + 4ll * node;
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
       st.nodes++;
@@ -322,7 +327,6 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
       }
       node = stk[sp].node;
     }
-    EMRT_ITER_GUARD(st)
     if (leaf_tri<ANY>(b, (uint32_t)(~node), r, tmin, tmax, face, ex0, ex1, st)) {
       hit = true;
       if (ANY) return true;
