@@ -81,6 +81,10 @@ def parse():
                     help="cached legs: trace without the static-hit cache")
     ap.add_argument("--profile", action="store_true",
                     help="timed plain frames only (no e2e, cache or CPU legs)")
+    ap.add_argument("--profile-cached", action="store_true",
+                    help="cached frames only, call by call (for launch lists): a full "
+                         "trace fills the cache, then --steps frames of revalidation, "
+                         "N/10 rediscovery with the static-hit cache and fields")
     return ap.parse_args()
 
 
@@ -693,6 +697,24 @@ def main():
     cap = paths.capacity
     out = engine.Paths(cap * 2, dev)
     chs = [None, None]
+    if args.profile_cached:
+        cache = engine.Paths(cap * 4, dev)
+        g.trace_async(cache, static_cache=True)
+        g.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(1, total):
+            g.update(frames[k])
+            g.rediscover(cache, n_rays=sc.n_rays // max(args.rediscovery_fraction, 1),
+                         static_cache=True, revalidate=True)
+            chs[:] = g.channels(cache, sc.freqs, outs=chs)
+            g.sync()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_cached": True, "frames": total - 1,
+                          "ms_per_frame": e0.elapsed_time(e1) / max(1, total - 1),
+                          "paths": cache.n()}), flush=True)
+        return
 
     sort_rays = not args.no_sort_rays
     bf = args.breadth_first
