@@ -65,18 +65,45 @@ __device__ inline bool slab(const RayQ &r, float lx, float hx, float ly, float h
   return tn <= tf * 1.00000024f;
 }
 
-// Slab test of one child box with separate origin terms for the low and high
-// planes (t = p idir - ol for the low planes, p idir - oh for the high ones)
-// and tmin = 0.  ol = oh = o idir is slab() exactly; ol = (o + e) idir and
-// oh = (o - e) idir test the box grown by e on every side.
-__device__ inline bool slab_lh(const float3 &idir, const float3 &ol, const float3 &oh, float lx,
-                               float hx, float ly, float hy, float lz, float hz, float tmax,
-                               float &tnear) {
-  float t0x = fmaf(lx, idir.x, -ol.x), t1x = fmaf(hx, idir.x, -oh.x);
-  float t0y = fmaf(ly, idir.y, -ol.y), t1y = fmaf(hy, idir.y, -oh.y);
-  float t0z = fmaf(lz, idir.z, -ol.z), t1z = fmaf(hz, idir.z, -oh.z);
-  float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
-  float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+// Two FMAs in one packed f32x2 instruction (sm_100 and later); each lane is
+// rounded exactly like fmaf, so results equal the scalar form bit for bit.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+      "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// The ray's slab terms as lane pairs for ffma2, per axis (idir, idir) and
+// the origin terms of the low and the high plane, (-ol, -oh): t = p idir - ol
+// for the low planes, p idir - oh for the high ones.  ray_pairs(): ol = oh =
+// o idir, slab() exactly; ray_pairs_lh() with ol = (o + e) idir and oh =
+// (o - e) idir tests the box grown by e on every side.
+struct RayPairs {
+  float2 ix, iy, iz, ox, oy, oz;
+};
+__device__ inline RayPairs ray_pairs(const RayQ &r) {
+  return RayPairs{make_float2(r.idir.x, r.idir.x), make_float2(r.idir.y, r.idir.y),
+                  make_float2(r.idir.z, r.idir.z), make_float2(-r.ood.x, -r.ood.x),
+                  make_float2(-r.ood.y, -r.ood.y), make_float2(-r.ood.z, -r.ood.z)};
+}
+__device__ inline RayPairs ray_pairs_lh(const float3 &idir, const float3 &ol, const float3 &oh) {
+  return RayPairs{make_float2(idir.x, idir.x), make_float2(idir.y, idir.y),
+                  make_float2(idir.z, idir.z), make_float2(-ol.x, -oh.x),
+                  make_float2(-ol.y, -oh.y), make_float2(-ol.z, -oh.z)};
+}
+
+// slab() with the low and the high plane of each axis in one packed FMA
+__device__ inline bool slab_p(const RayPairs &q, float lx, float hx, float ly, float hy, float lz,
+                              float hz, float tmin, float tmax, float &tnear) {
+  const float2 tx = ffma2(make_float2(lx, hx), q.ix, q.ox);
+  const float2 ty = ffma2(make_float2(ly, hy), q.iy, q.oy);
+  const float2 tz = ffma2(make_float2(lz, hz), q.iz, q.oz);
+  float tn = fmaxf(fmaxf(fminf(tx.x, tx.y), fminf(ty.x, ty.y)), fmaxf(fminf(tz.x, tz.y), tmin));
+  float tf = fminf(fminf(fmaxf(tx.x, tx.y), fmaxf(ty.x, ty.y)), fminf(fmaxf(tz.x, tz.y), tmax));
   tnear = tn;
   return tn <= tf * 1.00000024f;
 }
@@ -234,18 +261,27 @@ __device__ inline bool trace_tris8(const BVHView &b, const RayQ &r, float tmin, 
       const uint32_t fy0 = ny ? qy.x : qy.z, fy1 = ny ? qy.y : qy.w;
       const uint32_t nz0 = nz ? qz.z : qz.x, nz1 = nz ? qz.w : qz.y;
       const uint32_t fz0 = nz ? qz.x : qz.z, fz1 = nz ? qz.y : qz.w;
+      // near and far plane of an axis in one packed FMA
+      const float2 ax2 = make_float2(ax, ax), ay2 = make_float2(ay, ay), az2 = make_float2(az, az);
+      const float2 cx2 = make_float2(cx, cx), cy2 = make_float2(cy, cy), cz2 = make_float2(cz, cz);
       uint32_t hits = 0;
 #pragma unroll
       for (int sl = 0; sl < 8; sl++) {
         const uint32_t sel = 0x7440u | (uint32_t)(sl & 3);
-        const float tnx = fmaf(__uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x4B000000u, sel)), ax, cx);
-        const float tfx = fmaf(__uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x4B000000u, sel)), ax, cx);
-        const float tny = fmaf(__uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x4B000000u, sel)), ay, cy);
-        const float tfy = fmaf(__uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x4B000000u, sel)), ay, cy);
-        const float tnz = fmaf(__uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x4B000000u, sel)), az, cz);
-        const float tfz = fmaf(__uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x4B000000u, sel)), az, cz);
-        const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, tmin));
-        const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+        const float2 tx = ffma2(
+            make_float2(__uint_as_float(__byte_perm(sl < 4 ? nx0 : nx1, 0x4B000000u, sel)),
+                        __uint_as_float(__byte_perm(sl < 4 ? fx0 : fx1, 0x4B000000u, sel))),
+            ax2, cx2);
+        const float2 ty = ffma2(
+            make_float2(__uint_as_float(__byte_perm(sl < 4 ? ny0 : ny1, 0x4B000000u, sel)),
+                        __uint_as_float(__byte_perm(sl < 4 ? fy0 : fy1, 0x4B000000u, sel))),
+            ay2, cy2);
+        const float2 tz = ffma2(
+            make_float2(__uint_as_float(__byte_perm(sl < 4 ? nz0 : nz1, 0x4B000000u, sel)),
+                        __uint_as_float(__byte_perm(sl < 4 ? fz0 : fz1, 0x4B000000u, sel))),
+            az2, cz2);
+        const float tn = fmaxf(fmaxf(tx.x, ty.x), fmaxf(tz.x, tmin));
+        const float tf = fminf(fminf(tx.y, ty.y), fminf(tz.y, tmax));
         if (tn <= tf * 1.00000024f) hits |= 1u << sl;
       }
       const uint32_t imask = h0.w >> 24, lmask = h1.x >> 24;
@@ -293,6 +329,7 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
   // with the slab test's own slack (closest hit), so that pruning on pop and
   // on visit agree and exact ties in t can still reach the lower face ID
   const float pop_slack = ANY ? 1.f : 1.00000024f;
+  const RayPairs rp = ray_pairs(r);
   for (;;) {
     // descend through inner nodes until this lane reaches a leaf, so that
     // the lanes of a warp test their leaves together
@@ -305,8 +342,8 @@ __device__ inline bool trace_tris(const BVHView &b, const RayQ &r, float tmin, f
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
       st.nodes++;
       float tn0, tn1;
-      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
-      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
+      bool h0 = slab_p(rp, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
+      bool h1 = slab_p(rp, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
         int nearc = c0, farc = c1;
@@ -370,6 +407,7 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
                                    uint32_t &face, uint32_t fs, uint32_t exv0, uint32_t exv1,
                                    StackSlot *stk, TravStats &st) {
   if (b.n_prims == 0) return false;
+  const RayPairs rp = ray_pairs(r);
   bool hit = false;
   int sp = 0;
   int node = b.root;
@@ -381,8 +419,8 @@ __device__ inline bool trace_boxes(const BVHView &b, const RayQ &r, float tmin, 
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
       st.dnodes++;
       float tn0, tn1;
-      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
-      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
+      bool h0 = slab_p(rp, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmin, tmax, tn0);
+      bool h1 = slab_p(rp, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmin, tmax, tn1);
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
         int nearc = c0, farc = c1;
@@ -442,6 +480,7 @@ __device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax
                                 r.ood.z + rmax * r.idir.z);
   const float3 oh = make_float3(r.ood.x - rmax * r.idir.x, r.ood.y - rmax * r.idir.y,
                                 r.ood.z - rmax * r.idir.z);
+  const RayPairs rp = ray_pairs_lh(r.idir, ol, oh);
   int sp = 0;
   int node = b.root;
   float tcur = 0.f;  // entry distance of the node being visited
@@ -456,8 +495,8 @@ __device__ inline void trace_veh_rx(const BVHView &b, const RayQ &r, float &tmax
       float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
       st.dnodes++;
       float tn0, tn1;
-      bool h0 = slab_lh(r.idir, ol, oh, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax, tn0);
-      bool h1 = slab_lh(r.idir, ol, oh, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax, tn1);
+      bool h0 = slab_p(rp, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, 0.f, tmax, tn0);
+      bool h1 = slab_p(rp, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, 0.f, tmax, tn1);
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
         int nearc = c0, farc = c1;
