@@ -52,7 +52,13 @@ __device__ inline float escape_t(float3 o, float3 d, float3 rlo, float3 rhi) {
          fmaxf(d.z * (rlo.z - o.z), d.z * (rhi.z - o.z));
 }
 
-constexpr int kRxBuf = 4;  // receivers buffered per segment by the merged query
+// Receivers buffered per segment by the merged query (in local memory).  A
+// segment that meets more takes the receiver-tree query instead, a second
+// traversal with grown boxes; with 4 those were the cache walker's slowest
+// chunks at low ray densities (large reception spheres): 64 took the city's
+// N/10 rediscovery walk from 0.66-0.73 to 0.52-0.60 ms, 128 and 256 gained
+// nothing more, and the full-density traces did not change.
+constexpr int kRxBuf = 64;
 
 // Vehicle boxes and reception spheres of one segment after its static
 // closest hit (tbest, face): one traversal of the merged vehicle + receiver

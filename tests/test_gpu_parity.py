@@ -374,6 +374,34 @@ def test_edge_cases(engine):
     assert small.n() > 2
 
 
+@pytest.mark.parametrize("form", ["depth_first", "breadth_first", "static_cache"])
+def test_dense_receiver_cluster(engine, form):
+    """Segments whose reception spheres hold more receivers than the merged
+    query buffers (64) take the receiver-tree query instead; the detections
+    are the oracle's either way.  A cube of 1000 receivers 20 m from the
+    transmitter, 5000 rays (sphere radius ~0.8 m there): the rays through it
+    detect ~200 receivers each."""
+    E = engine
+    rng = np.random.default_rng(3)
+    rx = np.column_stack([rng.uniform(18.5, 21.5, 1000), rng.uniform(-1.5, 1.5, 1000),
+                          rng.uniform(0.5, 3.5, 1000)])
+    sc = S.custom_scene([S.rect_xy(-60, -60, 60, 60)], [0], (0, 0, 10), rx, n_rays=5000,
+                        depth=1)
+    g = _gpu(E, sc)
+    p = g.trace(keep_rejected=True, breadth_first=form == "breadth_first",
+                static_cache=form == "static_cache")
+    st = g.last_stats
+    assert st["rx_node_visits"] > 0, st  # the receiver-tree query ran
+    o = oracle.OracleScene(sc, sc.frame(0))
+    gu = rec_to_paths(p.records())
+    cands, ray_marg, _ = oracle.trace(o, sc.n_rays, sc.max_depth)
+    assert len(cands) > 500
+    rc = compare_candidates(gu, cands, ray_marg)
+    assert not rc["missing"] and not rc["extra_bad"], rc
+    ra = compare_acceptance(o, gu)
+    assert ra["n_diff_unflagged"] == 0, ra
+
+
 def test_tree_builders_agree_at_the_size_threshold(engine):
     """Per-frame trees of up to 4096 primitives are built by one block, larger
     ones by the device-wide path; the trees differ but every query is exact,
