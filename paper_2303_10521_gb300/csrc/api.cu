@@ -259,6 +259,9 @@ emrt_status emrt_scene_create(const emrt_scene_desc *d, emrt_stream stream, emrt
   if ((e = bvh_alloc(s->txb, PRIM_POINT, std::max(s->max_tx, 2u)))) return fail(e);
   if ((e = bvh_alloc(s->mix, PRIM_BOX, std::max(s->V + s->max_rx, 2u)))) return fail(e);
   s->dyn.pad = s->rxb.pad = s->txb.pad = s->mix.pad = pad;
+  // the per-frame builds report a barrier that gave up through the
+  // scene's error word (read by the next emrt_sync)
+  s->dyn.err_word = s->rxb.err_word = s->txb.err_word = s->mix.err_word = &s->ctr->err;
   if ((e = grow(&s->mix_lo, c, s->V + s->max_rx))) return fail(e); c = 0;
   if ((e = grow(&s->mix_hi, c, s->V + s->max_rx))) return fail(e); c = 0;
   uint32_t V1 = std::max(s->V, 1u);
@@ -1009,6 +1012,7 @@ emrt_status emrt_sync(emrt_scene s, emrt_stream stream, emrt_stats *out) {
   emrt_status r = s->sticky;
   s->sticky = EMRT_OK;
   if (r != EMRT_OK) return r;
+  if (h.err & ERR_WAIT) return EMRT_ERR_TIMEOUT;
   if (h.err & (ERR_STACK | ERR_NONFINITE)) return EMRT_ERR_DEVICE;
   if (h.err & ERR_UNSORTED) return EMRT_ERR_INVALID_ARG;
   if (h.err & (ERR_CAND_OVERFLOW | ERR_PATH_OVERFLOW | ERR_RAY_OVERFLOW)) return EMRT_ERR_CAPACITY;

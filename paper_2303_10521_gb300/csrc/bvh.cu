@@ -4,6 +4,8 @@
 // counter per inner node (the second thread to arrive merges the children).
 #include <cfloat>
 
+#include <cuda/atomic>
+
 #include "bvh.cuh"
 
 namespace emrt {
@@ -77,30 +79,30 @@ __global__ void k_morton_points(const float4 *p, uint32_t n, const float4 *bb, K
   idx[i] = i;
 }
 
-__device__ inline int delta(const KeyW<2> *k, int n, int i, int j) {
-  if (j < 0 || j >= n) return -1;
-  uint64_t a = get_key(k[i]), b = get_key(k[j]);
-  if (a == b) return 64 + __clz(i ^ j);
-  return __clzll(a ^ b);
-}
-
-// one thread per inner node i in [0, n-2]
-__global__ void k_hierarchy(const KeyW<2> *k, int n, float4 *nodes, uint32_t *leaf_parent) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
-  int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
-  int dmin = delta(k, n, i, i - d);
+// Inner node i in [0, n-2] of the radix tree over the sorted keys k: its
+// range, split and children, and the parent links of the children.
+template <typename KeyAt>
+__device__ inline void hierarchy_node(KeyAt key, int n, int i, float4 *nodes,
+                                      uint32_t *leaf_parent) {
+  auto delta = [&](int a, int c) -> int {
+    if (c < 0 || c >= n) return -1;
+    const uint64_t x = key(a), y = key(c);
+    if (x == y) return 64 + __clz(a ^ c);
+    return __clzll(x ^ y);
+  };
+  int d = (delta(i, i + 1) - delta(i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(i, i - d);
   int lmax = 2;
-  while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (delta(i, i + lmax * d) > dmin) lmax <<= 1;
   int l = 0;
   for (int t = lmax >> 1; t >= 1; t >>= 1)
-    if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    if (delta(i, i + (l + t) * d) > dmin) l += t;
   int j = i + l * d;
-  int dnode = delta(k, n, i, j);
+  int dnode = delta(i, j);
   int s = 0, t = l;
   do {
     t = (t + 1) >> 1;
-    if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    if (delta(i, i + (s + t) * d) > dnode) s += t;
   } while (t > 1);
   int gamma = i + s * d + min(d, 0);
   int left = min(i, j) == gamma ? ~gamma : gamma;
@@ -115,6 +117,13 @@ __global__ void k_hierarchy(const KeyW<2> *k, int n, float4 *nodes, uint32_t *le
   if (right < 0) leaf_parent[~right] = code1;
   else reinterpret_cast<int *>(nodes + 4ll * right + 3)[2] = code1;
   if (i == 0) n3[2] = -1;
+}
+
+// one thread per inner node i in [0, n-2]
+__global__ void k_hierarchy(const KeyW<2> *k, int n, float4 *nodes, uint32_t *leaf_parent) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  hierarchy_node([k](int a) { return get_key(k[a]); }, n, i, nodes, leaf_parent);
 }
 
 __global__ void k_gather_tris(const float *t, const uint32_t *face, const uint32_t *idx,
@@ -173,6 +182,29 @@ __device__ inline Box prim_box(const float4 *prims, uint32_t g) {
   return b;
 }
 
+// From a child box b whose parent link is `code` (parent * 2 + side) towards
+// the root: the box is written into its parent, and the second thread to
+// arrive at a node (arrival counters `flags`, global or shared) continues
+// with the node's own box.  The arrival is one acquire-release atomic: it
+// publishes this thread's box and, for the second arrival, makes the
+// sibling's visible (no full fences; each level is on the critical path).
+__device__ inline void refit_up(Box b, int code, float4 *nodes, uint32_t *flags) {
+  for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
+    const int p = code >> 1, side = code & 1;
+    float4 *np = nodes + 4ll * p;
+    reinterpret_cast<float4 *>(np + side)[0] = make_float4(b.lo.x, b.hi.x, b.lo.y, b.hi.y);
+    reinterpret_cast<float2 *>(np + 2)[side] = make_float2(b.lo.z, b.hi.z);
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> arrivals(flags[p]);
+    if (arrivals.fetch_add(1u, cuda::memory_order_acq_rel) == 0) return;
+    const float4 a0 = __ldcg(np), a1 = __ldcg(np + 1), a2 = __ldcg(np + 2);
+    b.lo = make_float3(fminf(a0.x, a1.x), fminf(a0.z, a1.z), fminf(a2.x, a2.z));
+    b.hi = make_float3(fmaxf(a0.y, a1.y), fmaxf(a0.w, a1.w), fmaxf(a2.y, a2.w));
+    const int pc = __ldcg(reinterpret_cast<const int *>(np + 3) + 2);
+    if (pc < 0) return;
+    code = pc;
+  }
+}
+
 // Bottom-up boxes: one thread per leaf walks to the root; the second child
 // to arrive at a node continues.  MULTI: leaves of 1-4 prims (leaf code
 // ~(first << 2 | count - 1)); prims other than a leaf's first have
@@ -196,21 +228,7 @@ __global__ void k_refit(const float4 *prims, uint32_t n, float4 *nodes, const ui
   }
   b.lo = make_float3(b.lo.x - pad, b.lo.y - pad, b.lo.z - pad);
   b.hi = make_float3(b.hi.x + pad, b.hi.y + pad, b.hi.z + pad);
-  for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
-    int p = code >> 1, side = code & 1;
-    float4 *np = nodes + 4ll * p;
-    reinterpret_cast<float4 *>(np + side)[0] = make_float4(b.lo.x, b.hi.x, b.lo.y, b.hi.y);
-    reinterpret_cast<float2 *>(np + 2)[side] = make_float2(b.lo.z, b.hi.z);
-    __threadfence();
-    if (atomicAdd(&flags[p], 1u) == 0) return;
-    __threadfence();
-    float4 a0 = __ldcg(np), a1 = __ldcg(np + 1), a2 = __ldcg(np + 2);
-    b.lo = make_float3(fminf(a0.x, a1.x), fminf(a0.z, a1.z), fminf(a2.x, a2.z));
-    b.hi = make_float3(fmaxf(a0.y, a1.y), fmaxf(a0.w, a1.w), fmaxf(a2.y, a2.w));
-    int pc = __ldcg(reinterpret_cast<const int *>(np + 3) + 2);
-    if (pc < 0) return;
-    code = pc;
-  }
+  refit_up(b, code, nodes, flags);
 }
 
 struct Child {
@@ -465,11 +483,6 @@ __global__ void k_bbox_fin(const uint32_t *acc, float4 *bb) {
 constexpr uint32_t kSmallBuildMax = 4096;
 constexpr int kSmallBlock = 1024;
 
-__device__ inline int delta_u64(const unsigned long long *k, int n, int i, int j) {
-  if (j < 0 || j >= n) return -1;
-  return __clzll(k[i] ^ k[j]);
-}
-
 template <int KIND>
 __global__ void __launch_bounds__(kSmallBlock) k_small_build(
     const float4 *a, const float4 *b, uint32_t n, uint32_t np2, const float4 *bb, float4 *prims,
@@ -518,36 +531,11 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_build(
     }
   }
   if (n < 2) return;
-  // hierarchy: inner node i over the sorted keys
+  // hierarchy: inner node i over the sorted keys (all distinct: the index
+  // is in the low bits)
   const int nn = (int)n;
-  for (int i = (int)tid; i < nn - 1; i += (int)blockDim.x) {
-    const int d = (delta_u64(sk, nn, i, i + 1) - delta_u64(sk, nn, i, i - 1)) >= 0 ? 1 : -1;
-    const int dmin = delta_u64(sk, nn, i, i - d);
-    int lmax = 2;
-    while (delta_u64(sk, nn, i, i + lmax * d) > dmin) lmax <<= 1;
-    int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-      if (delta_u64(sk, nn, i, i + (l + t) * d) > dmin) l += t;
-    const int j = i + l * d;
-    const int dnode = delta_u64(sk, nn, i, j);
-    int sp = 0, t = l;
-    do {
-      t = (t + 1) >> 1;
-      if (delta_u64(sk, nn, i, i + (sp + t) * d) > dnode) sp += t;
-    } while (t > 1);
-    const int gamma = i + sp * d + min(d, 0);
-    const int left = min(i, j) == gamma ? ~gamma : gamma;
-    const int right = max(i, j) == gamma + 1 ? ~(gamma + 1) : gamma + 1;
-    int *n3 = reinterpret_cast<int *>(nodes + 4ll * i + 3);
-    n3[0] = left;
-    n3[1] = right;
-    n3[3] = 0;
-    if (left < 0) leaf_parent[~left] = 2u * i;
-    else reinterpret_cast<int *>(nodes + 4ll * left + 3)[2] = 2 * i;
-    if (right < 0) leaf_parent[~right] = 2u * i + 1u;
-    else reinterpret_cast<int *>(nodes + 4ll * right + 3)[2] = 2 * i + 1;
-    if (i == 0) n3[2] = -1;
-  }
+  for (int i = (int)tid; i < nn - 1; i += (int)blockDim.x)
+    hierarchy_node([](int q) { return (uint64_t)sk[q]; }, nn, i, nodes, leaf_parent);
   __threadfence_block();
   __syncthreads();
   // bottom-up boxes: the second thread to reach a node merges its children
@@ -556,21 +544,7 @@ __global__ void __launch_bounds__(kSmallBlock) k_small_build(
     bx.lo = make_float3(bx.lo.x - pad, bx.lo.y - pad, bx.lo.z - pad);
     bx.hi = make_float3(bx.hi.x + pad, bx.hi.y + pad, bx.hi.z + pad);
     int code = (int)__ldcg(leaf_parent + g);
-    for (int guard = 0; guard < 4096; guard++) {  // tree depth bound (safety net)
-      const int p = code >> 1, side = code & 1;
-      float4 *np = nodes + 4ll * p;
-      reinterpret_cast<float4 *>(np + side)[0] = make_float4(bx.lo.x, bx.hi.x, bx.lo.y, bx.hi.y);
-      reinterpret_cast<float2 *>(np + 2)[side] = make_float2(bx.lo.z, bx.hi.z);
-      __threadfence();
-      if (atomicAdd(&sflag[p], 1u) == 0) break;
-      __threadfence();
-      const float4 a0 = __ldcg(np), a1 = __ldcg(np + 1), a2 = __ldcg(np + 2);
-      bx.lo = make_float3(fminf(a0.x, a1.x), fminf(a0.z, a1.z), fminf(a2.x, a2.z));
-      bx.hi = make_float3(fmaxf(a0.y, a1.y), fmaxf(a0.w, a1.w), fmaxf(a2.y, a2.w));
-      const int pc = __ldcg(reinterpret_cast<const int *>(np + 3) + 2);
-      if (pc < 0) break;
-      code = pc;
-    }
+    refit_up(bx, code, nodes, sflag);
   }
 }
 
@@ -586,6 +560,194 @@ cudaError_t small_build(BVHBuf &b, const float4 *a, const float4 *bx, uint32_t n
   emrt::note_launch(), k_small_build<KIND><<<1, kSmallBlock, smem, s>>>(a, bx, n, np2, bbox, b.prims,
                                                                        b.nodes, b.leaf_parent, b.pad);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-frame trees of kSmallBuildMax + 1 .. kCoopMax primitives: the steps of
+// the device-wide build (Morton codes, four stable 8-bit radix passes over
+// the 30-bit codes, gather, hierarchy, bottom-up boxes) in one cooperative
+// launch, separated by a grid barrier, instead of ~18 launches and memsets
+// whose latencies set a 5-15k primitive tree's build time.  Each block owns
+// one tile of at most kCoopTile keys; a radix pass counts the tile's digits,
+// and after the barrier every block sums the counts of all blocks (its own
+// offsets: the digits' totals and the counts of the blocks before it) and
+// scatters its tile, ranking equal digits by tile position, so every pass is
+// stable and the sorted order, the tree and every query result are those of
+// the device-wide path.  The barrier's wait is bounded: past kBarrierSpins
+// polls the block records ERR_WAIT and the build stops (the cooperative
+// launch keeps all blocks resident, so the bound is only a safety net).
+constexpr uint32_t kCoopMax = 65536;
+constexpr int kCoopBlock = 256;
+constexpr uint32_t kCoopTile = 512;
+constexpr uint32_t kBarrierSpins = 1u << 22;
+
+// bar[0]: arrivals, bar[1]: generation, bar[2]: gave-up flag (zeroed
+// before the launch)
+__device__ inline bool grid_barrier(uint32_t *bar, uint32_t nb, uint32_t *err_word) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t *gen = bar + 1;
+    const uint32_t g = *gen;
+    __threadfence();
+    bool ok = true;
+    if (atomicAdd(bar, 1u) == nb - 1u) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint32_t it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierSpins || *(volatile uint32_t *)(bar + 2)) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (!ok) {
+      atomicExch(bar + 2, 1u);
+      if (err_word) atomicOr(err_word, ERR_WAIT);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int KIND>
+__device__ inline float3 dyn_centre(const float4 *a, const float4 *b, uint32_t i) {
+  const float4 p = a[i];
+  if (KIND == PRIM_BOX) {
+    const float4 q = b[i];
+    return make_float3(0.5f * (p.x + q.x), 0.5f * (p.y + q.y), 0.5f * (p.z + q.z));
+  }
+  return f3(p);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kCoopBlock) k_coop_build(
+    const float4 *a, const float4 *bx, uint32_t n, const float4 *bb, KeyW<2> *k0, uint32_t *i0,
+    KeyW<2> *k1, uint32_t *i1, uint32_t *hist, float4 *prims, float4 *nodes,
+    uint32_t *leaf_parent, uint32_t *flags, float pad, uint32_t *bar, uint32_t *err_word) {
+  __shared__ uint32_t s_code[kCoopTile], s_idx[kCoopTile];
+  __shared__ uint32_t s_base[256], s_pre[256];
+  const uint32_t nb = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
+  const uint32_t tile = (n + nb - 1) / nb;  // <= kCoopTile (host check)
+  const uint32_t t0 = min(blk * tile, n), tn = min(t0 + tile, n) - t0;
+  for (uint32_t t = tid; t < tn; t += blockDim.x) {
+    s_code[t] = (uint32_t)morton_code<kMortonBitsDyn>(dyn_centre<KIND>(a, bx, t0 + t), bb);
+    s_idx[t] = t0 + t;
+  }
+  // LSD radix sort, 8 bits a pass; passes write k1/i1, k0/i0, k1/i1, k0/i0
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 8 * pass;
+    KeyW<2> *ko = (pass & 1) ? k0 : k1;
+    uint32_t *io = (pass & 1) ? i0 : i1;
+    for (uint32_t d = tid; d < 256; d += blockDim.x) s_base[d] = 0u;
+    __syncthreads();
+    for (uint32_t t = tid; t < tn; t += blockDim.x) atomicAdd(&s_base[(s_code[t] >> shift) & 255u], 1u);
+    __syncthreads();
+    for (uint32_t d = tid; d < 256; d += blockDim.x) hist[256ull * blk + d] = s_base[d];
+    if (!grid_barrier(bar, nb, err_word)) return;
+    for (uint32_t d = tid; d < 256; d += blockDim.x) {
+      uint32_t tot = 0, pre = 0;
+      for (uint32_t j = 0; j < nb; j++) {
+        const uint32_t v = __ldcg(hist + 256ull * j + d);
+        tot += v;
+        pre += j < blk ? v : 0u;
+      }
+      s_base[d] = tot;
+      s_pre[d] = pre;
+    }
+    __syncthreads();
+    if (tid == 0) {  // exclusive scan of the digit totals
+      uint32_t run = 0;
+      for (uint32_t d = 0; d < 256; d++) {
+        const uint32_t v = s_base[d];
+        s_base[d] = run;
+        run += v;
+      }
+    }
+    __syncthreads();
+    for (uint32_t t = tid; t < tn; t += blockDim.x) {
+      const uint32_t dg = (s_code[t] >> shift) & 255u;
+      uint32_t r = 0;
+      for (uint32_t u = 0; u < t; u++) r += ((s_code[u] >> shift) & 255u) == dg;
+      const uint32_t dst = s_base[dg] + s_pre[dg] + r;
+      KeyW<2> kk;
+      kk.w[0] = s_code[t];
+      kk.w[1] = 0u;
+      ko[dst] = kk;
+      io[dst] = s_idx[t];
+    }
+    if (!grid_barrier(bar, nb, err_word)) return;
+    if (pass < 3) {
+      for (uint32_t t = tid; t < tn; t += blockDim.x) {
+        s_code[t] = __ldcg(&ko[t0 + t].w[0]);
+        s_idx[t] = __ldcg(io + t0 + t);
+      }
+      __syncthreads();
+    }
+  }
+  // primitives in leaf order, arrival counters cleared, hierarchy
+  const uint32_t stride = nb * blockDim.x;
+  for (uint32_t g = blk * blockDim.x + tid; g < n; g += stride) {
+    const uint32_t src = __ldcg(i0 + g);
+    const float4 p = a[src];
+    if (KIND == PRIM_BOX) {
+      const float4 q = bx[src];
+      prims[2ull * g + 0] = make_float4(p.x, p.y, p.z, __uint_as_float(src));
+      prims[2ull * g + 1] = make_float4(q.x, q.y, q.z, 0.f);
+    } else {
+      prims[g] = make_float4(p.x, p.y, p.z, __uint_as_float(src));
+    }
+    flags[g] = 0u;
+  }
+  for (uint32_t i = blk * blockDim.x + tid; i + 1 < n; i += stride)
+    hierarchy_node([k0](int q) { return (uint64_t)__ldcg(&k0[q].w[0]); }, (int)n, (int)i, nodes,
+                   leaf_parent);
+  if (!grid_barrier(bar, nb, err_word)) return;
+  // bottom-up boxes (this thread gathered primitive g itself)
+  for (uint32_t g = blk * blockDim.x + tid; g < n; g += stride) {
+    Box b = prim_box<KIND>(prims, g);
+    b.lo = make_float3(b.lo.x - pad, b.lo.y - pad, b.lo.z - pad);
+    b.hi = make_float3(b.hi.x + pad, b.hi.y + pad, b.hi.z + pad);
+    refit_up(b, (int)__ldcg(leaf_parent + g), nodes, flags);
+  }
+}
+
+int g_sms = 0;
+int sm_count() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+// blocks of the cooperative build of n primitives (tiles of about 128 keys,
+// at most one block per SM, at least ceil(n / kCoopTile))
+uint32_t coop_grid(uint32_t n) {
+  const uint32_t g = std::min<uint32_t>((uint32_t)sm_count(), ceil_div(n, 128u));
+  return std::max<uint32_t>(g, ceil_div(n, kCoopTile));
+}
+
+template <int KIND>
+cudaError_t coop_build(BVHBuf &b, const float4 *a, const float4 *bx, uint32_t n,
+                       const float4 *bbox, cudaStream_t s) {
+  uint32_t grid = coop_grid(n);
+  cudaMemsetAsync(b.coop_bar, 0, 3 * sizeof(uint32_t), s);
+  void *args[] = {(void *)&a,        (void *)&bx,          (void *)&n,       (void *)&bbox,
+                  (void *)&b.keys,   (void *)&b.idx,       (void *)&b.keys2, (void *)&b.idx2,
+                  (void *)&b.coop_hist, (void *)&b.prims,  (void *)&b.nodes, (void *)&b.leaf_parent,
+                  (void *)&b.flags,  (void *)&b.pad,       (void *)&b.coop_bar, (void *)&b.err_word};
+  emrt::note_launch();
+  return cudaLaunchCooperativeKernel((const void *)k_coop_build<KIND>, dim3(grid),
+                                     dim3(kCoopBlock), args, 0, s);
 }
 
 template <int KIND>
@@ -643,12 +805,18 @@ cudaError_t bvh_alloc(BVHBuf &b, PrimKind kind, uint32_t cap) {
   A((void **)&b.idx, sizeof(uint32_t) * b.cap);
   A((void **)&b.idx2, sizeof(uint32_t) * b.cap);
   A((void **)&b.d_n, sizeof(uint32_t));
+  if (kind != PRIM_TRI && b.cap > kSmallBuildMax) {
+    A((void **)&b.coop_hist, sizeof(uint32_t) * 256 * (size_t)coop_grid(std::min(b.cap, kCoopMax)));
+    A((void **)&b.coop_bar, sizeof(uint32_t) * 4);
+  }
   return e;
 }
 
 void bvh_free(BVHBuf &b) {
   cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.leaf_parent); cudaFree(b.flags);
   cudaFree(b.keys); cudaFree(b.keys2); cudaFree(b.idx); cudaFree(b.idx2); cudaFree(b.d_n);
+  cudaFree(b.coop_hist); cudaFree(b.coop_bar);
+  b.coop_hist = b.coop_bar = nullptr;
   cudaFree(b.nodes8);
   cudaFree(b.prims8);
   b.nodes8 = nullptr;
@@ -675,6 +843,7 @@ cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint3
   b.n = n;
   if (n == 0) return cudaSuccess;
   if (n <= kSmallBuildMax) return small_build<PRIM_BOX>(b, lo, hi, n, bbox, s);
+  if (n <= kCoopMax && b.coop_bar) return coop_build<PRIM_BOX>(b, lo, hi, n, bbox, s);
   emrt::note_launch(), k_morton_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_BOX>(b, hist, s);
   emrt::note_launch(), k_gather_boxes<<<ceil_div(n, 256), 256, 0, s>>>(lo, hi, b.idx, n, b.prims);
@@ -697,6 +866,7 @@ cudaError_t bvh_build_points(BVHBuf &b, const float4 *pts, uint32_t n, const flo
   b.n = n;
   if (n == 0) return cudaSuccess;
   if (n <= kSmallBuildMax) return small_build<PRIM_POINT>(b, pts, nullptr, n, bbox, s);
+  if (n <= kCoopMax && b.coop_bar) return coop_build<PRIM_POINT>(b, pts, nullptr, n, bbox, s);
   emrt::note_launch(), k_morton_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, n, bbox, b.keys, b.idx);
   sort_codes<PRIM_POINT>(b, hist, s);
   emrt::note_launch(), k_gather_points<<<ceil_div(n, 256), 256, 0, s>>>(pts, b.idx, n, b.prims);

@@ -29,6 +29,12 @@ struct BVHBuf {
   // coordinate of the scene, keeps the test conservative for ray origins in
   // the scene (no cracks at box planes that are also triangle edges).
   float pad = 0.f;
+  // scratch of the one-launch cooperative build (per-block digit counts and
+  // the grid barrier), and the device error word it reports a barrier that
+  // gave up to (ERR_WAIT; may be null)
+  uint32_t *coop_hist = nullptr;
+  uint32_t *coop_bar = nullptr;
+  uint32_t *err_word = nullptr;
   BVHView view() const;
 };
 

@@ -15,6 +15,7 @@ enum : uint32_t {
   ERR_STACK = 4u,           // traversal stack overflow
   ERR_RAY_OVERFLOW = 8u,    // ray scratch too small (internal bug)
   ERR_UNSORTED = 16u,       // a merge input is not in canonical order
+  ERR_WAIT = 64u,           // a bounded wait between blocks gave up
 };
 
 // per-call counters kept in device memory (one struct per scene)

@@ -402,25 +402,27 @@ def test_dense_receiver_cluster(engine, form):
     assert ra["n_diff_unflagged"] == 0, ra
 
 
-def test_tree_builders_agree_at_the_size_threshold(engine):
-    """Per-frame trees of up to 4096 primitives are built by one block, larger
-    ones by the device-wide path; the trees differ but every query is exact,
-    so the paths of 4096 receivers are the same whether a 4097th receiver
-    (which moves the receiver and merged trees to the other builder) is
-    present or not."""
+@pytest.mark.parametrize("n_small", [4096, 65536])
+def test_tree_builders_agree_at_the_size_threshold(engine, n_small):
+    """Per-frame trees of up to 4096 primitives are built by one block, up to
+    65536 by one cooperative launch, larger ones by the device-wide path; the
+    trees may differ but every query is exact, so the paths of n_small
+    receivers are the same whether one more receiver (which moves the
+    receiver and merged trees to the next builder) is present or not."""
     E = engine
     sc = S.toy_scene(seed=0)
     fr = sc.frame(0)
     rng = np.random.default_rng(9)
-    rx = np.column_stack([rng.uniform(-90, 90, 4097), rng.uniform(-90, 90, 4097),
-                          rng.uniform(1.0, 3.0, 4097)]).astype(np.float32)
+    m = n_small + 1
+    rx = np.column_stack([rng.uniform(-90, 90, m), rng.uniform(-90, 90, m),
+                          rng.uniform(1.0, 3.0, m)]).astype(np.float32)
     big = dataclasses.replace(fr, rx_pos=rx, rx_vel=np.zeros_like(rx))
-    small = dataclasses.replace(fr, rx_pos=rx[:4096], rx_vel=np.zeros_like(rx[:4096]))
-    g = _gpu(E, sc, big, max_rx=4097)
+    small = dataclasses.replace(fr, rx_pos=rx[:n_small], rx_vel=np.zeros_like(rx[:n_small]))
+    g = _gpu(E, sc, big, max_rx=m)
     rb = g.trace(n_rays=50_000).records()
     g.update(small)
     rs = g.trace(n_rays=50_000).records()
-    keep = rb[rb[:, 1] < 4096]
+    keep = rb[rb[:, 1] < n_small]
     assert len(rs) > 1000
     assert np.array_equal(keep, rs)
 
