@@ -139,8 +139,12 @@ void emrt_scene_destroy(emrt_scene sc);
  * tracked object speeds): vehicle boxes at veh_pos (box centres, [V][3]) with
  * velocities veh_vel; receivers rx_pos/rx_vel [n_rx][3]; transmitters
  * tx_pos/tx_vel [n_tx][3].  Refits the vehicle BVH (rebuilds it every
- * rebuild_every calls) and rebuilds the receiver BVH.  veh_* may be NULL
- * when V = 0; *_vel may be NULL for zero velocity. */
+ * rebuild_every calls) and rebuilds the receiver BVH and the merged
+ * vehicle + receiver BVH.  Trees of 4097-65536 primitives are built in one
+ * cooperative launch whose blocks wait on one another at a bounded grid
+ * barrier; a barrier that gives up makes the next emrt_sync return
+ * EMRT_ERR_TIMEOUT (the trees are then invalid).  veh_* may be NULL when
+ * V = 0; *_vel may be NULL for zero velocity. */
 emrt_status emrt_scene_update_dynamic(emrt_scene sc, const float *veh_pos,
                                       const float *veh_vel, const float *rx_pos,
                                       const float *rx_vel, uint32_t n_rx,
