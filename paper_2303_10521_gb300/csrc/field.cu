@@ -286,13 +286,40 @@ __device__ inline void pick_freq(const FreqSet &fs, double &freq, double *&out) 
 
 // Field of every path at the frequency blockIdx.y of fs (frequencies share
 // the launch, so a frame's ~1e4 paths at two frequencies fill twice the warps).
-__global__ void k_field(GeomView g, MatView m, const uint32_t *rec, const uint32_t *n, uint32_t cap,
-                        FreqSet fs, Counters *ctr) {
+// A block takes kFieldBlock consecutive paths and hands them to its threads
+// ordered by depth, so that a warp's paths mostly share their number of
+// reflections: the per-bounce loops then run for the warp's own depth, not
+// for the deepest path among 32 of every depth.  On GB300 each warp-wide FP64
+// instruction holds the SM's FP64 units for many cycles whatever the number
+// of active lanes, so lanes idled by shallower paths cost as much as busy
+// ones.  Which thread computes a path does not change its result.
+constexpr int kFieldBlock = 128;
+__global__ void __launch_bounds__(kFieldBlock) k_field(GeomView g, MatView m, const uint32_t *rec,
+                                                       const uint32_t *n, uint32_t cap,
+                                                       FreqSet fs, Counters *ctr) {
+  __shared__ uint32_t s_cnt[EMRT_MAX_DEPTH + 2];
+  __shared__ uint32_t s_order[kFieldBlock];
   double freq;
   double *out;
   pick_freq(fs, freq, out);
-  uint32_t cnt = min(*n, cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+  const uint32_t cnt = min(*n, cap);
+  for (uint32_t base = blockIdx.x * kFieldBlock; base < cnt; base += gridDim.x * kFieldBlock) {
+    // counting sort of the block's paths by depth (records past the end and
+    // malformed depths go last)
+    if (threadIdx.x <= EMRT_MAX_DEPTH + 1) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint32_t mine = base + threadIdx.x;
+    const uint32_t bucket =
+        mine < cnt ? min(rec[8ull * mine + 2] & 15u, (uint32_t)EMRT_MAX_DEPTH + 1u) : EMRT_MAX_DEPTH + 1u;
+    const uint32_t rank = atomicAdd(&s_cnt[bucket], 1u);
+    __syncthreads();
+    uint32_t start = 0;
+    for (uint32_t q = 0; q < bucket; q++) start += s_cnt[q];
+    s_order[start + rank] = mine;
+    __syncthreads();
+    const uint32_t i = s_order[threadIdx.x];
+    __syncthreads();
+    if (i >= cnt) continue;
     PathGeom P;
     const uint32_t *r = rec + 8ull * i;
     uint32_t tx = r[0], rx = r[1];
@@ -621,10 +648,8 @@ void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, u
 void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                     uint32_t cap, const FreqSet &fs, uint32_t n_tx, uint32_t n_rx,
                     double tx_power_w, Counters *ctr, cudaStream_t s) {
-  // one warp per block: the ~1e4 paths of a frame spread over every SM's
-  // FP64 units (128-thread blocks left half the SMs idle; measured 4 % of
-  // the channel stage); one grid row per frequency
-  emrt::note_launch(), k_field<<<dim3(152 * 16, fs.n), 32, 0, s>>>(g, m, rec, n, cap, fs, ctr);
+  // one grid row per frequency
+  emrt::note_launch(), k_field<<<dim3(152 * 4, fs.n), kFieldBlock, 0, s>>>(g, m, rec, n, cap, fs, ctr);
   uint32_t np = n_tx * n_rx;
   for (uint32_t q = 0; q < fs.n; q++) cudaMemsetAsync(fs.pair_out[q], 0, sizeof(double) * 8 * np, s);
   emrt::note_launch(), k_pair_seq<<<dim3(152 * 8, fs.n), 256, 0, s>>>(rec, n, cap, n_tx, n_rx, fs);
