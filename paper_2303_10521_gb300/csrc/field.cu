@@ -199,12 +199,12 @@ __device__ inline void load_geom(const GeomView &g, const uint32_t *rec, PathGeo
   }
 }
 
-// Field of one path.  tx: transmitter position (seeded with tangents by the
-// caller), epsr/sig: per-bounce material parameters.
+// Geometry of one path (frequency-independent): image points, reflection
+// points, the unfolded length L and the unit direction kh[q] of every leg.
+// tx: transmitter position (seeded with tangents by the caller).
 template <typename T>
-__device__ inline void path_field(const PathGeom &P, V3<T> tx, V3<double> rx, const T *epsr,
-                                  const T *sig, const double *gam, bool const_gamma, double freq,
-                                  Cx<T> &amp, T &Lout, V3<T> *kh) {
+__device__ inline void path_geometry(const PathGeom &P, V3<T> tx, V3<double> rx, T &Lout,
+                                     V3<T> *kh) {
   const uint32_t k = P.k;
   V3<T> I[EMRT_MAX_DEPTH + 1], Q[EMRT_MAX_DEPTH + 2];
   I[0] = tx;
@@ -228,6 +228,17 @@ __device__ inline void path_field(const PathGeom &P, V3<T> tx, V3<double> rx, co
     L = L + l;
     kh[q] = scale(D, T(1.0) / l);
   }
+  Lout = L;
+}
+
+// Field of a path of geometry (kh, L) at one frequency: polarisation
+// transport through the Fresnel reflections, spreading and phase.
+// epsr/sig: per-bounce material parameters.
+template <typename T>
+__device__ inline void path_transport(const PathGeom &P, const V3<T> *kh, T L, const T *epsr,
+                                      const T *sig, const double *gam, bool const_gamma,
+                                      double freq, Cx<T> &amp) {
+  const uint32_t k = P.k;
   const double lam = kC / freq;
   V3<T> p0 = polar(kh[0]);
   CV3<T> E;
@@ -269,23 +280,33 @@ __device__ inline void path_field(const PathGeom &P, V3<T> tx, V3<double> rx, co
   tsincos(ph, sp, cp);
   T sc = T(lam / (4.0 * kPi)) / L;
   amp = cscale(rcv * cx<T>(cp, sp), sc);
-  Lout = L;
 }
 
-// frequency blockIdx.y of a set (kernel parameters; no dynamic indexing)
-__device__ inline void pick_freq(const FreqSet &fs, double &freq, double *&out) {
+// Field of one path at one frequency (geometry and transport).
+template <typename T>
+__device__ inline void path_field(const PathGeom &P, V3<T> tx, V3<double> rx, const T *epsr,
+                                  const T *sig, const double *gam, bool const_gamma, double freq,
+                                  Cx<T> &amp, T &Lout, V3<T> *kh) {
+  path_geometry<T>(P, tx, rx, Lout, kh);
+  path_transport<T>(P, kh, Lout, epsr, sig, gam, const_gamma, freq, amp);
+}
+
+// frequency q of a set (kernel parameters; no dynamic indexing)
+__device__ inline void pick_freq(const FreqSet &fs, uint32_t q, double &freq, double *&out) {
   freq = fs.f[0];
   out = fs.path_out[0];
 #pragma unroll
-  for (uint32_t q = 1; q < kMaxFreq; q++)
-    if (blockIdx.y == q) {
-      freq = fs.f[q];
-      out = fs.path_out[q];
+  for (uint32_t j = 1; j < kMaxFreq; j++)
+    if (q == j) {
+      freq = fs.f[j];
+      out = fs.path_out[j];
     }
 }
 
-// Field of every path at the frequency blockIdx.y of fs (frequencies share
-// the launch, so a frame's ~1e4 paths at two frequencies fill twice the warps).
+// Field of every path at the frequencies 2 blockIdx.y and 2 blockIdx.y + 1
+// of fs: the path's geometry (image and reflection points, legs, Doppler
+// rate) once, the transport at each of the two frequencies (the same
+// arithmetic as for one frequency alone).
 // A block takes kFieldBlock consecutive paths and hands them to its threads
 // ordered by depth, so that a warp's paths mostly share their number of
 // reflections: the per-bounce loops then run for the warp's own depth, not
@@ -299,9 +320,12 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(GeomView g, MatView m, co
                                                        FreqSet fs, Counters *ctr) {
   __shared__ uint32_t s_cnt[EMRT_MAX_DEPTH + 2];
   __shared__ uint32_t s_order[kFieldBlock];
-  double freq;
-  double *out;
-  pick_freq(fs, freq, out);
+  const uint32_t q0 = 2u * blockIdx.y;
+  const bool two = q0 + 1u < fs.n;
+  double freq0, freq1;
+  double *out0, *out1;
+  pick_freq(fs, q0, freq0, out0);
+  pick_freq(fs, two ? q0 + 1u : q0, freq1, out1);
   const uint32_t cnt = min(*n, cap);
   for (uint32_t base = blockIdx.x * kFieldBlock; base < cnt; base += gridDim.x * kFieldBlock) {
     // counting sort of the block's paths by depth (records past the end and
@@ -324,7 +348,8 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(GeomView g, MatView m, co
     const uint32_t *r = rec + 8ull * i;
     uint32_t tx = r[0], rx = r[1];
     if (!record_ok(g, r)) {  // malformed record: no field
-      reinterpret_cast<double4_32a *>(out)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      reinterpret_cast<double4_32a *>(out0)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      if (two) reinterpret_cast<double4_32a *>(out1)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
       continue;
     }
     load_geom(g, r, P);
@@ -337,10 +362,9 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(GeomView g, MatView m, co
     }
     float3 t3 = f3(g.tx_pos[tx]), r3 = f3(g.rx_pos[rx]);
     V3<double> txp = mk3<double>(t3.x, t3.y, t3.z), rxp = mk3<double>(r3.x, r3.y, r3.z);
-    Cx<double> a;
     double L;
     V3<double> kh[EMRT_MAX_DEPTH + 1];
-    path_field<double>(P, txp, rxp, epsr, sig, gam, m.const_gamma != 0, freq, a, L, kh);
+    path_geometry<double>(P, txp, rxp, L, kh);
     // Doppler: rate of change of the unfolded length (Eq. 3 generalised)
     float3 vt = f3(g.tx_vel[tx]), vr = f3(g.rx_vel[rx]);
     double dL = -(vt.x * kh[0].x + vt.y * kh[0].y + vt.z * kh[0].z) +
@@ -349,14 +373,20 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(GeomView g, MatView m, co
       float3 v = P.vel[q - 1];
       dL += v.x * (kh[q - 1].x - kh[q].x) + v.y * (kh[q - 1].y - kh[q].y) + v.z * (kh[q - 1].z - kh[q].z);
     }
-    double4_32a o;
-    o.x = a.re;
-    o.y = a.im;
-    o.z = L / kC;
-    o.w = -(freq / kC) * dL;
-    if (!isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z) || !isfinite(o.w))
-      atomicOr(&ctr->err, ERR_NONFINITE);
-    reinterpret_cast<double4_32a *>(out)[i] = o;
+    for (int f = 0; f < 2; f++) {
+      if (f == 1 && !two) break;
+      const double freq = f ? freq1 : freq0;
+      Cx<double> a;
+      path_transport<double>(P, kh, L, epsr, sig, gam, m.const_gamma != 0, freq, a);
+      double4_32a o;
+      o.x = a.re;
+      o.y = a.im;
+      o.z = L / kC;
+      o.w = -(freq / kC) * dL;
+      if (!isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z) || !isfinite(o.w))
+        atomicOr(&ctr->err, ERR_NONFINITE);
+      reinterpret_cast<double4_32a *>(f ? out1 : out0)[i] = o;
+    }
   }
 }
 
@@ -648,8 +678,8 @@ void launch_compact_ids(const uint32_t *flag, const uint32_t *pos, uint32_t n, u
 void launch_channel(const GeomView &g, MatView m, const uint32_t *rec, const uint32_t *n,
                     uint32_t cap, const FreqSet &fs, uint32_t n_tx, uint32_t n_rx,
                     double tx_power_w, Counters *ctr, cudaStream_t s) {
-  // one grid row per frequency
-  emrt::note_launch(), k_field<<<dim3(152 * 4, fs.n), kFieldBlock, 0, s>>>(g, m, rec, n, cap, fs, ctr);
+  // one grid row per pair of frequencies
+  emrt::note_launch(), k_field<<<dim3(152 * 4, (fs.n + 1) / 2), kFieldBlock, 0, s>>>(g, m, rec, n, cap, fs, ctr);
   uint32_t np = n_tx * n_rx;
   for (uint32_t q = 0; q < fs.n; q++) cudaMemsetAsync(fs.pair_out[q], 0, sizeof(double) * 8 * np, s);
   emrt::note_launch(), k_pair_seq<<<dim3(152 * 8, fs.n), 256, 0, s>>>(rec, n, cap, n_tx, n_rx, fs);
