@@ -384,7 +384,10 @@ typedef struct {
   uint64_t candidates;        /* reception-sphere detections                 */
   uint64_t unique_candidates; /* after deduplication                         */
   uint64_t accepted;          /* paths written                                */
-  uint64_t occlusion_rays;    /* any-hit segments traced by acceptance        */
+  uint64_t occlusion_rays;    /* any-hit segments traced by acceptance (each
+                                 leg as 4 pieces; pieces of a leg already
+                                 found occluded are skipped, so the count
+                                 varies a little from run to run)           */
   uint64_t node_visits;       /* static BVH inner nodes visited (closest hit) */
   uint64_t tri_tests;         /* triangles tested (closest hit)               */
   uint64_t dyn_node_visits;   /* vehicle BVH inner nodes visited              */
