@@ -65,6 +65,31 @@ struct BVHView {
                         // prim 0 alone either way
 };
 
+// Index of the path this thread takes among the block's records base ..
+// base + blockDim.x - 1 (8 words each), handed out in order of depth (word
+// 2, low 4 bits; depths above EMRT_MAX_DEPTH and records past cnt last), so
+// that a warp's paths mostly share their number of reflections and its
+// per-bounce loops run for its own depth.  A result >= cnt means none.
+// Called by every thread of the block (it synchronises); s_cnt holds
+// EMRT_MAX_DEPTH + 2 words, s_order blockDim.x.
+__device__ inline uint32_t depth_ordered(const uint32_t *rec, uint32_t base, uint32_t cnt,
+                                         uint32_t *s_cnt, uint32_t *s_order) {
+  if (threadIdx.x <= EMRT_MAX_DEPTH + 1) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint32_t mine = base + threadIdx.x;
+  const uint32_t bucket =
+      mine < cnt ? min(rec[8ull * mine + 2] & 15u, (uint32_t)EMRT_MAX_DEPTH + 1u) : EMRT_MAX_DEPTH + 1u;
+  const uint32_t rank = atomicAdd(&s_cnt[bucket], 1u);
+  __syncthreads();
+  uint32_t start = 0;
+  for (uint32_t q = 0; q < bucket; q++) start += s_cnt[q];
+  s_order[start + rank] = mine;
+  __syncthreads();
+  const uint32_t i = s_order[threadIdx.x];
+  __syncthreads();
+  return i;
+}
+
 // ray state between bounces: 48 B
 struct Ray {
   float4 o_L;    // origin, unfolded length travelled so far (L_acc)

@@ -328,21 +328,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(GeomView g, MatView m, co
   pick_freq(fs, two ? q0 + 1u : q0, freq1, out1);
   const uint32_t cnt = min(*n, cap);
   for (uint32_t base = blockIdx.x * kFieldBlock; base < cnt; base += gridDim.x * kFieldBlock) {
-    // counting sort of the block's paths by depth (records past the end and
-    // malformed depths go last)
-    if (threadIdx.x <= EMRT_MAX_DEPTH + 1) s_cnt[threadIdx.x] = 0u;
-    __syncthreads();
-    const uint32_t mine = base + threadIdx.x;
-    const uint32_t bucket =
-        mine < cnt ? min(rec[8ull * mine + 2] & 15u, (uint32_t)EMRT_MAX_DEPTH + 1u) : EMRT_MAX_DEPTH + 1u;
-    const uint32_t rank = atomicAdd(&s_cnt[bucket], 1u);
-    __syncthreads();
-    uint32_t start = 0;
-    for (uint32_t q = 0; q < bucket; q++) start += s_cnt[q];
-    s_order[start + rank] = mine;
-    __syncthreads();
-    const uint32_t i = s_order[threadIdx.x];
-    __syncthreads();
+    const uint32_t i = depth_ordered(rec, base, cnt, s_cnt, s_order);
     if (i >= cnt) continue;
     PathGeom P;
     const uint32_t *r = rec + 8ull * i;

@@ -371,8 +371,13 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kBounceBlock) k_accept_geom(GeomView G, const BatchScene *__restrict__ tab,
                                                               uint32_t *rec, const uint32_t *n,
                                                               float4 *pts, uint32_t cap) {
+  __shared__ uint32_t s_cnt[EMRT_MAX_DEPTH + 2];
+  __shared__ uint32_t s_order[kBounceBlock];
   const uint32_t cnt = min(*n, cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+  // FP64 work per path grows with its depth: paths handed out by depth
+  for (uint32_t base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
+    const uint32_t i = depth_ordered(rec, base, cnt, s_cnt, s_order);
+    if (i >= cnt) continue;
     uint4 *r = reinterpret_cast<uint4 *>(rec + 8ull * i);
     uint4 a = r[0], b = r[1];
     uint32_t k = a.z & 15u;
