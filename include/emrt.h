@@ -482,6 +482,18 @@ const char *emrt_status_string(emrt_status e);
  * (diagnostics; host-side counter). */
 uint64_t emrt_kernel_launches(void);
 
+/* Self-test of the bounded grid barrier that separates the phases of the
+ * per-frame cooperative tree builds (no paper passage): one cooperative
+ * launch of 4 blocks on the legacy default stream waits at the barrier for
+ * 4 + missing_blocks arrivals, then the call synchronises the device.
+ * *blocks_passed (host) = blocks that got through (4 when missing_blocks is
+ * 0), *timed_out (host) = 1 when the blocks gave up after the barrier's
+ * poll limit (well under a second; always when missing_blocks > 0).  The
+ * context stays usable.  EMRT_ERR_INVALID_ARG for null pointers or
+ * missing_blocks > 1024, EMRT_ERR_CUDA if the launch fails. */
+emrt_status emrt_selftest_grid_barrier(uint32_t missing_blocks, uint32_t *blocks_passed,
+                                       uint32_t *timed_out);
+
 #ifdef __cplusplus
 }
 #endif

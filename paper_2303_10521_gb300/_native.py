@@ -106,6 +106,7 @@ SIGNATURES = {
     "emrt_batch_destroy": (None, [vp]),
     "emrt_status_string": (C.c_char_p, [C.c_int]),
     "emrt_kernel_launches": (u64, []),
+    "emrt_selftest_grid_barrier": (C.c_int, [u32, C.POINTER(u32), C.POINTER(u32)]),
 }
 
 _lib = None

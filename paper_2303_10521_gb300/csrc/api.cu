@@ -173,6 +173,17 @@ extern "C" {
 
 uint64_t emrt_kernel_launches(void) { return emrt::launch_count(); }
 
+emrt_status emrt_selftest_grid_barrier(uint32_t missing_blocks, uint32_t *blocks_passed,
+                                       uint32_t *timed_out) {
+  if (!blocks_passed || !timed_out || missing_blocks > 1024u) return EMRT_ERR_INVALID_ARG;
+  cudaError_t e = emrt::grid_barrier_selftest(missing_blocks, blocks_passed, timed_out);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return EMRT_ERR_CUDA;
+  }
+  return EMRT_OK;
+}
+
 const char *emrt_status_string(emrt_status e) {
   switch (e) {
     case EMRT_OK: return "ok";

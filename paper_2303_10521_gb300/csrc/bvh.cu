@@ -579,7 +579,7 @@ cudaError_t small_build(BVHBuf &b, const float4 *a, const float4 *bx, uint32_t n
 constexpr uint32_t kCoopMax = 65536;
 constexpr int kCoopBlock = 256;
 constexpr uint32_t kCoopTile = 512;
-constexpr uint32_t kBarrierSpins = 1u << 22;
+constexpr uint32_t kBarrierSpins = 1u << 20;  // polls: well under a second
 
 // bar[0]: arrivals, bar[1]: generation, bar[2]: gave-up flag (zeroed
 // before the launch)
@@ -750,6 +750,13 @@ cudaError_t coop_build(BVHBuf &b, const float4 *a, const float4 *bx, uint32_t n,
                                      dim3(kCoopBlock), args, 0, s);
 }
 
+// grid_barrier with nb arrivals expected from a launch of `blocks` blocks:
+// with nb > blocks the barrier cannot complete and every block gives up
+__global__ void k_barrier_selftest(uint32_t *bar, uint32_t nb, uint32_t *err_word,
+                                   uint32_t *passed) {
+  if (grid_barrier(bar, nb, err_word) && threadIdx.x == 0) atomicAdd(passed, 1u);
+}
+
 template <int KIND>
 cudaError_t finish_build(BVHBuf &b, cudaStream_t s) {
   uint32_t n = b.n;
@@ -836,6 +843,27 @@ cudaError_t bvh_build_tris(BVHBuf &b, const float *tri_xyz, const uint32_t *tri_
   sort_codes<PRIM_TRI>(b, hist, s);
   emrt::note_launch(), k_gather_tris<<<ceil_div(n, 256), 256, 0, s>>>(tri_xyz, tri_face, b.idx, n, b.prims);
   return finish_build<PRIM_TRI>(b, s);
+}
+
+cudaError_t grid_barrier_selftest(uint32_t missing, uint32_t *passed, uint32_t *timed_out) {
+  const uint32_t blocks = 4;
+  uint32_t *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(uint32_t) * 6);  // bar[4], err word, passed
+  if (e != cudaSuccess) return e;
+  cudaMemset(d, 0, sizeof(uint32_t) * 6);
+  uint32_t *bar = d, *err = d + 4, *pass = d + 5;
+  uint32_t nb = blocks + missing;
+  void *args[] = {(void *)&bar, (void *)&nb, (void *)&err, (void *)&pass};
+  emrt::note_launch();
+  e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(blocks), dim3(kCoopBlock),
+                                  args, 0, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  uint32_t h[6] = {0, 0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  *passed = h[5];
+  *timed_out = (h[4] & ERR_WAIT) ? 1u : 0u;
+  return e;
 }
 
 cudaError_t bvh_build_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, uint32_t n,

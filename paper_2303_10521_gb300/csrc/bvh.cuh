@@ -70,6 +70,11 @@ cudaError_t bvh_refit_boxes(BVHBuf &b, const float4 *lo, const float4 *hi, cudaS
 // on the node's grid.  Synchronises the stream (build time only).
 cudaError_t bvh8_build(BVHBuf &b, cudaStream_t s);
 
+// Runs the per-frame builds' grid barrier once in a cooperative launch of 4
+// blocks expecting 4 + missing arrivals (synchronous): passed = blocks that
+// got through, timed_out = 1 when a block gave up (ERR_WAIT).
+cudaError_t grid_barrier_selftest(uint32_t missing, uint32_t *passed, uint32_t *timed_out);
+
 // Axis-aligned bounds of n float[9] triangles, written to bbox[2].
 void bbox_of_tris(const float *tri_xyz, uint32_t n, float4 *bbox, cudaStream_t s);
 
