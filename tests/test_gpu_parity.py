@@ -402,13 +402,16 @@ def test_dense_receiver_cluster(engine, form):
     assert ra["n_diff_unflagged"] == 0, ra
 
 
-@pytest.mark.parametrize("n_small", [4096, 65536])
-def test_tree_builders_agree_at_the_size_threshold(engine, n_small):
+@pytest.mark.parametrize("n_small,clustered", [(4096, False), (65536, False), (4096, True),
+                                               (65536, True)])
+def test_tree_builders_agree_at_the_size_threshold(engine, n_small, clustered):
     """Per-frame trees of up to 4096 primitives are built by one block, up to
     65536 by one cooperative launch, larger ones by the device-wide path; the
     trees may differ but every query is exact, so the paths of n_small
     receivers are the same whether one more receiver (which moves the
-    receiver and merged trees to the next builder) is present or not."""
+    receiver and merged trees to the next builder) is present or not.
+    Clustered: half of the receivers in one 0.5 m cube, so that many share a
+    Morton code and the sorts' ties (by index) decide the trees."""
     E = engine
     sc = S.toy_scene(seed=0)
     fr = sc.frame(0)
@@ -416,6 +419,9 @@ def test_tree_builders_agree_at_the_size_threshold(engine, n_small):
     m = n_small + 1
     rx = np.column_stack([rng.uniform(-90, 90, m), rng.uniform(-90, 90, m),
                           rng.uniform(1.0, 3.0, m)]).astype(np.float32)
+    if clustered:
+        h = m // 2
+        rx[:h] = (np.array([12.0, -7.0, 1.5]) + rng.uniform(0, 0.5, (h, 3))).astype(np.float32)
     big = dataclasses.replace(fr, rx_pos=rx, rx_vel=np.zeros_like(rx))
     small = dataclasses.replace(fr, rx_pos=rx[:n_small], rx_vel=np.zeros_like(rx[:n_small]))
     g = _gpu(E, sc, big, max_rx=m)
