@@ -488,7 +488,7 @@ uint64_t emrt_kernel_launches(void);
  * 4 + missing_blocks arrivals, then the call synchronises the device.
  * *blocks_passed (host) = blocks that got through (4 when missing_blocks is
  * 0), *timed_out (host) = 1 when the blocks gave up after the barrier's
- * poll limit (well under a second; always when missing_blocks > 0).  The
+ * poll limit (about 0.7 s; always when missing_blocks > 0).  The
  * context stays usable.  EMRT_ERR_INVALID_ARG for null pointers or
  * missing_blocks > 1024, EMRT_ERR_CUDA if the launch fails. */
 emrt_status emrt_selftest_grid_barrier(uint32_t missing_blocks, uint32_t *blocks_passed,

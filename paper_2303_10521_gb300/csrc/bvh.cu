@@ -579,7 +579,7 @@ cudaError_t small_build(BVHBuf &b, const float4 *a, const float4 *bx, uint32_t n
 constexpr uint32_t kCoopMax = 65536;
 constexpr int kCoopBlock = 256;
 constexpr uint32_t kCoopTile = 512;
-constexpr uint32_t kBarrierSpins = 1u << 20;  // polls: well under a second
+constexpr uint32_t kBarrierSpins = 1u << 19;  // polls of ~1.4 us: about 0.7 s
 
 // bar[0]: arrivals, bar[1]: generation, bar[2]: gave-up flag (zeroed
 // before the launch)

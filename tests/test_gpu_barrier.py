@@ -34,7 +34,7 @@ def test_barrier_gives_up_and_context_survives(lib):
     rc, passed, timed = _run(lib, 1)
     dt = time.perf_counter() - t0
     assert rc == 0 and passed == 0 and timed == 1
-    assert dt < 10.0
+    assert dt < 5.0
     assert _run(lib, 0) == (0, 4, 0)  # the next launch works
     x = torch.arange(8, device="cuda").sum().item()
     assert x == 28
