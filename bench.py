@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import dataclasses
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -120,10 +121,22 @@ def job_throughput(units_per_rank: float, world: int, max_ms: float) -> float:
     return units_per_rank * world / (max_ms / 1e3)
 
 
+def _code_only(text):
+    """C++/CUDA source with comments and blank space removed (a string
+    literal holding comment markers would be cut too; the kernel sources
+    have none that matter), so that editing a comment does not count as a
+    kernel change."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash(form="depth_first"):
+    """Hash of the code (comments and spacing ignored) of the sources the
+    traversal kernel of this form is built from, plus the tree builder."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[form]:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -479,7 +479,8 @@ __global__ void k_bbox_fin(const uint32_t *acc, float4 *bb) {
 // every key distinct, which is the tie-break of equal codes by position.
 // Above 4096 primitives the one block's sort costs more than the launches
 // it saves (measured: the city's 15k-primitive merged tree took 0.57 ms of
-// update instead of 0.25), so larger trees take the device-wide path.
+// update instead of 0.25 with the device-wide path), so larger trees take
+// the cooperative build below (up to kCoopMax) or the device-wide path.
 constexpr uint32_t kSmallBuildMax = 4096;
 constexpr int kSmallBlock = 1024;
 
