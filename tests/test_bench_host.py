@@ -65,6 +65,24 @@ def test_ncu_figures_only_for_the_hashed_sources(tmp_path, monkeypatch):
     assert bench.ncu_summary("depth_first") is None
 
 
+def test_kernel_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+    src = tmp_path / "k.cuh"
+    src.write_text("// a kernel\n__device__ int f(int x) { return x + 1; }  /* one */\n")
+    monkeypatch.setitem(bench.KERNEL_SOURCES, "depth_first", [str(src)])
+    monkeypatch.setattr(bench, "ROOT", "/")
+    h0 = bench.kernel_hash("depth_first")
+    src.write_text("// the same kernel, reworded\n__device__ int f(int x)\n{\n  return x + 1;\n}\n")
+    assert bench.kernel_hash("depth_first") == h0
+    src.write_text("__device__ int f(int x) { return x + 2; }\n")
+    assert bench.kernel_hash("depth_first") != h0
+
+
+def test_committed_traffic_files_match_the_sources():
+    # the committed captures were taken on the code now in the tree
+    for form in ("depth_first", "breadth_first"):
+        assert bench.ncu_summary(form) is not None, form
+
+
 def test_committed_traffic_files_parse():
     for form in ("depth_first", "breadth_first"):
         kv = {}
